@@ -1,0 +1,112 @@
+"""Pins of the oracle's running-line smoother (the `smoothkernel` that Listing 1
+calls; Friedman 1984) against facts that do not come from the oracle itself:
+explicit weighted least squares, explicit leave-one-out refits, exact
+reproduction of constant and linear data, and hand-computed window sizes."""
+import numpy as np
+import pytest
+
+import oracle
+from tests import brute
+
+
+def _data(n, seed, distinct=True):
+    g = np.random.default_rng(seed)
+    x = np.sort(g.uniform(0.0, 1.0, n))
+    if distinct:
+        assert np.all(np.diff(x) > 0)
+    v = g.normal(0.0, 1.0, n)
+    w = g.uniform(0.5, 4.0, n)
+    return x, v, w
+
+
+@pytest.mark.parametrize("n,span,expect", [
+    (100, 0.05, 3), (100, 0.2, 10), (100, 0.5, 25), (3000, 0.05, 75), (3000, 0.2, 300),
+    (3000, 0.5, 750), (10, 0.05, 2), (4, 0.5, 1), (5, 0.05, 2), (30, 0.05, 2), (41, 0.2, 4),
+])
+def test_half_width_table(n, span, expect):
+    # floor(0.5*span*n + 0.5), at least 2, at most (n-1)/2
+    assert oracle.half_width(n, span) == expect
+
+
+@pytest.mark.parametrize("iper", [1, 2, -1, -2])
+@pytest.mark.parametrize("span", [0.05, 0.3, 0.5])
+@pytest.mark.parametrize("n", [5, 7, 12])
+def test_runline_matches_weighted_least_squares(n, span, iper):
+    x, v, w = _data(n, 1000 * n + int(100 * span) + iper)
+    smo, _ = oracle.runline_raw(x, v, w, span, iper, 0.0)
+    ref, _ = brute.runline(x, v, w, span, iper, 0.0, tie_average=False)
+    np.testing.assert_allclose(smo, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_runline_constant_slope_dropped_below_vsmlsq():
+    x, v, w = _data(9, 5)
+    smo, _ = oracle.runline_raw(x, v, w, 0.5, 2, 1e9)  # threshold above any spread
+    ref, _ = brute.runline(x, v, w, 0.5, 2, 1e9, tie_average=False)
+    np.testing.assert_allclose(smo, ref, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("iper", [1, 2])
+def test_runline_reproduces_constant(iper):
+    x, _, w = _data(40, 11)
+    v = np.full(40, 3.25)
+    smo, acvr = oracle.runline(x, v, w, 0.2, iper, 0.0)
+    np.testing.assert_allclose(smo, v, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(acvr, 0.0, atol=1e-12)
+
+
+def test_runline_reproduces_linear_nonperiodic():
+    x, _, w = _data(50, 12)
+    v = -2.0 + 7.5 * x
+    for span in (0.05, 0.2, 0.5):
+        smo, acvr = oracle.runline(x, v, w, span, 1, 0.0)
+        np.testing.assert_allclose(smo, v, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(acvr, 0.0, atol=1e-11)
+
+
+def test_runline_reproduces_linear_periodic_interior():
+    n = 60
+    x, _, w = _data(n, 13)
+    v = 1.0 + 4.0 * x
+    span = 0.2
+    ibw = brute.half_width(n, span)
+    smo, _ = oracle.runline(x, v, w, span, 2, 0.0)
+    interior = np.arange(ibw, n - ibw)  # windows that do not wrap
+    np.testing.assert_allclose(smo[interior], v[interior], rtol=0, atol=1e-12)
+    # wrapped windows see x-1 / x+1 for the far points and cannot be linear
+    assert np.max(np.abs(smo[:ibw] - v[:ibw])) > 1e-3
+
+
+@pytest.mark.parametrize("iper", [1, 2])
+@pytest.mark.parametrize("n", [6, 9, 14])
+def test_cv_residual_is_leave_one_out(n, iper):
+    x, v, w = _data(n, 77 * n + iper)
+    for span in (0.05, 0.2, 0.5):
+        _, acvr = oracle.runline_raw(x, v, w, span, iper, 0.0)
+        _, ref = brute.runline(x, v, w, span, iper, 0.0, tie_average=False)
+        np.testing.assert_allclose(acvr, ref, rtol=1e-9, atol=1e-11)
+
+
+def test_cv_fallback_when_leverage_reaches_one():
+    n = 9
+    x, v, w = _data(n, 21)
+    w = np.ones(n)
+    w[0] = 1e20   # w_0 / W rounds to 1: the residual of point 0 falls back to 0
+    w[4] = 1e20   # and point 4 copies point 3's residual
+    _, acvr = oracle.runline_raw(x, v, w, 0.2, 2, 0.0)
+    assert acvr[0] == 0.0
+    assert acvr[4] == acvr[3]
+    assert acvr[3] > 0.0
+
+
+def test_tie_average_equals_weighted_mean_of_fits():
+    g = np.random.default_rng(3)
+    x = np.sort(np.concatenate([g.uniform(0, 1, 12), [0.25, 0.25, 0.7]]))
+    x = np.sort(np.concatenate([x, [0.25]]))  # a run of 3+ equal abscissae
+    v = g.normal(0, 1, x.size)
+    w = g.uniform(0.5, 2, x.size)
+    smo, _ = oracle.runline(x, v, w, 0.3, 2, 0.0)
+    raw, _ = brute.runline(x, v, w, 0.3, 2, 0.0, tie_average=False)
+    ref = brute.tie_avg(x, w, raw)
+    np.testing.assert_allclose(smo, ref, rtol=1e-12, atol=1e-12)
+    run = np.flatnonzero(x == 0.25)
+    assert run.size >= 3 and np.ptp(smo[run]) == 0.0

@@ -1,0 +1,135 @@
+"""Pins of the oracle's Super Smoother (Listing 1) and single-pass variant
+(Sec. 3, reading) against brute-force restatements built on explicit least
+squares, and against invariants the method has by construction."""
+import numpy as np
+import pytest
+
+import oracle
+from tests import brute
+
+
+def _lc(n, seed):
+    g = np.random.default_rng(seed)
+    x = np.sort(g.uniform(0.0, 1.0, n))
+    y = np.sin(2 * np.pi * x) + g.normal(0.0, 0.3, n)
+    w = g.uniform(0.5, 3.0, n)
+    return x, y, w
+
+
+@pytest.mark.parametrize("alpha", [0.0, 5.0, 9.0, 10.0])
+@pytest.mark.parametrize("n,seed", [(8, 1), (13, 2), (21, 3), (34, 4)])
+def test_supsmu_matches_brute_force(n, seed, alpha):
+    x, y, w = _lc(n, seed)
+    got = oracle.supsmu(x, y, w, iper=2, alpha=alpha)
+    ref = brute.supsmu(x, y, w, alpha=alpha, iper=2)
+    np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-10)
+
+
+@pytest.mark.parametrize("alpha", [0.0, 9.0])
+@pytest.mark.parametrize("n,seed", [(8, 5), (17, 6), (40, 7)])
+def test_supsmu_sp_matches_brute_force(n, seed, alpha):
+    x, y, w = _lc(n, seed)
+    got = oracle.supsmu_sp(x, y, w, iper=2, alpha=alpha)
+    ref = brute.supsmu_sp(x, y, w, alpha=alpha, iper=2)
+    np.testing.assert_allclose(got, ref, rtol=1e-10, atol=1e-11)
+
+
+def test_supsmu_nonperiodic_matches_brute_force():
+    x, y, w = _lc(19, 8)
+    np.testing.assert_allclose(oracle.supsmu(x, y, w, iper=1),
+                               brute.supsmu(x, y, w, iper=1), rtol=1e-9, atol=1e-10)
+    np.testing.assert_allclose(oracle.supsmu_sp(x, y, w, iper=1),
+                               brute.supsmu_sp(x, y, w, iper=1), rtol=1e-10, atol=1e-11)
+
+
+def test_linear_data_reproduced_nonperiodic():
+    g = np.random.default_rng(9)
+    x = np.sort(g.uniform(0, 1, 80))
+    y = 0.5 - 3.0 * x
+    w = g.uniform(1, 2, 80)
+    np.testing.assert_allclose(oracle.supsmu(x, y, w, iper=1), y, atol=1e-11)
+    np.testing.assert_allclose(oracle.supsmu_sp(x, y, w, iper=1), y, atol=1e-11)
+
+
+def test_degenerate_abscissae_give_weighted_mean():
+    x = np.full(10, 0.3)
+    y = np.arange(10.0)
+    w = np.linspace(1, 2, 10)
+    m = np.sum(w * y) / np.sum(w)
+    np.testing.assert_allclose(oracle.supsmu(x, y, w), m, rtol=1e-15)
+    np.testing.assert_allclose(oracle.supsmu_sp(x, y, w), m, rtol=1e-15)
+
+
+@pytest.mark.parametrize("fn", ["supsmu", "supsmu_sp"])
+def test_affine_equivariance(fn):
+    x, y, w = _lc(60, 10)
+    f = getattr(oracle, fn)
+    base = f(x, y, w)
+    np.testing.assert_allclose(f(x, 2.5 * y + 40.0, w), 2.5 * base + 40.0, rtol=1e-12, atol=1e-10)
+
+
+@pytest.mark.parametrize("fn", ["supsmu", "supsmu_sp"])
+def test_periodic_rotation_invariance(fn):
+    # rotating the phase circle permutes the points but keeps every window's
+    # relative geometry; a wrong sign in the +-1 wrap shift breaks this
+    x, y, w = _lc(50, 11)
+    f = getattr(oracle, fn)
+    base = f(x, y, w)
+    for delta in (0.13, 0.5, 0.91):
+        xr = (x + delta) % 1.0
+        order = np.argsort(xr, kind="stable")
+        rot = f(xr[order], y[order], w[order])
+        back = np.empty_like(rot)
+        back[order] = rot
+        np.testing.assert_allclose(back, base, rtol=1e-9, atol=1e-10)
+
+
+def test_alpha_zero_never_enhances():
+    # with alpha = 0 the chosen span is always one of the three spans, so the
+    # final output equals brute force without the bass step
+    x, y, w = _lc(30, 12)
+    np.testing.assert_allclose(oracle.supsmu(x, y, w, alpha=0.0),
+                               brute.supsmu(x, y, w, alpha=0.0), rtol=1e-9, atol=1e-10)
+    assert not np.allclose(oracle.supsmu(x, y, w, alpha=0.0), oracle.supsmu(x, y, w, alpha=9.0))
+
+
+def test_fixed_span_mode_is_one_running_line():
+    x, y, w = _lc(25, 13)
+    vs = brute.vsmlsq_of(x)
+    ref, _ = brute.runline(x, y, w, 0.3, 2, vs)
+    np.testing.assert_allclose(oracle.supsmu(x, y, w, span=0.3), ref, rtol=1e-10, atol=1e-11)
+
+
+def test_vsmlsq_hand_values():
+    # Listing 1: scale = x[3(n/4)-1] - x[n/4-1] (0-based), vsmlsq = 1e-6 scale^2
+    x = np.arange(8) / 8.0          # i = 1, j = 5
+    assert oracle.vsmlsq(x) == pytest.approx(1e-6 * (5 / 8 - 1 / 8) ** 2, rel=1e-15)
+    x = np.arange(13) / 13.0        # n/4 = 3: i = 2, j = 8
+    assert oracle.vsmlsq(x) == pytest.approx(1e-6 * (8 / 13 - 2 / 13) ** 2, rel=1e-15)
+    x = np.array([0.0, 0.1, 0.4, 0.9])  # n = 4: i = 0, j = 2
+    assert oracle.vsmlsq(x) == pytest.approx(1e-6 * 0.4 ** 2, rel=1e-15)
+
+
+def test_vsmlsq_threshold_drops_slope_where_spread_is_small():
+    # weights scaled so that window spreads straddle vsmlsq: the slope is then
+    # dropped in some windows only, which the brute force reproduces only with
+    # the same threshold
+    x, y, w = _lc(24, 14)
+    vs = brute.vsmlsq_of(x)
+    for scale in (3e-5, 1e-4, 3e-4):
+        ws = w * scale
+        np.testing.assert_allclose(oracle.supsmu(x, y, ws), brute.supsmu(x, y, ws),
+                                   rtol=1e-9, atol=1e-10)
+    assert vs > 0
+
+
+def test_clamp_of_smoothed_span_matters():
+    # clustered phases make the midrange line through the chosen spans
+    # overshoot [0.05, 0.5]; Listing 1 clamps before interpolating
+    g = np.random.default_rng(2)
+    x = np.sort(np.concatenate([g.uniform(0.0, 0.08, 10), g.uniform(0.5, 0.55, 10),
+                                g.uniform(0, 1, 4)]))
+    y = np.where(x < 0.3, 0.0, 1.0) + g.normal(0, 0.05, 24) + 3 * np.sin(6 * x)
+    w = g.uniform(0.5, 3, 24)
+    np.testing.assert_allclose(oracle.supsmu(x, y, w), brute.supsmu(x, y, w),
+                               rtol=1e-9, atol=1e-10)
