@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Throughput of the Super Smoother periodogram on one GB300 (or N, weak).
+
+Workload: one seasonal light curve of 3,000 points over 3,000 d with 100,000
+trial frequencies in [0.01, 20) (the single-large-object configuration,
+FP64 vs FP32-compensated).  One step = the whole hot path twice over that
+input -- Super Smoother (Listing 1) and SuperSmootherSP (Sec. 3) -- through
+the C ABI's device entry point in FP32C: fold, sort, smoother, chi2/power
+and argmax.  Metric: point*frequency evaluations per second.
+
+The JSON line also carries: FP64 throughput of the same work and its
+agreement with FP32C, the oracle checked on sampled frequencies, e2e through
+the host entry point from pinned memory, the roofline of the dominant
+kernel (ALU-bound), the oracle timed on the host cores, and SM clocks
+sampled during the timed region.
+
+--impl reference times the plain FP64 C oracle (the only reference there is)
+on the host cores over a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "point·frequency evals/s (SS & SSSP), FP32-comp vs FP64 at tol, 1 GB300"
+UNIT = "pt*f/s"
+# Algorithmic FP operations per (point, frequency), counted on Friedman's
+# updating-formula running line (one op per +, -, *, /): a window slide
+# (remove + add) is 36 ops, a fit 4, a cross-validated residual 9 more.
+# SS = 3 CV smooths + 3 residual smooths + span smooth + final smooth
+#      + span choice/bass (8) + clamp/interpolation (8) + chi2 (3) = 366.
+# SP = 3 fits + 3 generalized-validation residuals (3 each) + span choice (8)
+#      + interpolation (8) + chi2 (3) = 148.
+OPS_PER_PTF = {"ss": 3 * 49 + 3 * 40 + 40 + 40 + 8 + 8 + 3,
+               "sp": 3 * 40 + 3 * 3 + 8 + 8 + 3}
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--n-freq", type=int, default=100_000)
+    return ap.parse_args()
+
+
+def workload(n_freq):
+    from paper_2111_07396_gb300 import synth
+    cat = synth.config2(n_freq=n_freq)
+    desc = {"workload": f"single seasonal object n={cat.points}, {cat.freq.size} freqs "
+                        "in [0.01,20); SS + SP per step",
+            "objects": 1, "points": cat.points, "n_freq": int(cat.freq.size),
+            "variants": ["ss", "sp"], "precision": "fp32c",
+            "l2": "flushed between timed steps (512 MiB write)"}
+    return cat, desc
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(cat, budget_s=12.0, max_freq=4096):
+    """The FP64 oracle, as it stands, on the host cores over a bounded sample
+    of the workload's frequencies (both variants)."""
+    import oracle
+    t, y, dy = cat.obj(0)
+    n = t.size
+    rng = np.random.default_rng(7)
+    order = rng.permutation(cat.freq.size)
+    cores = os.cpu_count() or 1
+    done, used = 0, 0.0
+    batch = max(cores, 16)
+    while done < max_freq and used < budget_s:
+        fq = cat.freq[order[done:done + batch]]
+        t0 = time.perf_counter()
+        for code in (oracle.SS, oracle.SP):
+            oracle.periodogram(t, y, dy, [n], fq, code, n_threads=cores)
+        used += time.perf_counter() - t0
+        done += fq.size
+    ptf = 2 * n * done
+    return {"value": ptf / used, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} of {cat.freq.size} frequencies (random), SS+SP, n={n}, "
+                      f"{used:.1f} s wall"}
+
+
+def run_reference(args):
+    """Reference arm: the plain FP64 C oracle on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cat, desc = workload(args.n_freq)
+    t, y, dy = cat.obj(0)
+    n = t.size
+    cores = os.cpu_count() or 1
+    per_step = max(2 * cores, 32)
+    rng = np.random.default_rng(11)
+
+    def step(k):
+        fq = cat.freq[rng.choice(cat.freq.size, per_step, replace=False)]
+        for code in (oracle.SS, oracle.SP):
+            oracle.periodogram(t, y, dy, [n], fq, code, n_threads=cores)
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(k)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 2 * n * per_step / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": desc, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} random frequencies per step, SS+SP, n={n}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_2111_07396_gb300 import build as ssp_build
+    from paper_2111_07396_gb300 import ssp
+    from tests.parity import gate_error
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        ssp_build.build()
+    if dist is not None:
+        dist.barrier()
+    ssp.lib()
+
+    cat, desc = workload(args.n_freq)
+    n, nf = cat.points, int(cat.freq.size)
+    dev = torch.device("cuda", local)
+    t = torch.from_numpy(cat.t).to(dev)
+    y = torch.from_numpy(cat.y).to(dev)
+    dy = torch.from_numpy(cat.dy).to(dev)
+    fq = torch.from_numpy(cat.freq).to(dev)
+    npo = cat.n_per_object
+    out = {v: (torch.empty((1, nf), dtype=torch.float32, device=dev),
+               torch.empty(1, dtype=torch.float64, device=dev)) for v in ("ss", "sp")}
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    def step(precision="fp32c", outs=out):
+        for v in ("ss", "sp"):
+            ssp.ssp_periodogram_device(t, y, dy, npo, fq, outs[v][0], outs[v][1], variant=v,
+                                       precision=precision, stream=stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ssp.ssp_profile_read(reset=True)
+        ssp.ssp_profile_enable(True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            for k in range(args.steps):
+                flush.fill_(float(k))           # L2 flush, outside the timed events
+                ev[k][0].record(stream)
+                step()
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        ssp.ssp_profile_enable(False)
+        prof = ssp.ssp_profile_read(reset=True)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if dist is not None:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ptf_step = 2 * n * nf
+    value = world * ptf_step * args.steps / (total_ms / 1e3)
+    clocks = clk.summary()
+
+    # FP32C results of the last step, and the same work in FP64
+    p32 = {v: out[v][0].cpu().numpy()[0].astype(np.float64) for v in out}
+    b32 = {v: float(out[v][1].cpu().item()) for v in out}
+    fp64 = None
+    acc = {}
+    if not args.no_fp64:
+        out64 = {v: (torch.empty((1, nf), dtype=torch.float64, device=dev),
+                     torch.empty(1, dtype=torch.float64, device=dev)) for v in ("ss", "sp")}
+        with torch.cuda.stream(stream):
+            step("fp64", out64)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ssp.ssp_profile_enable(True)
+            e0.record(stream)
+            step("fp64", out64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ssp.ssp_profile_enable(False)
+            prof64 = ssp.ssp_profile_read(reset=True)
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": ptf_step / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                "pgram_ms": {"ss": prof64["pgram_ss"][1], "sp": prof64["pgram_sp"][1]}}
+        for v in ("ss", "sp"):
+            ref = out64[v][0].cpu().numpy()[0]
+            acc[v] = {"max_gate_err_vs_fp64": gate_error(p32[v], ref),
+                      "max_abs_err_vs_fp64": float(np.max(np.abs(p32[v] - ref))),
+                      "best_index_same": bool(np.argmax(p32[v]) == np.argmax(ref)),
+                      "tolerance": 2e-4}
+        fp64["speedup_fp32c_over_fp64"] = fp64["ms_per_step"] / (total_ms / args.steps)
+
+    # e2e through the host entry point from pinned host memory
+    th = torch.from_numpy(cat.t).pin_memory()
+    yh = torch.from_numpy(cat.y).pin_memory()
+    dyh = torch.from_numpy(cat.dy).pin_memory()
+    fh = torch.from_numpy(cat.freq).pin_memory()
+    pw_h = {v: torch.empty((1, nf), dtype=torch.float32).pin_memory() for v in ("ss", "sp")}
+    bp_h = {v: torch.empty(1, dtype=torch.float64).pin_memory() for v in ("ss", "sp")}
+
+    def e2e_step():
+        for v in ("ss", "sp"):
+            ssp.ssp_periodogram(th, yh, dyh, npo, fh, variant=v, precision="fp32c",
+                                out_power=pw_h[v], out_best_period=bp_h[v])
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    h2d = 2 * (3 * 8 * n + 8 * nf)
+    d2h = 2 * (4 * nf + 8)
+    e2e = {"value": world * ptf_step * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "api": "ssp_periodogram (host pointers, pinned), SS + SP"}
+
+    # roofline of the dominant kernel (SS periodogram kernel), ALU-bound
+    ss_launches, ss_ms = prof["pgram_ss"]
+    sp_launches, sp_ms = prof["pgram_sp"]
+    clk_mhz = clocks["sm_mhz"] if clocks else 1432.0
+    peak = FP32_LANES_PER_SM * sms * clk_mhz * 1e6 / 1e12
+    ach_ss = OPS_PER_PTF["ss"] * n * nf / (ss_ms / ss_launches / 1e3) / 1e12
+    ach_sp = OPS_PER_PTF["sp"] * n * nf / (sp_ms / sp_launches / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": "pgram_kernel<float,SS>", "achieved": ach_ss,
+            "peak": peak, "unit": "TFLOP/s", "frac": ach_ss / peak, "traffic": None,
+            "ops_per_ptf": OPS_PER_PTF["ss"], "avg_launch_ms": ss_ms / ss_launches,
+            "peak_basis": f"{FP32_LANES_PER_SM} FP32 ops/clk/SM x {sms} SMs x "
+                          f"{clk_mhz:.0f} MHz (median SM clock sampled during the timed region)",
+            "sp": {"kernel": "pgram_kernel<float,SP>", "achieved": ach_sp,
+                   "frac": ach_sp / peak, "ops_per_ptf": OPS_PER_PTF["sp"],
+                   "avg_launch_ms": sp_ms / sp_launches}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": desc, "e2e": e2e,
+            "gpu_launches": 6 * args.steps, "roofline": roof, "clocks": clocks,
+            "breakdown_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+            "per_variant_ptf_s": {"ss": ptf_step / 2 / (ss_ms / ss_launches / 1e3),
+                                  "sp": ptf_step / 2 / (sp_ms / sp_launches / 1e3)},
+            "fp64": fp64, "accuracy_fp32c": acc,
+            "best_period": b32}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cat)
+        # oracle at a few sampled frequencies against this run's FP32C output
+        import oracle
+        from tests.parity import oracle_powers, sample_freqs
+        tt_, yy, dyy = cat.obj(0)
+        chk = {}
+        for v, code in (("ss", oracle.SS), ("sp", oracle.SP)):
+            qs = sample_freqs(nf, 12, seed=5, include=[int(np.argmax(p32[v]))])
+            ref = oracle_powers(tt_, yy, dyy, cat.freq[qs], code)
+            chk[v] = {"frequencies": int(qs.size), "max_gate_err": gate_error(p32[v][qs], ref)}
+        line["oracle_check_fp32c"] = chk
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,151 @@
+/*
+ * ssp.h -- C ABI of libssp, a GB300 (sm_103a) implementation of the Super
+ * Smoother periodogram of Gowanlock, Butler, Trilling & McNeill, "GPU-Enabled
+ * Searches for Periodic Signals of Unknown Shape" (arXiv 2111.07396).
+ *
+ * For every (object, trial frequency) pair the library folds the light curve
+ * (phase = frac(tt * f), tt = t - min t; Alg. 1), sorts it by phase (stable,
+ * ties by original index), smooths the folded curve with Friedman's Super
+ * Smoother (Listing 1, "SS") or the single-pass generalized-validation
+ * variant (Sec. 3, "SP"), and reduces the smooth to
+ *     power = 1 - chi2 / chi0,  chi2 = sum w (y - smo)^2,
+ *     chi0 = sum w (y - ybar_w)^2,  w = dy^-2                  (Alg. 1)
+ * then reports the period 1/f of the first maximum (findPeriod, Alg. 1).
+ *
+ * Conventions for every entry point:
+ *  - Objects are concatenated in CSR order: object o owns n_per_object[o]
+ *    consecutive points of t, y and dy.  Times need not be sorted.  Frequency
+ *    is ordinary (cycles per time unit), not angular (App. A).
+ *  - freq_grid holds n_freq explicit trial frequencies shared by all objects
+ *    (Sec. 4.3, catalogs share one grid); any positive values, any order.
+ *  - out_power is row-major [n_objects][n_freq]; its element type is double
+ *    for SSP_FP64 and float for SSP_FP32C.  out_best_period is double
+ *    [n_objects].
+ *  - The caller owns every buffer; the library keeps no pointer after the
+ *    call returns (the device entry point keeps none after its work on the
+ *    stream completes).
+ *  - Return value: SSP_OK or a negative ssp_status.  On error the outputs
+ *    are unspecified; ssp_last_error() gives a message (per thread).
+ *  - Results are deterministic and independent of how many objects share a
+ *    call.
+ */
+#ifndef SSP_H
+#define SSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SSP_SS = 0, /* Super Smoother, cross-validated spans (Listing 1) */
+    SSP_SP = 1  /* SuperSmootherSP, generalized validation, one pass (Sec. 3) */
+} ssp_variant;
+
+typedef enum {
+    SSP_FP64 = 0,  /* every step in binary64; phase fold bit-identical to Alg. 1 */
+    SSP_FP32C = 1  /* exact fixed-point fold, FP32 smoothing with local origins,
+                      compensated chi2; power written as float */
+} ssp_precision;
+
+typedef enum {
+    SSP_OK = 0,
+    SSP_ERR_ARG = -1,         /* invalid argument or input value */
+    SSP_ERR_NOMEM = -2,       /* device memory budget exceeded */
+    SSP_ERR_CUDA = -3,        /* a CUDA call failed */
+    SSP_ERR_TIMEOUT = -4,     /* a bounded wait expired */
+    SSP_ERR_UNSUPPORTED = -5  /* valid request this build cannot run */
+} ssp_status;
+
+typedef struct {
+    double spans[3];     /* tweeter, midrange, woofer spans as fractions of n;
+                            default {0.05, 0.2, 0.5} (Listing 1).  Must satisfy
+                            0 < spans[0] < spans[1] < spans[2] <= 1. */
+    double alpha;        /* bass enhancement in [0, 10]; default 9 (Sec. 5.1);
+                            0 disables it (Sec. 5.4, transits). */
+    int periodic;        /* 1 (default): windows wrap around the phase circle
+                            (Listing 1 iper = 2).  0 is SSP_ERR_UNSUPPORTED. */
+    ssp_precision precision; /* default SSP_FP32C */
+    double hbm_fraction; /* beta of Eq. 1: fraction of free device memory the
+                            host entry point may use; default 0.75 (Sec. 4.1) */
+} ssp_params;
+
+/* Fill *p with the defaults listed above. */
+void ssp_default_params(ssp_params *p);
+
+/*
+ * Periodograms of a catalog from HOST memory (Alg. 1 end to end, batched).
+ *   t, y, dy        host f64 [sum n]; t and y finite, dy finite and > 0.
+ *   n_per_object    host i64 [n_objects]; every n >= 4 (Listing 1 reads
+ *                   x[3(n/4)-1]) and n <= 65535.
+ *   freq_grid       host f64 [n_freq]; finite and > 0.
+ *   params          NULL selects ssp_default_params.
+ *   out_power       host [n_objects][n_freq], double (FP64) or float (FP32C).
+ *   out_best_period host f64 [n_objects].
+ * Copies inputs to the device, runs the whole path there, copies the results
+ * back and returns when they are in host memory.  Objects are processed in
+ * batches sized to hbm_fraction of free device memory (Eq. 1's role).
+ * Errors: SSP_ERR_ARG (any rule above, n_objects < 1, n_freq < 1, bad
+ * params), SSP_ERR_NOMEM (one object's minimum batch does not fit),
+ * SSP_ERR_UNSUPPORTED (periodic = 0; FP32C with a weight outside the float
+ * range), SSP_ERR_CUDA.
+ */
+int ssp_periodogram(const double *t, const double *y, const double *dy,
+                    const int64_t *n_per_object, int64_t n_objects,
+                    const double *freq_grid, int64_t n_freq, ssp_variant variant,
+                    const ssp_params *params, void *out_power, double *out_best_period);
+
+/*
+ * Same computation on DEVICE memory, enqueued on `stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  t, y, dy, freq_grid, out_power and
+ * out_best_period are device pointers; n_per_object is a HOST array (the
+ * launch plan is built from it).  Returns after enqueueing (plus the host
+ * work of planning); results are valid once the stream reaches that point.
+ * Input values are checked on the device: an object with a non-finite t or y,
+ * or a dy that is not finite and > 0, gets NaN powers and a NaN best period.
+ * Temporary device memory is taken from the stream-ordered allocator.
+ * Errors: as ssp_periodogram, except that value checks become NaN outputs.
+ */
+int ssp_periodogram_device(const double *t, const double *y, const double *dy,
+                           const int64_t *n_per_object, int64_t n_objects,
+                           const double *freq_grid, int64_t n_freq, ssp_variant variant,
+                           const ssp_params *params, void *out_power,
+                           double *out_best_period, void *stream);
+
+/* Static text for a status code. */
+const char *ssp_status_string(int status);
+/* Detail of the last error returned on the calling thread ("" if none). */
+const char *ssp_last_error(void);
+
+/* Library version string, "ssp <major>.<minor> sm_103a". */
+const char *ssp_version(void);
+
+/*
+ * Per-phase timers (the paper's Tables 3-4 break time down the same way).
+ * When enabled, every launch of a phase is bracketed by two CUDA events
+ * recorded on the launching stream.  ssp_profile_read waits for the recorded
+ * events, fills out[k] for k = SSP_PHASE_PREP (Alg. 1 compute_chi0_tt_weights),
+ * SSP_PHASE_PGRAM_SS / SSP_PHASE_PGRAM_SP (fold + sort + smoother + chi2 of
+ * that variant, one launch per length bucket) and SSP_PHASE_ARGMAX
+ * (findPeriod), and clears them if reset != 0.  Off by default; enabling
+ * adds two event records per launch.
+ */
+enum {
+    SSP_PHASE_PREP = 0,
+    SSP_PHASE_PGRAM_SS = 1,
+    SSP_PHASE_PGRAM_SP = 2,
+    SSP_PHASE_ARGMAX = 3,
+    SSP_N_PHASES = 4
+};
+typedef struct {
+    int64_t launches; /* launches recorded */
+    double ms;        /* summed event-to-event time, milliseconds */
+} ssp_phase_time;
+void ssp_profile_enable(int on);
+int ssp_profile_read(ssp_phase_time out[SSP_N_PHASES], int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSP_H */

@@ -1,0 +1,577 @@
+// ssp_api.cu -- the C ABI of libssp (include/ssp.h): argument checks, the
+// launch planner (length buckets, work items, device-memory batches) and the
+// host/device entry points.  All arithmetic of the method runs in the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ssp.h"
+#include "ssp_launch.h"
+
+namespace ssp {
+cudaError_t prep_launch_fp32(const PrepArgs &, int, cudaStream_t);
+cudaError_t prep_launch_fp64(const PrepArgs &, int, cudaStream_t);
+cudaError_t argmax_launch_fp32(const ArgmaxArgs &, int, cudaStream_t);
+cudaError_t argmax_launch_fp64(const ArgmaxArgs &, int, cudaStream_t);
+cudaError_t pgram_occupancy_fp32(int, bool, int, size_t, int *);
+cudaError_t pgram_occupancy_fp64(int, bool, int, size_t, int *);
+cudaError_t pgram_launch_fp32(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_launch_fp64(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+size_t pgram_small_bytes_fp32(int);
+size_t pgram_small_bytes_fp64(int);
+size_t pgram_frame_bytes_fp32(int);
+size_t pgram_frame_bytes_fp64(int);
+
+cudaError_t prep_launch(int p, const PrepArgs &a, int n, cudaStream_t s)
+{
+    return p == SSP_FP64 ? prep_launch_fp64(a, n, s) : prep_launch_fp32(a, n, s);
+}
+cudaError_t argmax_launch(int p, const ArgmaxArgs &a, int n, cudaStream_t s)
+{
+    return p == SSP_FP64 ? argmax_launch_fp64(a, n, s) : argmax_launch_fp32(a, n, s);
+}
+cudaError_t pgram_occupancy(int p, int v, bool g, int G, size_t smem, int *bps)
+{
+    return p == SSP_FP64 ? pgram_occupancy_fp64(v, g, G, smem, bps)
+                         : pgram_occupancy_fp32(v, g, G, smem, bps);
+}
+cudaError_t pgram_launch(int p, int v, bool g, int grid, int G, size_t smem, const PgramArgs &a,
+                         cudaStream_t s)
+{
+    return p == SSP_FP64 ? pgram_launch_fp64(v, g, grid, G, smem, a, s)
+                         : pgram_launch_fp32(v, g, grid, G, smem, a, s);
+}
+size_t pgram_small_bytes(int p, int G)
+{
+    return p == SSP_FP64 ? pgram_small_bytes_fp64(G) : pgram_small_bytes_fp32(G);
+}
+size_t pgram_frame_bytes(int p, int n)
+{
+    return p == SSP_FP64 ? pgram_frame_bytes_fp64(n) : pgram_frame_bytes_fp32(n);
+}
+}  // namespace ssp
+
+using namespace ssp;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(SSP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SSP_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+constexpr int kMaxN = 65535;
+// device bytes set aside per batch for the per-CTA frames of large objects
+constexpr double kSlabReserve = 2.0e9;
+
+int check_params(const ssp_params *p)
+{
+    if (!(p->spans[0] > 0.0 && p->spans[0] < p->spans[1] && p->spans[1] < p->spans[2] &&
+          p->spans[2] <= 1.0))
+        return fail(SSP_ERR_ARG, "spans must satisfy 0 < s0 < s1 < s2 <= 1");
+    if (!(p->alpha >= 0.0 && p->alpha <= 10.0)) return fail(SSP_ERR_ARG, "alpha must be in [0, 10]");
+    if (p->precision != SSP_FP64 && p->precision != SSP_FP32C)
+        return fail(SSP_ERR_ARG, "unknown precision %d", (int)p->precision);
+    if (!(p->hbm_fraction > 0.0 && p->hbm_fraction <= 1.0))
+        return fail(SSP_ERR_ARG, "hbm_fraction must be in (0, 1]");
+    if (p->periodic != 1)
+        return fail(SSP_ERR_UNSUPPORTED, "only periodic windows are implemented (periodic = 1)");
+    return SSP_OK;
+}
+
+int check_shape(const int64_t *n_per_object, int64_t n_objects, int64_t n_freq, ssp_variant v)
+{
+    if (n_objects < 1) return fail(SSP_ERR_ARG, "n_objects must be >= 1");
+    if (n_objects > (int64_t)1 << 30) return fail(SSP_ERR_ARG, "n_objects too large");
+    if (n_freq < 1) return fail(SSP_ERR_ARG, "n_freq must be >= 1");
+    if (n_freq > (int64_t)1 << 31) return fail(SSP_ERR_ARG, "n_freq too large");
+    if (v != SSP_SS && v != SSP_SP) return fail(SSP_ERR_ARG, "unknown variant %d", (int)v);
+    if (!n_per_object) return fail(SSP_ERR_ARG, "n_per_object is NULL");
+    for (int64_t o = 0; o < n_objects; ++o) {
+        if (n_per_object[o] < 4)
+            return fail(SSP_ERR_ARG, "object %lld has %lld points; at least 4 are needed",
+                        (long long)o, (long long)n_per_object[o]);
+        if (n_per_object[o] > kMaxN)
+            return fail(SSP_ERR_ARG, "object %lld has %lld points; at most %d are supported",
+                        (long long)o, (long long)n_per_object[o], kMaxN);
+    }
+    return SSP_OK;
+}
+
+// threads per CTA for an object of n points: about a dozen centres per thread
+int group_size(int n)
+{
+    if (n <= 384) return 32;
+    if (n <= 768) return 64;
+    if (n <= 1536) return 128;
+    return 256;
+}
+
+struct Bucket {
+    int G = 32, n_max = 0;
+    bool gmem = false;
+    size_t smem = 0, slab_bytes = 0;
+    int grid = 0;
+    std::vector<int> objects;
+    std::vector<int4> items;
+};
+
+struct Plan {
+    std::vector<Bucket> buckets;
+    size_t items_total = 0, slab_total = 0;
+};
+
+int device_limits(int *num_sms, size_t *max_smem)
+{
+    int dev = 0, sms = 0, optin = 0;
+    SSP_CUDA(cudaGetDevice(&dev));
+    SSP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SSP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    *num_sms = sms;
+    *max_smem = (size_t)optin;
+    return SSP_OK;
+}
+
+// Length buckets (one launch each, sized for the bucket's largest object),
+// work items (object, frequency range) ordered longest first.
+int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision, int variant,
+               Plan &plan)
+{
+    int sms = 0;
+    size_t max_smem = 0;
+    int rc = device_limits(&sms, &max_smem);
+    if (rc) return rc;
+    plan.buckets.clear();
+    for (int G : {32, 64, 128, 256}) {
+        Bucket b;
+        b.G = G;
+        for (int64_t o = 0; o < n_obj; ++o)
+            if (group_size((int)npo[o]) == G) {
+                b.objects.push_back((int)o);
+                b.n_max = std::max(b.n_max, (int)npo[o]);
+            }
+        if (!b.objects.empty()) plan.buckets.push_back(std::move(b));
+    }
+    plan.items_total = 0;
+    plan.slab_total = 0;
+    for (Bucket &b : plan.buckets) {
+        const size_t small = align16(pgram_small_bytes(precision, b.G));
+        const size_t frame = align16(pgram_frame_bytes(precision, b.n_max));
+        b.gmem = small + frame + 1024 > max_smem;
+        b.smem = b.gmem ? small : small + frame;
+        b.slab_bytes = b.gmem ? frame : 0;
+        int bps = 0;
+        cudaError_t e = pgram_occupancy(precision, variant, b.gmem, b.G, b.smem, &bps);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+        if (bps < 1) return fail(SSP_ERR_NOMEM, "a CTA frame for n = %d does not fit", b.n_max);
+        const int resident = bps * sms;
+        // enough items for dynamic balance: ~8 per resident CTA
+        const int64_t want = std::max<int64_t>(8LL * resident, (int64_t)b.objects.size());
+        int64_t per_obj = (want + (int64_t)b.objects.size() - 1) / (int64_t)b.objects.size();
+        per_obj = std::max<int64_t>(1, std::min<int64_t>(per_obj, n_freq));
+        const int64_t chunk = (n_freq + per_obj - 1) / per_obj;
+        std::vector<std::pair<int64_t, int4>> keyed;
+        for (int o : b.objects)
+            for (int64_t q0 = 0; q0 < n_freq; q0 += chunk) {
+                const int q1 = (int)std::min<int64_t>(n_freq, q0 + chunk);
+                keyed.push_back({-(int64_t)npo[o] * (q1 - q0), make_int4(o, (int)q0, q1, 0)});
+            }
+        std::stable_sort(keyed.begin(), keyed.end(),
+                         [](const auto &x, const auto &y) { return x.first < y.first; });
+        b.items.resize(keyed.size());
+        for (size_t k = 0; k < keyed.size(); ++k) b.items[k] = keyed[k].second;
+        b.grid = (int)std::min<int64_t>((int64_t)b.items.size(), resident);
+        plan.items_total += b.items.size();
+        plan.slab_total += b.gmem ? b.slab_bytes * (size_t)b.grid : 0;
+    }
+    return SSP_OK;
+}
+
+size_t rsize(int precision) { return precision == SSP_FP64 ? 8 : 4; }
+
+// device bytes of one batch apart from the caller's arrays
+size_t workspace_bytes(const Plan &plan, int64_t n_obj, int64_t n_points, int precision)
+{
+    size_t b = 0;
+    b += align16(8 * (size_t)(n_obj + 1));               // off
+    b += align16(8 * (size_t)n_points);                  // tt or tfix
+    b += align16(4 * (size_t)n_obj) * 2;                 // texp, bad
+    b += align16(rsize(precision) * (size_t)n_points) * 2;  // yc, wv
+    b += align16(8 * (size_t)n_obj);                     // chi0
+    b += align16(sizeof(int4) * plan.items_total);
+    b += align16(4 * plan.buckets.size() + 4);
+    b += plan.slab_total;
+    return b;
+}
+
+// ---- per-phase event timers ----
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+struct Mark {
+    int phase;
+    cudaEvent_t a, b;
+};
+std::vector<Mark> g_marks;
+
+bool prof_begin(int phase, cudaStream_t s, Mark &m)
+{
+    if (!g_prof_on) return false;
+    m.phase = phase;
+    if (cudaEventCreate(&m.a) != cudaSuccess) return false;
+    if (cudaEventCreate(&m.b) != cudaSuccess) {
+        cudaEventDestroy(m.a);
+        return false;
+    }
+    cudaEventRecord(m.a, s);
+    return true;
+}
+
+void prof_end(bool on, Mark &m, cudaStream_t s)
+{
+    if (!on) return;
+    cudaEventRecord(m.b, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_marks.push_back(m);
+}
+
+void keep_pool_memory()
+{
+    // keep freed stream-ordered memory cached in the pool between calls
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+}
+
+
+// The whole device path of one batch, enqueued on stream s.
+int run_device(const double *t, const double *y, const double *dy, const int64_t *npo,
+               int64_t n_obj, const double *freq, int64_t n_freq, ssp_variant variant,
+               const ssp_params &P, void *out_power, double *out_best, cudaStream_t s)
+{
+    const int prec = (int)P.precision;
+    Plan plan;
+    int rc = build_plan(npo, n_obj, n_freq, prec, (int)variant, plan);
+    if (rc) return rc;
+    std::vector<int64_t> off((size_t)n_obj + 1, 0);
+    for (int64_t o = 0; o < n_obj; ++o) off[o + 1] = off[o] + npo[o];
+    const int64_t N = off[n_obj];
+    const size_t ws = workspace_bytes(plan, n_obj, N, prec);
+    unsigned char *base = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&base, ws, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SSP_ERR_NOMEM, "workspace of %zu bytes: %s", ws, cudaGetErrorString(e));
+    }
+    size_t cur = 0;
+    auto take = [&](size_t bytes) {
+        unsigned char *p = base + cur;
+        cur += align16(bytes);
+        return p;
+    };
+    int64_t *d_off = (int64_t *)take(8 * (size_t)(n_obj + 1));
+    void *d_tt = take(8 * (size_t)N);
+    int *d_texp = (int *)take(4 * (size_t)n_obj);
+    int *d_bad = (int *)take(4 * (size_t)n_obj);
+    void *d_yc = take(rsize(prec) * (size_t)N);
+    void *d_wv = take(rsize(prec) * (size_t)N);
+    double *d_chi0 = (double *)take(8 * (size_t)n_obj);
+    int4 *d_items = (int4 *)take(sizeof(int4) * plan.items_total);
+    int *d_counters = (int *)take(4 * plan.buckets.size() + 4);
+    unsigned char *d_slab = base + cur;
+
+    std::vector<int4> items;
+    items.reserve(plan.items_total);
+    for (const Bucket &b : plan.buckets) items.insert(items.end(), b.items.begin(), b.items.end());
+    int status = SSP_OK;
+    do {
+        if ((e = cudaMemcpyAsync(d_off, off.data(), 8 * off.size(), cudaMemcpyHostToDevice, s))) break;
+        if ((e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(),
+                                 cudaMemcpyHostToDevice, s)))
+            break;
+        if ((e = cudaMemsetAsync(d_counters, 0, 4 * plan.buckets.size() + 4, s))) break;
+        PrepArgs pa{};
+        pa.t = t;
+        pa.y = y;
+        pa.dy = dy;
+        pa.off = d_off;
+        pa.tt = (double *)d_tt;
+        pa.tfix = (uint64_t *)d_tt;
+        pa.texp = d_texp;
+        pa.yc = d_yc;
+        pa.wv = d_wv;
+        pa.chi0 = d_chi0;
+        pa.bad = d_bad;
+        Mark mk;
+        bool on = prof_begin(SSP_PHASE_PREP, s, mk);
+        if ((e = prep_launch(prec, pa, (int)n_obj, s))) break;
+        prof_end(on, mk, s);
+        size_t item_base = 0, slab_cur = 0;
+        for (size_t k = 0; k < plan.buckets.size(); ++k) {
+            const Bucket &b = plan.buckets[k];
+            PgramArgs ga{};
+            ga.off = d_off;
+            ga.tt = (const double *)d_tt;
+            ga.tfix = (const uint64_t *)d_tt;
+            ga.texp = d_texp;
+            ga.yc = d_yc;
+            ga.wv = d_wv;
+            ga.chi0 = d_chi0;
+            ga.bad = d_bad;
+            ga.freq = freq;
+            ga.n_freq = n_freq;
+            ga.items = d_items + item_base;
+            ga.n_items = (int)b.items.size();
+            ga.item_counter = d_counters + k;
+            ga.power = out_power;
+            for (int i = 0; i < 3; ++i) ga.spans[i] = P.spans[i];
+            ga.alpha = P.alpha;
+            ga.slab = b.gmem ? d_slab + slab_cur : nullptr;
+            ga.slab_bytes = b.slab_bytes;
+            on = prof_begin(variant == SSP_SP ? SSP_PHASE_PGRAM_SP : SSP_PHASE_PGRAM_SS, s, mk);
+            if ((e = pgram_launch(prec, (int)variant, b.gmem, b.grid, b.G, b.smem, ga, s))) break;
+            prof_end(on, mk, s);
+            item_base += b.items.size();
+            slab_cur += b.gmem ? b.slab_bytes * (size_t)b.grid : 0;
+        }
+        if (e) break;
+        ArgmaxArgs aa{};
+        aa.power = out_power;
+        aa.freq = freq;
+        aa.n_freq = n_freq;
+        aa.bad = d_bad;
+        aa.best_period = out_best;
+        on = prof_begin(SSP_PHASE_ARGMAX, s, mk);
+        if ((e = argmax_launch(prec, aa, (int)n_obj, s))) break;
+        prof_end(on, mk, s);
+    } while (0);
+    if (e) status = cuda_fail(e, "enqueue");
+    cudaError_t ef = cudaFreeAsync(base, s);
+    if (status == SSP_OK && ef != cudaSuccess) status = cuda_fail(ef, "cudaFreeAsync");
+    return status;
+}
+
+std::once_flag g_pool_once;
+
+}  // namespace
+
+extern "C" {
+
+void ssp_default_params(ssp_params *p)
+{
+    if (!p) return;
+    p->spans[0] = 0.05;
+    p->spans[1] = 0.2;
+    p->spans[2] = 0.5;
+    p->alpha = 9.0;
+    p->periodic = 1;
+    p->precision = SSP_FP32C;
+    p->hbm_fraction = 0.75;
+}
+
+const char *ssp_status_string(int status)
+{
+    switch (status) {
+    case SSP_OK: return "ok";
+    case SSP_ERR_ARG: return "invalid argument";
+    case SSP_ERR_NOMEM: return "device memory budget exceeded";
+    case SSP_ERR_CUDA: return "CUDA error";
+    case SSP_ERR_TIMEOUT: return "bounded wait expired";
+    case SSP_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+    }
+}
+
+const char *ssp_last_error(void) { return g_err.c_str(); }
+
+const char *ssp_version(void) { return "ssp 0.1 sm_103a"; }
+
+void ssp_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+}
+
+int ssp_profile_read(ssp_phase_time out[SSP_N_PHASES], int reset)
+{
+    g_err.clear();
+    if (!out) return fail(SSP_ERR_ARG, "NULL output");
+    for (int k = 0; k < SSP_N_PHASES; ++k) out[k] = ssp_phase_time{0, 0.0};
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int status = SSP_OK;
+    for (Mark &m : g_marks) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(m.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, m.a, m.b);
+        if (e != cudaSuccess) {
+            status = cuda_fail(e, "profile event");
+            continue;
+        }
+        out[m.phase].launches += 1;
+        out[m.phase].ms += ms;
+    }
+    if (reset) {
+        for (Mark &m : g_marks) {
+            cudaEventDestroy(m.a);
+            cudaEventDestroy(m.b);
+        }
+        g_marks.clear();
+    }
+    return status;
+}
+
+int ssp_periodogram_device(const double *t, const double *y, const double *dy,
+                           const int64_t *n_per_object, int64_t n_objects,
+                           const double *freq_grid, int64_t n_freq, ssp_variant variant,
+                           const ssp_params *params, void *out_power, double *out_best_period,
+                           void *stream)
+{
+    g_err.clear();
+    ssp_params P;
+    ssp_default_params(&P);
+    if (params) P = *params;
+    int rc = check_params(&P);
+    if (rc) return rc;
+    rc = check_shape(n_per_object, n_objects, n_freq, variant);
+    if (rc) return rc;
+    if (!t || !y || !dy || !freq_grid || !out_power || !out_best_period)
+        return fail(SSP_ERR_ARG, "NULL array argument");
+    std::call_once(g_pool_once, keep_pool_memory);
+    return run_device(t, y, dy, n_per_object, n_objects, freq_grid, n_freq, variant, P, out_power,
+                      out_best_period, (cudaStream_t)stream);
+}
+
+int ssp_periodogram(const double *t, const double *y, const double *dy,
+                    const int64_t *n_per_object, int64_t n_objects, const double *freq_grid,
+                    int64_t n_freq, ssp_variant variant, const ssp_params *params,
+                    void *out_power, double *out_best_period)
+{
+    g_err.clear();
+    ssp_params P;
+    ssp_default_params(&P);
+    if (params) P = *params;
+    int rc = check_params(&P);
+    if (rc) return rc;
+    rc = check_shape(n_per_object, n_objects, n_freq, variant);
+    if (rc) return rc;
+    if (!t || !y || !dy || !freq_grid || !out_power || !out_best_period)
+        return fail(SSP_ERR_ARG, "NULL array argument");
+    int64_t N = 0;
+    for (int64_t o = 0; o < n_objects; ++o) N += n_per_object[o];
+    for (int64_t i = 0; i < N; ++i) {
+        if (!std::isfinite(t[i]) || !std::isfinite(y[i]))
+            return fail(SSP_ERR_ARG, "t or y at point %lld is not finite", (long long)i);
+        if (!std::isfinite(dy[i]) || !(dy[i] > 0.0))
+            return fail(SSP_ERR_ARG, "dy at point %lld must be finite and > 0", (long long)i);
+        const double w = 1.0 / (dy[i] * dy[i]);
+        if (!(w > 0.0) || !std::isfinite(w))
+            return fail(SSP_ERR_ARG, "dy at point %lld gives a weight outside binary64", (long long)i);
+        if (P.precision == SSP_FP32C && !(w >= 1.1754943508222875e-38 && w <= 3.4028234663852886e38))
+            return fail(SSP_ERR_UNSUPPORTED,
+                        "dy at point %lld gives a weight outside float range; use SSP_FP64",
+                        (long long)i);
+    }
+    for (int64_t q = 0; q < n_freq; ++q)
+        if (!std::isfinite(freq_grid[q]) || !(freq_grid[q] > 0.0))
+            return fail(SSP_ERR_ARG, "freq_grid[%lld] must be finite and > 0", (long long)q);
+    std::call_once(g_pool_once, keep_pool_memory);
+
+    cudaStream_t s;
+    SSP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    const size_t rs = P.precision == SSP_FP64 ? 8 : 4;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaStreamDestroy(s);
+        return cuda_fail(cudaGetLastError(), "cudaMemGetInfo");
+    }
+    const double budget = P.hbm_fraction * (double)free_b;
+    // batch objects so that inputs, outputs and working storage fit the budget
+    int status = SSP_OK;
+    double *d_freq = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&d_freq, 8 * (size_t)n_freq, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_freq, freq_grid, 8 * (size_t)n_freq, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) status = cuda_fail(e, "frequency grid");
+    int64_t o0 = 0, p0 = 0;
+    while (status == SSP_OK && o0 < n_objects) {
+        // grow the batch while its estimate fits
+        int64_t o1 = o0, pts = 0;
+        double need = 0.0;
+        while (o1 < n_objects) {
+            const double add = (double)n_per_object[o1] * (24.0 + 8.0 + 2.0 * rs) +
+                               (double)n_freq * rs + 64.0;
+            if (o1 > o0 && need + add > budget - kSlabReserve) break;
+            need += add;
+            pts += n_per_object[o1];
+            ++o1;
+        }
+        const int64_t nb = o1 - o0;
+        unsigned char *blk = nullptr;
+        const size_t in_b = 8 * (size_t)pts, pw_b = rs * (size_t)nb * (size_t)n_freq;
+        e = cudaMallocAsync((void **)&blk, 3 * align16(in_b) + align16(pw_b) + align16(8 * nb), s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            status = fail(SSP_ERR_NOMEM, "batch of %lld objects does not fit", (long long)nb);
+            break;
+        }
+        double *d_t = (double *)blk, *d_y = (double *)(blk + align16(in_b)),
+               *d_dy = (double *)(blk + 2 * align16(in_b));
+        void *d_pw = blk + 3 * align16(in_b);
+        double *d_best = (double *)(blk + 3 * align16(in_b) + align16(pw_b));
+        do {
+            if ((e = cudaMemcpyAsync(d_t, t + p0, in_b, cudaMemcpyHostToDevice, s))) break;
+            if ((e = cudaMemcpyAsync(d_y, y + p0, in_b, cudaMemcpyHostToDevice, s))) break;
+            if ((e = cudaMemcpyAsync(d_dy, dy + p0, in_b, cudaMemcpyHostToDevice, s))) break;
+        } while (0);
+        if (e) {
+            status = cuda_fail(e, "input copy");
+        } else {
+            status = run_device(d_t, d_y, d_dy, n_per_object + o0, nb, d_freq, n_freq, variant, P,
+                                d_pw, d_best, s);
+            if (status == SSP_OK) {
+                e = cudaMemcpyAsync((unsigned char *)out_power + rs * (size_t)o0 * (size_t)n_freq,
+                                    d_pw, pw_b, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(out_best_period + o0, d_best, 8 * (size_t)nb,
+                                        cudaMemcpyDeviceToHost, s);
+                if (e != cudaSuccess) status = cuda_fail(e, "output copy");
+            }
+        }
+        cudaFreeAsync(blk, s);
+        o0 = o1;
+        p0 += pts;
+    }
+    if (d_freq) cudaFreeAsync(d_freq, s);
+    e = cudaStreamSynchronize(s);
+    if (status == SSP_OK && e != cudaSuccess) status = cuda_fail(e, "synchronize");
+    cudaStreamDestroy(s);
+    return status;
+}
+
+}  // extern "C"

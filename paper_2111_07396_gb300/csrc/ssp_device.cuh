@@ -1,0 +1,916 @@
+// ssp_device.cuh -- device code of the Super Smoother periodogram (arXiv
+// 2111.07396) for sm_103a.
+//
+// One CTA processes one (object, trial frequency) at a time, looping over
+// work items (object, frequency range) taken from a global counter.  For
+// each frequency everything stays in the CTA's frame (shared memory, or a
+// per-CTA global slab for objects too large for shared memory):
+//
+//   fold    phase = frac(tt*f) (Alg. 1, computePhasedTime).  FP64 path: the
+//           rounded binary64 product, bit-identical to the paper's formula.
+//           FP32C path: the exact 128-bit product of fixed-point time and
+//           frequency, top 32 fraction bits.
+//   sort    stable argsort by phase (Alg. 1, argsort + mapArgsort): one
+//           counting pass into ~n buckets by the top phase bits, then each
+//           element ranks itself inside its bucket; CTA-wide bitonic sort if
+//           a bucket is crowded.
+//   smooth  running lines (the `smoothkernel` of Listing 1; Friedman 1984):
+//           the n centres are split into one contiguous chunk per thread;
+//           each thread builds its first window from per-chunk aggregates
+//           plus the ragged ends, then slides the window through its chunk
+//           with add/remove updates of sums taken about a local origin.
+//           SS = Listing 1 as four sweeps (three spans with CV, smoothed
+//           residuals with span choice and bass, smoothed spans with the
+//           interpolation, final tweeter pass with chi2); SP = one sweep with
+//           three windows and the generalized-validation span choice.
+//   reduce  chi2 per frequency, power = 1 - chi2/chi0 (computePgram).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ssp {
+
+enum { VAR_SS = 0, VAR_SP = 1 };
+constexpr int kMaxThreads = 512;
+constexpr int kBucketRankMax = 64;   // larger buckets switch to the bitonic sort
+
+struct PgramArgs {
+    const int64_t *off;     // [n_obj + 1] CSR offsets
+    const double *tt;       // [N] t - min t (FP64 path)
+    const uint64_t *tfix;   // [N] fixed-point tt (FP32C path)
+    const int *texp;        // [n_obj] tt < 2^texp
+    const void *yc;         // [N] centred magnitudes, R
+    const void *wv;         // [N] weights dy^-2, R
+    const double *chi0;     // [n_obj]
+    const int *bad;         // [n_obj] nonzero: invalid input, NaN output
+    const double *freq;     // [n_freq]
+    int64_t n_freq;
+    const int4 *items;      // (object, q0, q1, -)
+    int n_items;
+    int *item_counter;      // work-queue head, zero before launch
+    void *power;            // [n_obj][n_freq] R
+    double spans[3];
+    double alpha;
+    unsigned char *slab;    // per-CTA frames when they do not fit shared memory
+    size_t slab_bytes;
+};
+
+// ---------------------------------------------------------------------------
+// frame layout (per CTA, sized for the largest n of a launch)
+// ---------------------------------------------------------------------------
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+__host__ __device__ inline int bucket_count(int n)
+{
+    int nb = 32;
+    while (nb < n) nb <<= 1;
+    return nb;
+}
+
+template <typename R>
+struct Frame {
+    R *X, *WT, *Y;          // sorted phase, weight, centred magnitude
+    R *C[7];                // smoother columns
+    uint32_t *key, *slot, *tmp, *perm, *cnt;  // sort scratch (aliases C)
+    double *ph;             // FP64 phase by original index (aliases C)
+};
+
+template <typename R>
+__host__ __device__ inline size_t frame_bytes(int n)
+{
+    size_t cols = align16(sizeof(R) * (size_t)n) * 10;
+    size_t s = align16(sizeof(R) * (size_t)n) * 3;
+    size_t nb = (size_t)bucket_count(n);
+    s += align16(4 * (size_t)n) * 3 + align16(4 * nb) * 2;
+    if (sizeof(R) == 8) s += align16(8 * (size_t)n);
+    return cols > s ? cols : s;
+}
+
+template <typename R>
+__device__ inline Frame<R> carve_frame(unsigned char *base, int n)
+{
+    Frame<R> f;
+    size_t col = align16(sizeof(R) * (size_t)n);
+    f.X = (R *)base;
+    f.WT = (R *)(base + col);
+    f.Y = (R *)(base + 2 * col);
+    for (int k = 0; k < 7; ++k) f.C[k] = (R *)(base + (3 + k) * col);
+    unsigned char *s = base + 3 * col;
+    size_t a4 = align16(4 * (size_t)n), nb4 = align16(4 * (size_t)bucket_count(n));
+    f.key = (uint32_t *)s;
+    f.slot = (uint32_t *)(s + a4);
+    f.tmp = (uint32_t *)(s + 2 * a4);
+    f.perm = (uint32_t *)(s + 3 * a4);
+    f.cnt = (uint32_t *)(s + 3 * a4 + nb4);
+    f.ph = (double *)(s + 3 * a4 + 2 * nb4);
+    return f;
+}
+
+// per-thread chunk table and block-reduction scratch (always shared memory)
+template <typename R>
+struct Small {
+    int *cs;                // [G + 1] chunk starts
+    R *org, *aW, *aA, *aB;  // [G] chunk origin and x-moments
+    R *aC, *aD;             // [3][G] channel moments
+    double *red;            // [32] reduction scratch
+    int *ired;              // [32]
+    int *flags;             // [4]
+};
+
+template <typename R>
+__host__ __device__ inline size_t small_bytes(int G)
+{
+    return align16(4 * (size_t)(G + 1)) + align16(sizeof(R) * (size_t)G) * 4 +
+           align16(sizeof(R) * 3 * (size_t)G) * 2 + 32 * 8 + 32 * 4 + 16;
+}
+
+template <typename R>
+__device__ inline Small<R> carve_small(unsigned char *base, int G)
+{
+    Small<R> s;
+    size_t g = align16(sizeof(R) * (size_t)G), g3 = align16(sizeof(R) * 3 * (size_t)G);
+    s.cs = (int *)base;
+    base += align16(4 * (size_t)(G + 1));
+    s.org = (R *)base;
+    s.aW = (R *)(base + g);
+    s.aA = (R *)(base + 2 * g);
+    s.aB = (R *)(base + 3 * g);
+    base += 4 * g;
+    s.aC = (R *)base;
+    s.aD = (R *)(base + g3);
+    base += 2 * g3;
+    s.red = (double *)base;
+    s.ired = (int *)(base + 256);
+    s.flags = (int *)(base + 256 + 128);
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// block helpers
+// ---------------------------------------------------------------------------
+__device__ inline double block_sum(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < nw; ++k) t += red[k];
+        red[0] = t;
+    }
+    __syncthreads();
+    t = red[0];
+    __syncthreads();
+    return t;
+}
+
+// exclusive scan of cnt[0..nb) in place; returns the largest count
+__device__ inline int block_exclusive_scan(uint32_t *cnt, int nb, int *ired)
+{
+    const int G = blockDim.x, tid = threadIdx.x;
+    const int per = (nb + G - 1) / G;
+    const int a = min(nb, tid * per), b = min(nb, a + per);
+    uint32_t sum = 0, mx = 0;
+    for (int i = a; i < b; ++i) {
+        uint32_t c = cnt[i];
+        sum += c;
+        mx = c > mx ? c : mx;
+    }
+    // inclusive warp scan of per-thread sums
+    const int lane = tid & 31, warp = tid >> 5, nw = (G + 31) >> 5;
+    uint32_t inc = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __syncthreads();
+    if (lane == 31) ired[warp] = (int)inc;
+    if (lane == 0) ired[16 + warp] = (int)mx;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (int k = 0; k < warp; ++k) wbase += (uint32_t)ired[k];
+    int gmax = 0;
+    for (int k = 0; k < nw; ++k) gmax = max(gmax, ired[16 + k]);
+    uint32_t run = wbase + inc - sum;
+    for (int i = a; i < b; ++i) {
+        uint32_t c = cnt[i];
+        cnt[i] = run;
+        run += c;
+    }
+    __syncthreads();
+    return gmax;
+}
+
+// ---------------------------------------------------------------------------
+// fold (Alg. 1 computePhasedTime)
+// ---------------------------------------------------------------------------
+// FP64: the binary64 product rounded once, then its fraction (exact).
+__device__ inline double fold_fp64(double tt, double f)
+{
+    double p = __dmul_rn(tt, f);
+    return __dsub_rn(p, floor(p));
+}
+
+// FP32C: T = tt * 2^(63-E) (u64), F = f * 2^(63-Ef) exactly; the 128-bit
+// product has its binary point at bit 126-E-Ef, so the top 32 fraction bits
+// start at bit s = 94-E-Ef (0 <= s is checked on the host).
+__device__ inline uint32_t fold_fixed(uint64_t T, uint64_t F, int s)
+{
+    uint64_t lo = T * F, hi = __umul64hi(T, F);
+    if (s >= 128) return 0u;
+    if (s >= 64) return (uint32_t)(hi >> (s - 64));
+    if (s == 0) return (uint32_t)lo;
+    return (uint32_t)((hi << (64 - s)) | (lo >> s));
+}
+
+// ---------------------------------------------------------------------------
+// stable argsort of the folded phases: perm[j] = index of the j-th smallest
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ inline bool key_less(const Frame<R> &fr, uint32_t i, uint32_t j)
+{
+    uint32_t ki = fr.key[i], kj = fr.key[j];
+    if (ki != kj) return ki < kj;
+    if (sizeof(R) == 8) {
+        double a = fr.ph[i], b = fr.ph[j];
+        if (a != b) return a < b;
+    }
+    return i < j;
+}
+
+template <typename R>
+__device__ void bitonic_argsort(const Frame<R> &fr, int n, int nb)
+{
+    const int tid = threadIdx.x, G = blockDim.x;
+    for (int p = tid; p < nb; p += G) fr.perm[p] = (p < n) ? (uint32_t)p : 0xffffffffu;
+    __syncthreads();
+    for (int k = 2; k <= nb; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int p = tid; p < nb; p += G) {
+                int q = p ^ jj;
+                if (q > p) {
+                    uint32_t a = fr.perm[p], b = fr.perm[q];
+                    bool up = ((p & k) == 0);
+                    // padding (0xffffffff) sorts last
+                    bool a_gt_b = (a == 0xffffffffu) ? (b != 0xffffffffu)
+                                : (b == 0xffffffffu) ? false : key_less(fr, b, a);
+                    if (a_gt_b == up) {
+                        fr.perm[p] = b;
+                        fr.perm[q] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <typename R>
+__device__ void argsort_phases(const Frame<R> &fr, int n, const Small<R> &sm)
+{
+    const int tid = threadIdx.x, G = blockDim.x;
+    const int nb = bucket_count(n);
+    const int lb = 31 - __clz(nb);
+    const int shift = 32 - lb;
+    for (int b = tid; b < nb; b += G) fr.cnt[b] = 0u;
+    __syncthreads();
+    for (int i = tid; i < n; i += G) fr.slot[i] = atomicAdd(&fr.cnt[fr.key[i] >> shift], 1u);
+    __syncthreads();
+    const int crowd = block_exclusive_scan(fr.cnt, nb, sm.ired);
+    if (crowd > kBucketRankMax) {
+        bitonic_argsort(fr, n, nb);
+        return;
+    }
+    for (int i = tid; i < n; i += G) fr.tmp[fr.cnt[fr.key[i] >> shift] + fr.slot[i]] = (uint32_t)i;
+    __syncthreads();
+    for (int p = tid; p < n; p += G) {
+        uint32_t i = fr.tmp[p];
+        uint32_t b = fr.key[i] >> shift;
+        int lo = (int)fr.cnt[b];
+        int hi = (b + 1 < (uint32_t)nb) ? (int)fr.cnt[b + 1] : n;
+        int rank = 0;
+        for (int q = lo; q < hi; ++q) rank += key_less(fr, fr.tmp[q], i) ? 1 : 0;
+        fr.perm[lo + rank] = i;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// running-line machinery
+// ---------------------------------------------------------------------------
+// Neighbours per side (Friedman 1984): trunc(0.5*span*n + 0.5), >= 2, and at
+// most (n-1)/2 so that no window holds a point twice.  Rounded exactly as the
+// binary64 expression reads (no contraction).
+__device__ inline int half_width(int n, double span)
+{
+    int ibw = (int)__dadd_rn(__dmul_rn(__dmul_rn(0.5, span), (double)n), 0.5);
+    if (ibw < 2) ibw = 2;
+    if (2 * ibw + 1 > n) ibw = (n - 1) / 2;
+    return ibw;
+}
+
+// sums of a window about origin o: W = sum w, A = sum w dx, B = sum w dx^2,
+// C[c] = sum w v_c, D[c] = sum w dx v_c, dx = x - o
+template <typename R, int NCH>
+struct Win {
+    R W, A, B, C[NCH], D[NCH];
+    __device__ inline void zero()
+    {
+        W = A = B = R(0);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) C[c] = D[c] = R(0);
+    }
+};
+
+// window slot e (may lie one period before 0 or after n-1) -> point, shift
+__device__ inline int slot_point(int e, int n, int &sh)
+{
+    if (e < 0) { sh = -1; return e + n; }
+    if (e >= n) { sh = 1; return e - n; }
+    sh = 0;
+    return e;
+}
+
+template <typename R, int NCH>
+__device__ inline void win_add(Win<R, NCH> &s, const Frame<R> &fr, const R *const *v, int e,
+                               int n, R o, R sign)
+{
+    int sh;
+    int p = slot_point(e, n, sh);
+    R dx = (fr.X[p] - o) + (R)sh;
+    R w = sign * fr.WT[p];
+    R wdx = w * dx;
+    s.W += w;
+    s.A += wdx;
+    s.B += wdx * dx;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        R vc = v[c][p];
+        s.C[c] += w * vc;
+        s.D[c] += wdx * vc;
+    }
+}
+
+// last chunk u with cs[u] <= p (cs non-decreasing, cs[0] = 0 <= p < cs[G] = n)
+__device__ inline int find_chunk(const int *cs, int G, int p)
+{
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (cs[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Sums of the window [c - h, c + h] about origin o, from whole-chunk
+// aggregates where a chunk lies inside the window and single points at the
+// ragged ends.
+template <typename R, int NCH>
+__device__ void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R> &sm,
+                         const R *const *v, int c, int h, int n, R o)
+{
+    const int G = blockDim.x;
+    s.zero();
+    int e = c - h;
+    const int e_end = c + h;
+    int sh;
+    int p = slot_point(e, n, sh);
+    int u = find_chunk(sm.cs, G, p);
+    while (e <= e_end) {
+        p = slot_point(e, n, sh);
+        if (p < sm.cs[u]) u = 0;                 // wrapped past n-1
+        while (sm.cs[u + 1] <= p) ++u;           // skips empty chunks
+        const int len = sm.cs[u + 1] - sm.cs[u];
+        if (p == sm.cs[u] && e + len - 1 <= e_end) {
+            const R d = (sm.org[u] - o) + (R)sh;
+            const R aW = sm.aW[u], aA = sm.aA[u];
+            s.W += aW;
+            s.A += aA + d * aW;
+            s.B += sm.aB[u] + d * (R(2) * aA + d * aW);
+#pragma unroll
+            for (int ch = 0; ch < NCH; ++ch) {
+                const R cC = sm.aC[ch * G + u];
+                s.C[ch] += cC;
+                s.D[ch] += sm.aD[ch * G + u] + d * cC;
+            }
+            e += len;
+        } else {
+            win_add<R, NCH>(s, fr, v, e, n, o, R(1));
+            e += 1;
+        }
+    }
+}
+
+// per-thread chunk aggregates of the channels (about the chunk origin)
+template <typename R, int NCH>
+__device__ void channel_aggregates(const Frame<R> &fr, const Small<R> &sm, const R *const *v)
+{
+    const int tid = threadIdx.x, G = blockDim.x;
+    const int c0 = sm.cs[tid], c1 = sm.cs[tid + 1];
+    const R o = sm.org[tid];
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+        R sc = R(0), sd = R(0);
+        for (int j = c0; j < c1; ++j) {
+            R wv = fr.WT[j] * v[ch][j];
+            sc += wv;
+            sd += wv * (fr.X[j] - o);
+        }
+        sm.aC[ch * G + tid] = sc;
+        sm.aD[ch * G + tid] = sd;
+    }
+}
+
+// the line fit of a window evaluated at the centre j
+template <typename R, int NCH>
+struct Fit {
+    R rW, rS, dxj;   // 1/W, 1/Sxx (0 when the slope is dropped), x_j - xbar
+    bool slope;
+    R s[NCH];
+};
+
+template <typename R, int NCH>
+__device__ inline void win_fit(Fit<R, NCH> &f, const Win<R, NCH> &s, R xj_minus_o, R vsmlsq)
+{
+    f.rW = R(1) / s.W;
+    const R xb = s.A * f.rW;
+    const R sxx = s.B - xb * s.A;
+    f.slope = sxx > vsmlsq;
+    f.rS = f.slope ? R(1) / sxx : R(0);
+    f.dxj = xj_minus_o - xb;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        const R sxv = s.D[c] - xb * s.C[c];
+        f.s[c] = s.C[c] * f.rW + (sxv * f.rS) * f.dxj;
+    }
+}
+
+// FP32C guard: when the centred spread is a tiny remainder of the raw moment
+// (more than 12 bits cancelled), refit this centre's window directly in FP64.
+template <typename R, int NCH>
+__device__ void win_refit_fp64(Fit<R, NCH> &f, const Frame<R> &fr, const R *const *v, int j,
+                               int h, int n, double vsmlsq)
+{
+    double sw = 0.0, swx = 0.0, swv[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) swv[c] = 0.0;
+    for (int e = j - h; e <= j + h; ++e) {
+        int sh;
+        int p = slot_point(e, n, sh);
+        double w = (double)fr.WT[p], x = (double)fr.X[p] + sh;
+        sw += w;
+        swx += w * x;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) swv[c] += w * (double)v[c][p];
+    }
+    const double xm = swx / sw;
+    double sxx = 0.0, sxv[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) sxv[c] = 0.0;
+    for (int e = j - h; e <= j + h; ++e) {
+        int sh;
+        int p = slot_point(e, n, sh);
+        double w = (double)fr.WT[p], dx = (double)fr.X[p] + sh - xm;
+        sxx += w * dx * dx;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) sxv[c] += w * dx * (double)v[c][p];
+    }
+    const bool slope = sxx > vsmlsq;
+    const double dxj = (double)fr.X[j] - xm;
+    f.rW = (R)(1.0 / sw);
+    f.slope = slope;
+    f.rS = slope ? (R)(1.0 / sxx) : R(0);
+    f.dxj = (R)dxj;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c)
+        f.s[c] = (R)(swv[c] / sw + (slope ? sxv[c] / sxx : 0.0) * dxj);
+}
+
+template <typename R, int NCH>
+__device__ inline void win_fit_checked(Fit<R, NCH> &f, const Win<R, NCH> &s, const Frame<R> &fr,
+                                       const R *const *v, int j, int h, int n, R o, R vsmlsq)
+{
+    win_fit<R, NCH>(f, s, fr.X[j] - o, vsmlsq);
+    if (sizeof(R) == 4) {
+        const R sxx = s.B - (s.A / s.W) * s.A;
+        if (sxx < s.B * R(1.0 / 4096.0) && s.B > R(0))
+            win_refit_fp64<R, NCH>(f, fr, v, j, h, n, (double)vsmlsq);
+    }
+}
+
+// slide a window from centre j to j + 1
+template <typename R, int NCH>
+__device__ inline void win_slide(Win<R, NCH> &s, const Frame<R> &fr, const R *const *v, int j,
+                                 int h, int n, R o)
+{
+    win_add<R, NCH>(s, fr, v, j - h, n, o, R(-1));
+    win_add<R, NCH>(s, fr, v, j + h + 1, n, o, R(1));
+}
+
+// ---------------------------------------------------------------------------
+// Listing 1 pieces shared by SS and SP
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ inline R choose_span(const double *spans, R r0, R r1, R r2, R res_woof, double alpha,
+                                R fallback)
+{
+    R resmin = R(1.0e20), s = fallback;
+    if (r0 < resmin) { resmin = r0; s = (R)spans[0]; }
+    if (r1 < resmin) { resmin = r1; s = (R)spans[1]; }
+    if (r2 < resmin) { resmin = r2; s = (R)spans[2]; }
+    if (alpha > 0.0 && alpha <= 10.0 && resmin < res_woof && resmin > R(0)) {
+        R tmp = resmin / res_woof;
+        if (tmp < R(1.0e-7)) tmp = R(1.0e-7);
+        const R ex = (R)(10.0 - alpha);
+        const R pw = (ex == R(1)) ? tmp : pow(tmp, ex);
+        s += ((R)spans[2] - s) * pw;
+    }
+    return s;
+}
+
+template <typename R>
+__device__ inline R interpolate_span(const double *spans, R s, R tw, R mid, R woof)
+{
+    const R s0 = (R)spans[0], s1 = (R)spans[1], s2 = (R)spans[2];
+    if (s <= s0) s = s0;
+    if (s >= s2) s = s2;
+    R f = s - s1;
+    if (f < R(0)) {
+        f /= s0 - s1;
+        return (R(1) - f) * mid + f * tw;
+    }
+    f /= s2 - s1;
+    return (R(1) - f) * mid + f * woof;
+}
+
+// Kahan-compensated running sum (FP32C chi2)
+template <typename R>
+struct KSum {
+    R s = R(0), c = R(0);
+    __device__ inline void add(R v)
+    {
+        if (sizeof(R) == 8) { s += v; return; }
+        R y = v - c;
+        R t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ inline double value() const { return (double)s - (double)c; }
+};
+
+// Run bookkeeping for the averaging step of every running line: centres with
+// equal abscissae get the weighted mean of their values.  Chunks never split
+// a run, so a thread sees each run whole.
+template <typename R, int K>
+struct RunAvg {
+    int start;
+    R w, s[K];
+    __device__ inline void reset(int j)
+    {
+        start = j;
+        w = R(0);
+#pragma unroll
+        for (int k = 0; k < K; ++k) s[k] = R(0);
+    }
+};
+
+template <typename R, int K, typename Emit>
+__device__ inline void run_push(RunAvg<R, K> &ra, const Frame<R> &fr, int j, int n, bool ties,
+                                const R (&vals)[K], Emit &&emit)
+{
+    if (!ties) {
+        emit(j, vals);
+        return;
+    }
+    const R wj = fr.WT[j];
+    ra.w += wj;
+#pragma unroll
+    for (int k = 0; k < K; ++k) ra.s[k] += wj * vals[k];
+    if (j + 1 < n && fr.X[j + 1] == fr.X[j]) return;   // run continues
+    if (ra.start == j) {
+        emit(j, vals);
+    } else {
+        R avg[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) avg[k] = ra.s[k] / ra.w;
+        for (int i = ra.start; i <= j; ++i) emit(i, avg);
+    }
+    ra.reset(j + 1);
+}
+
+// ---------------------------------------------------------------------------
+// one (object, frequency): returns chi2 (block-uniform)
+// ---------------------------------------------------------------------------
+template <typename R, int VARIANT>
+__device__ double process_frequency(const PgramArgs &a, int obj, int n, double f, const Frame<R> &fr,
+                                    const Small<R> &sm)
+{
+    const int tid = threadIdx.x, G = blockDim.x;
+    const int64_t base = a.off[obj];
+    const R *yc = (const R *)a.yc + base;
+    const R *wv = (const R *)a.wv + base;
+
+    // ---- fold ----
+    if (sizeof(R) == 8) {
+        const double *tt = a.tt + base;
+        for (int i = tid; i < n; i += G) {
+            double ph = fold_fp64(tt[i], f);
+            fr.ph[i] = ph;
+            fr.key[i] = __double2uint_rz(ph * 4294967296.0);
+        }
+    } else {
+        int ef;
+        frexp(f, &ef);
+        const uint64_t F = (uint64_t)ldexp(f, 63 - ef);
+        const int s = 94 - a.texp[obj] - ef;
+        const uint64_t *tf = a.tfix + base;
+        for (int i = tid; i < n; i += G) fr.key[i] = fold_fixed(tf[i], F, s);
+    }
+    __syncthreads();
+
+    // ---- sort ----
+    argsort_phases<R>(fr, n, sm);
+
+    // ---- gather ----
+    for (int j = tid; j < n; j += G) {
+        const uint32_t i = fr.perm[j];
+        R x;
+        if (sizeof(R) == 8) x = (R)fr.ph[i];
+        else x = (R)(__uint2float_rz(fr.key[i]) * 2.3283064365386963e-10f);
+        fr.X[j] = x;
+        fr.WT[j] = wv[i];
+        fr.Y[j] = yc[i];
+    }
+    __syncthreads();
+    int tie = 0;
+    for (int j = tid; j + 1 < n; j += G) tie |= (fr.X[j + 1] == fr.X[j]);
+    const bool ties = __syncthreads_or(tie) != 0;
+
+    // ---- degenerate abscissae: weighted mean (Listing 1) ----
+    if (!(fr.X[n - 1] > fr.X[0])) {
+        double sw = 0.0, swy = 0.0;
+        for (int j = tid; j < n; j += G) {
+            sw += (double)fr.WT[j];
+            swy += (double)fr.WT[j] * (double)fr.Y[j];
+        }
+        sw = block_sum(sw, sm.red);
+        swy = block_sum(swy, sm.red);
+        const R m = (R)(sw > 0.0 ? swy / sw : 0.0);
+        double c2 = 0.0;
+        for (int j = tid; j < n; j += G) {
+            const double d = (double)(fr.Y[j] - m);
+            c2 += (double)fr.WT[j] * d * d;
+        }
+        return block_sum(c2, sm.red);
+    }
+
+    const int qi = n / 4 - 1, qj = 3 * (qi + 1) - 1;
+    const R scale = fr.X[qj] - fr.X[qi];
+    const R vsmlsq = (R)1.0e-6 * scale * scale;
+    const int h0 = half_width(n, a.spans[0]);
+    const int h1 = half_width(n, a.spans[1]);
+    const int h2 = half_width(n, a.spans[2]);
+
+    // ---- chunks: contiguous centre ranges that never split a run of ties ----
+    {
+        int c = (int)(((long long)tid * n) / G);
+        if (ties)
+            while (c > 0 && c < n && fr.X[c] == fr.X[c - 1]) ++c;
+        sm.cs[tid] = c;
+        if (tid == 0) sm.cs[G] = n;
+    }
+    __syncthreads();
+    const int c0 = sm.cs[tid], c1 = sm.cs[tid + 1];
+    const R o = (c0 < c1) ? fr.X[c0] : R(0);
+    {
+        R w_ = R(0), a_ = R(0), b_ = R(0);
+        for (int j = c0; j < c1; ++j) {
+            const R w = fr.WT[j], d = fr.X[j] - o;
+            w_ += w;
+            a_ += w * d;
+            b_ += w * d * d;
+        }
+        sm.org[tid] = o;
+        sm.aW[tid] = w_;
+        sm.aA[tid] = a_;
+        sm.aB[tid] = b_;
+    }
+
+    KSum<R> chi2;
+
+    if (VARIANT == VAR_SP) {
+        // one sweep, three windows on y, generalized validation (Sec. 3)
+        const R *vy[1] = {fr.Y};
+        channel_aggregates<R, 1>(fr, sm, vy);
+        __syncthreads();
+        if (c0 < c1) {
+            Win<R, 1> w0, w1, w2;
+            win_init<R, 1>(w0, fr, sm, vy, c0, h0, n, o);
+            win_init<R, 1>(w1, fr, sm, vy, c0, h1, n, o);
+            win_init<R, 1>(w2, fr, sm, vy, c0, h2, n, o);
+            const R m0 = (R)(2 * h0 + 1), m1 = (R)(2 * h1 + 1), m2 = (R)(2 * h2 + 1);
+            RunAvg<R, 1> ra;
+            ra.reset(c0);
+            auto emit = [&](int i, const R (&v)[1]) {
+                const R d = fr.Y[i] - v[0];
+                chi2.add(fr.WT[i] * d * d);
+            };
+            for (int j = c0; j < c1; ++j) {
+                Fit<R, 1> f0, f1, f2;
+                win_fit_checked<R, 1>(f0, w0, fr, vy, j, h0, n, o, vsmlsq);
+                win_fit_checked<R, 1>(f1, w1, fr, vy, j, h1, n, o, vsmlsq);
+                win_fit_checked<R, 1>(f2, w2, fr, vy, j, h2, n, o, vsmlsq);
+                const R yj = fr.Y[j];
+                const R g0 = fabs(yj - f0.s[0]) / (R(1) - (f0.slope ? R(2) : R(1)) / m0);
+                const R g1 = fabs(yj - f1.s[0]) / (R(1) - (f1.slope ? R(2) : R(1)) / m1);
+                const R g2 = fabs(yj - f2.s[0]) / (R(1) - (f2.slope ? R(2) : R(1)) / m2);
+                const R sp = choose_span<R>(a.spans, g0, g1, g2, g2, a.alpha, (R)a.spans[2]);
+                const R val[1] = {interpolate_span<R>(a.spans, sp, f0.s[0], f1.s[0], f2.s[0])};
+                run_push<R, 1>(ra, fr, j, n, ties, val, emit);
+                if (j + 1 < c1) {
+                    win_slide<R, 1>(w0, fr, vy, j, h0, n, o);
+                    win_slide<R, 1>(w1, fr, vy, j, h1, n, o);
+                    win_slide<R, 1>(w2, fr, vy, j, h2, n, o);
+                }
+            }
+        }
+        return block_sum(chi2.value(), sm.red);
+    }
+
+    // ===== SS, Listing 1 =====
+    // pass A: the three spans on y with cross-validation.  C0/C2/C4 = smooths
+    // (tweeter/midrange/woofer), C1/C3/C5 = CV residuals (-1 marks a centre
+    // whose leverage reached 1; resolved below).
+    {
+        const R *vy[1] = {fr.Y};
+        channel_aggregates<R, 1>(fr, sm, vy);
+        __syncthreads();
+        if (c0 < c1) {
+            Win<R, 1> w0, w1, w2;
+            win_init<R, 1>(w0, fr, sm, vy, c0, h0, n, o);
+            win_init<R, 1>(w1, fr, sm, vy, c0, h1, n, o);
+            win_init<R, 1>(w2, fr, sm, vy, c0, h2, n, o);
+            RunAvg<R, 3> ra;
+            ra.reset(c0);
+            auto emit = [&](int i, const R (&v)[3]) {
+                fr.C[0][i] = v[0];
+                fr.C[2][i] = v[1];
+                fr.C[4][i] = v[2];
+            };
+            for (int j = c0; j < c1; ++j) {
+                Fit<R, 1> f0, f1, f2;
+                win_fit_checked<R, 1>(f0, w0, fr, vy, j, h0, n, o, vsmlsq);
+                win_fit_checked<R, 1>(f1, w1, fr, vy, j, h1, n, o, vsmlsq);
+                win_fit_checked<R, 1>(f2, w2, fr, vy, j, h2, n, o, vsmlsq);
+                const R yj = fr.Y[j], wj = fr.WT[j];
+                const R d0 = R(1) - wj * (f0.rW + f0.dxj * f0.dxj * f0.rS);
+                const R d1 = R(1) - wj * (f1.rW + f1.dxj * f1.dxj * f1.rS);
+                const R d2 = R(1) - wj * (f2.rW + f2.dxj * f2.dxj * f2.rS);
+                fr.C[1][j] = d0 > R(0) ? fabs(yj - f0.s[0]) / d0 : R(-1);
+                fr.C[3][j] = d1 > R(0) ? fabs(yj - f1.s[0]) / d1 : R(-1);
+                fr.C[5][j] = d2 > R(0) ? fabs(yj - f2.s[0]) / d2 : R(-1);
+                const R val[3] = {f0.s[0], f1.s[0], f2.s[0]};
+                run_push<R, 3>(ra, fr, j, n, ties, val, emit);
+                if (j + 1 < c1) {
+                    win_slide<R, 1>(w0, fr, vy, j, h0, n, o);
+                    win_slide<R, 1>(w1, fr, vy, j, h1, n, o);
+                    win_slide<R, 1>(w2, fr, vy, j, h2, n, o);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // a residual whose leverage reached 1 repeats the previous centre's (0 at
+    // the first centre); reading neighbours while they are being resolved is
+    // safe because a resolved value equals what the walk would find
+    for (int j = c0; j < c1; ++j) {
+#pragma unroll
+        for (int k = 1; k < 6; k += 2) {
+            if (fr.C[k][j] < R(0)) {
+                int q = j - 1;
+                while (q >= 0 && fr.C[k][q] < R(0)) --q;
+                fr.C[k][j] = (q >= 0) ? fr.C[k][q] : R(0);
+            }
+        }
+    }
+    __syncthreads();
+
+    // pass B: midrange smooth of the three residual columns, span choice with
+    // bass enhancement -> C6
+    {
+        const R *vr[3] = {fr.C[1], fr.C[3], fr.C[5]};
+        channel_aggregates<R, 3>(fr, sm, vr);
+        __syncthreads();
+        if (c0 < c1) {
+            Win<R, 3> w1;
+            win_init<R, 3>(w1, fr, sm, vr, c0, h1, n, o);
+            RunAvg<R, 3> ra;
+            ra.reset(c0);
+            auto emit = [&](int i, const R (&v)[3]) {
+                // when no residual is below 1e20 the span column keeps the
+                // woofer's CV residual, as Listing 1's column 6 does
+                fr.C[6][i] = choose_span<R>(a.spans, v[0], v[1], v[2], v[2], a.alpha, fr.C[5][i]);
+            };
+            for (int j = c0; j < c1; ++j) {
+                Fit<R, 3> f1;
+                win_fit_checked<R, 3>(f1, w1, fr, vr, j, h1, n, o, vsmlsq);
+                const R val[3] = {f1.s[0], f1.s[1], f1.s[2]};
+                run_push<R, 3>(ra, fr, j, n, ties, val, emit);
+                if (j + 1 < c1) win_slide<R, 3>(w1, fr, vr, j, h1, n, o);
+            }
+        }
+    }
+    __syncthreads();
+
+    // pass C: midrange smooth of the chosen spans, clamp and interpolate -> C1
+    {
+        const R *vs[1] = {fr.C[6]};
+        channel_aggregates<R, 1>(fr, sm, vs);
+        __syncthreads();
+        if (c0 < c1) {
+            Win<R, 1> w1;
+            win_init<R, 1>(w1, fr, sm, vs, c0, h1, n, o);
+            RunAvg<R, 1> ra;
+            ra.reset(c0);
+            auto emit = [&](int i, const R (&v)[1]) {
+                fr.C[1][i] = interpolate_span<R>(a.spans, v[0], fr.C[0][i], fr.C[2][i], fr.C[4][i]);
+            };
+            for (int j = c0; j < c1; ++j) {
+                Fit<R, 1> f1;
+                win_fit_checked<R, 1>(f1, w1, fr, vs, j, h1, n, o, vsmlsq);
+                const R val[1] = {f1.s[0]};
+                run_push<R, 1>(ra, fr, j, n, ties, val, emit);
+                if (j + 1 < c1) win_slide<R, 1>(w1, fr, vs, j, h1, n, o);
+            }
+        }
+    }
+    __syncthreads();
+
+    // pass D: final tweeter smooth and chi2
+    {
+        const R *vv[1] = {fr.C[1]};
+        channel_aggregates<R, 1>(fr, sm, vv);
+        __syncthreads();
+        if (c0 < c1) {
+            Win<R, 1> w0;
+            win_init<R, 1>(w0, fr, sm, vv, c0, h0, n, o);
+            RunAvg<R, 1> ra;
+            ra.reset(c0);
+            auto emit = [&](int i, const R (&v)[1]) {
+                const R d = fr.Y[i] - v[0];
+                chi2.add(fr.WT[i] * d * d);
+            };
+            for (int j = c0; j < c1; ++j) {
+                Fit<R, 1> f0;
+                win_fit_checked<R, 1>(f0, w0, fr, vv, j, h0, n, o, vsmlsq);
+                const R val[1] = {f0.s[0]};
+                run_push<R, 1>(ra, fr, j, n, ties, val, emit);
+                if (j + 1 < c1) win_slide<R, 1>(w0, fr, vv, j, h0, n, o);
+            }
+        }
+    }
+    return block_sum(chi2.value(), sm.red);
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+template <typename R, int VARIANT, bool GMEM>
+__global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item;
+    const int G = blockDim.x;
+    Small<R> sm = carve_small<R>(smem, G);
+    unsigned char *big = GMEM ? a.slab + (size_t)blockIdx.x * a.slab_bytes
+                              : smem + align16(small_bytes<R>(G));
+    R *power = (R *)a.power;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(a.item_counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= a.n_items) break;
+        const int4 item = a.items[it];
+        const int o = item.x;
+        const int n = (int)(a.off[o + 1] - a.off[o]);
+        const Frame<R> fr = carve_frame<R>(big, n);
+        const bool bad = a.bad[o] != 0;
+        for (int q = item.y; q < item.z; ++q) {
+            double pw;
+            if (bad) {
+                pw = __longlong_as_double(0x7ff8000000000000LL);
+            } else {
+                const double c2 = process_frequency<R, VARIANT>(a, o, n, a.freq[q], fr, sm);
+                const double c0 = a.chi0[o];
+                pw = (c0 > 0.0) ? 1.0 - c2 / c0 : 0.0;
+            }
+            if (threadIdx.x == 0) power[(int64_t)o * a.n_freq + q] = (R)pw;
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace ssp

@@ -1,0 +1,180 @@
+// ssp_kernels.cuh -- per-object preparation and per-object argmax kernels,
+// and the launch wrappers instantiated once per precision (ssp_fp32.cu,
+// ssp_fp64.cu define SSP_R and SSP_PREC before including this file).
+#pragma once
+#include <cfloat>
+#include <cmath>
+
+#include "ssp_launch.h"
+
+namespace ssp {
+
+__device__ inline double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Alg. 1 compute_chi0_tt_weights, one CTA per object: tt = t - min t,
+// w = dy^-2, ybar = sum w y / sum w, chi0 = sum w (y - ybar)^2; the smoother's
+// inputs are stored in R (magnitudes centred on ybar, which leaves chi2
+// unchanged because every running line reproduces constants), and for the
+// FP32C fold tt becomes the fixed-point integer tt * 2^(63-E), tt < 2^E.
+template <typename R>
+__global__ void __launch_bounds__(256) prep_kernel(PrepArgs a)
+{
+    __shared__ double s_red[4][8];
+    __shared__ int s_bad[8];
+    const int o = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t base = a.off[o];
+    const int n = (int)(a.off[o + 1] - base);
+    double tmin = INFINITY, tmax = -INFINITY, sw = 0.0, swy = 0.0;
+    int bad = 0;
+    for (int i = tid; i < n; i += blockDim.x) {
+        const double t = a.t[base + i], y = a.y[base + i], dy = a.dy[base + i];
+        if (!isfinite(t) || !isfinite(y) || !isfinite(dy) || !(dy > 0.0)) bad = 1;
+        const double w = __ddiv_rn(1.0, __dmul_rn(dy, dy));
+        if (!(w > 0.0) || !isfinite(w)) bad = 1;
+        if (sizeof(R) == 4 && !(w >= (double)FLT_MIN && w <= (double)FLT_MAX)) bad = 1;
+        tmin = fmin(tmin, t);
+        tmax = fmax(tmax, t);
+        sw += w;
+        swy += w * y;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, off));
+        tmax = fmax(tmax, __shfl_xor_sync(0xffffffffu, tmax, off));
+    }
+    sw = warp_sum(sw);
+    swy = warp_sum(swy);
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        s_red[0][warp] = tmin;
+        s_red[1][warp] = tmax;
+        s_red[2][warp] = sw;
+        s_red[3][warp] = swy;
+        s_bad[warp] = bad;
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    tmin = s_red[0][0];
+    tmax = s_red[1][0];
+    sw = 0.0;
+    swy = 0.0;
+    bad = 0;
+    for (int k = 0; k < nw; ++k) {
+        tmin = fmin(tmin, s_red[0][k]);
+        tmax = fmax(tmax, s_red[1][k]);
+        sw += s_red[2][k];
+        swy += s_red[3][k];
+        bad |= s_bad[k];
+    }
+    __syncthreads();
+    const double ybar = swy / sw;
+    const double span = tmax - tmin;
+    int E = 0;
+    if (span > 0.0) frexp(span, &E);
+    double c0 = 0.0;
+    R *yc = (R *)a.yc + base;
+    R *wv = (R *)a.wv + base;
+    for (int i = tid; i < n; i += blockDim.x) {
+        const double t = a.t[base + i], y = a.y[base + i], dy = a.dy[base + i];
+        const double w = __ddiv_rn(1.0, __dmul_rn(dy, dy));
+        const double tt = __dsub_rn(t, tmin);
+        const double d = y - ybar;
+        c0 += w * d * d;
+        if (sizeof(R) == 8) a.tt[base + i] = tt;
+        else a.tfix[base + i] = __double2ull_rn(ldexp(tt, 63 - E));
+        yc[i] = (R)d;
+        wv[i] = (R)w;
+    }
+    c0 = warp_sum(c0);
+    if (lane == 0) s_red[0][warp] = c0;
+    __syncthreads();
+    if (tid == 0) {
+        double c = 0.0;
+        for (int k = 0; k < nw; ++k) c += s_red[0][k];
+        a.chi0[o] = c;
+        a.texp[o] = E;
+        a.bad[o] = bad;
+    }
+}
+
+// findPeriod (Alg. 1): first index of the largest power, period = 1/f.
+template <typename R>
+__global__ void __launch_bounds__(256) argmax_kernel(ArgmaxArgs a)
+{
+    __shared__ double s_v[8];
+    __shared__ long long s_i[8];
+    const int o = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const R *row = (const R *)a.power + (int64_t)o * a.n_freq;
+    double bv = -INFINITY;
+    long long bi = -1;
+    for (int64_t q = tid; q < a.n_freq; q += blockDim.x) {
+        const double v = (double)row[q];
+        if (v > bv) { bv = v; bi = q; }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+        const long long oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { s_v[warp] = bv; s_i[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            const double ov = s_v[k];
+            const long long oi = s_i[k];
+            if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) { bv = ov; bi = oi; }
+        }
+        a.best_period[o] = (a.bad[o] || bi < 0) ? __longlong_as_double(0x7ff8000000000000LL)
+                                                : 1.0 / a.freq[bi];
+    }
+}
+
+}  // namespace ssp
+
+#define SSP_INSTANTIATE(R, PREC)                                                              \
+    namespace ssp {                                                                           \
+    cudaError_t prep_launch_##PREC(const PrepArgs &a, int n_obj, cudaStream_t s)              \
+    {                                                                                         \
+        prep_kernel<R><<<n_obj, 256, 0, s>>>(a);                                              \
+        return cudaGetLastError();                                                            \
+    }                                                                                         \
+    cudaError_t argmax_launch_##PREC(const ArgmaxArgs &a, int n_obj, cudaStream_t s)          \
+    {                                                                                         \
+        argmax_kernel<R><<<n_obj, 256, 0, s>>>(a);                                            \
+        return cudaGetLastError();                                                            \
+    }                                                                                         \
+    template <int V, bool GM>                                                                 \
+    static cudaError_t occ_##PREC(int G, size_t smem, int *bps)                               \
+    {                                                                                         \
+        cudaError_t e = cudaFuncSetAttribute(pgram_kernel<R, V, GM>,                          \
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                             (int)smem);                                      \
+        if (e != cudaSuccess) return e;                                                       \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, pgram_kernel<R, V, GM>, G,  \
+                                                             smem);                           \
+    }                                                                                         \
+    cudaError_t pgram_occupancy_##PREC(int variant, bool gmem, int G, size_t smem, int *bps)  \
+    {                                                                                         \
+        if (variant == VAR_SS) return gmem ? occ_##PREC<VAR_SS, true>(G, smem, bps)           \
+                                           : occ_##PREC<VAR_SS, false>(G, smem, bps);         \
+        return gmem ? occ_##PREC<VAR_SP, true>(G, smem, bps)                                  \
+                    : occ_##PREC<VAR_SP, false>(G, smem, bps);                                \
+    }                                                                                         \
+    cudaError_t pgram_launch_##PREC(int variant, bool gmem, int grid, int G, size_t smem,     \
+                                    const PgramArgs &a, cudaStream_t s)                       \
+    {                                                                                         \
+        if (variant == VAR_SS) {                                                              \
+            if (gmem) pgram_kernel<R, VAR_SS, true><<<grid, G, smem, s>>>(a);                 \
+            else pgram_kernel<R, VAR_SS, false><<<grid, G, smem, s>>>(a);                     \
+        } else {                                                                              \
+            if (gmem) pgram_kernel<R, VAR_SP, true><<<grid, G, smem, s>>>(a);                 \
+            else pgram_kernel<R, VAR_SP, false><<<grid, G, smem, s>>>(a);                     \
+        }                                                                                     \
+        return cudaGetLastError();                                                            \
+    }                                                                                         \
+    size_t pgram_small_bytes_##PREC(int G) { return small_bytes<R>(G); }                      \
+    size_t pgram_frame_bytes_##PREC(int n) { return frame_bytes<R>(n); }                      \
+    }

@@ -1,0 +1,43 @@
+// ssp_launch.h -- host-side launch wrappers shared by the kernel translation
+// units (one per precision) and the C ABI in ssp_api.cu.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ssp_device.cuh"
+
+namespace ssp {
+
+struct PrepArgs {
+    const double *t, *y, *dy;  // [N] caller's device arrays
+    const int64_t *off;        // [n_obj + 1]
+    double *tt;                // [N] FP64 path
+    uint64_t *tfix;            // [N] FP32C path
+    int *texp;                 // [n_obj]
+    void *yc, *wv;             // [N] R
+    double *chi0;              // [n_obj]
+    int *bad;                  // [n_obj]
+};
+
+struct ArgmaxArgs {
+    const void *power;         // [n_obj][n_freq] R
+    const double *freq;
+    int64_t n_freq;
+    const int *bad;
+    double *best_period;       // [n_obj]
+};
+
+// precision: 0 = FP64, 1 = FP32C
+cudaError_t prep_launch(int precision, const PrepArgs &a, int n_obj, cudaStream_t s);
+cudaError_t argmax_launch(int precision, const ArgmaxArgs &a, int n_obj, cudaStream_t s);
+// sets the dynamic shared-memory limit and returns resident CTAs per SM
+cudaError_t pgram_occupancy(int precision, int variant, bool gmem, int G, size_t smem,
+                            int *blocks_per_sm);
+cudaError_t pgram_launch(int precision, int variant, bool gmem, int grid, int G, size_t smem,
+                         const PgramArgs &a, cudaStream_t s);
+
+size_t pgram_small_bytes(int precision, int G);
+size_t pgram_frame_bytes(int precision, int n);
+
+}  // namespace ssp

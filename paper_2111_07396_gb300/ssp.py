@@ -1,0 +1,199 @@
+"""ctypes binding of libssp (``include/ssp.h``): argument marshalling only.
+
+The function names are the C ABI's.  Every step of the periodogram runs in
+the library's CUDA kernels; nothing here computes.  ``lib()`` raises if the
+shared library has not been built (``paper_2111_07396_gb300.build.build()``):
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SO = os.path.join(HERE, "libssp.so")
+
+SSP_SS, SSP_SP = 0, 1
+SSP_FP64, SSP_FP32C = 0, 1
+SSP_OK, SSP_ERR_ARG, SSP_ERR_NOMEM, SSP_ERR_CUDA, SSP_ERR_TIMEOUT, SSP_ERR_UNSUPPORTED = (
+    0, -1, -2, -3, -4, -5)
+VARIANTS = {"ss": SSP_SS, "sp": SSP_SP, SSP_SS: SSP_SS, SSP_SP: SSP_SP}
+PRECISIONS = {"fp64": SSP_FP64, "fp32c": SSP_FP32C, SSP_FP64: SSP_FP64, SSP_FP32C: SSP_FP32C}
+
+
+class ssp_params(ctypes.Structure):
+    _fields_ = [("spans", ctypes.c_double * 3), ("alpha", ctypes.c_double),
+                ("periodic", ctypes.c_int), ("precision", ctypes.c_int),
+                ("hbm_fraction", ctypes.c_double)]
+
+
+class ssp_phase_time(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
+PHASES = ("prep", "pgram_ss", "pgram_sp", "argmax")
+
+
+class SSPError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libssp.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(SO):
+            raise RuntimeError(f"libssp.so is not built ({SO}); run "
+                               "paper_2111_07396_gb300.build.build() first")
+        L = ctypes.CDLL(SO)
+        P, i64 = ctypes.c_void_p, ctypes.c_int64
+        L.ssp_default_params.argtypes = [ctypes.POINTER(ssp_params)]
+        L.ssp_default_params.restype = None
+        L.ssp_periodogram.argtypes = [P, P, P, P, i64, P, i64, ctypes.c_int,
+                                      ctypes.POINTER(ssp_params), P, P]
+        L.ssp_periodogram.restype = ctypes.c_int
+        L.ssp_periodogram_device.argtypes = [P, P, P, P, i64, P, i64, ctypes.c_int,
+                                             ctypes.POINTER(ssp_params), P, P, P]
+        L.ssp_periodogram_device.restype = ctypes.c_int
+        L.ssp_status_string.argtypes = [ctypes.c_int]
+        L.ssp_status_string.restype = ctypes.c_char_p
+        L.ssp_last_error.argtypes = []
+        L.ssp_last_error.restype = ctypes.c_char_p
+        L.ssp_version.argtypes = []
+        L.ssp_version.restype = ctypes.c_char_p
+        L.ssp_profile_enable.argtypes = [ctypes.c_int]
+        L.ssp_profile_enable.restype = None
+        L.ssp_profile_read.argtypes = [ctypes.POINTER(ssp_phase_time), ctypes.c_int]
+        L.ssp_profile_read.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def ssp_default_params(precision="fp32c", alpha=None, spans=None, hbm_fraction=None) -> ssp_params:
+    p = ssp_params()
+    lib().ssp_default_params(ctypes.byref(p))
+    p.precision = PRECISIONS[precision]
+    if alpha is not None:
+        p.alpha = float(alpha)
+    if spans is not None:
+        for k in range(3):
+            p.spans[k] = float(spans[k])
+    if hbm_fraction is not None:
+        p.hbm_fraction = float(hbm_fraction)
+    return p
+
+
+def ssp_status_string(status: int) -> str:
+    return lib().ssp_status_string(int(status)).decode()
+
+
+def ssp_last_error() -> str:
+    return lib().ssp_last_error().decode()
+
+
+def ssp_version() -> str:
+    return lib().ssp_version().decode()
+
+
+def ssp_profile_enable(on: bool = True) -> None:
+    lib().ssp_profile_enable(1 if on else 0)
+
+
+def ssp_profile_read(reset: bool = True) -> dict:
+    out = (ssp_phase_time * len(PHASES))()
+    _check(lib().ssp_profile_read(out, 1 if reset else 0))
+    return {name: (int(out[k].launches), float(out[k].ms)) for k, name in enumerate(PHASES)}
+
+
+def _check(rc: int):
+    if rc != SSP_OK:
+        raise SSPError(rc, f"{ssp_status_string(rc)}: {ssp_last_error()}")
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def ssp_periodogram(t, y, dy, n_per_object, freq_grid, variant="ss", precision="fp32c",
+                    alpha=9.0, spans=None, params=None, out_power=None, out_best_period=None):
+    """Host-memory entry point.  Arrays may be numpy arrays or CPU torch
+    tensors (pinned or not); returns (power [n_objects, n_freq], best_period)."""
+    p = params if params is not None else ssp_default_params(precision, alpha, spans)
+    t_, y_, dy_ = (_host_array(a) for a in (t, y, dy))
+    npo = np.ascontiguousarray(n_per_object, dtype=np.int64)
+    fq = _host_array(freq_grid)
+    n_obj, n_freq = int(npo.size), _numel(fq)
+    dt = np.float64 if p.precision == SSP_FP64 else np.float32
+    if out_power is None:
+        out_power = np.empty((n_obj, n_freq), dtype=dt)
+    if out_best_period is None:
+        out_best_period = np.empty(n_obj, dtype=np.float64)
+    rc = lib().ssp_periodogram(_host_ptr(t_), _host_ptr(y_), _host_ptr(dy_), _ptr(npo), n_obj,
+                               _host_ptr(fq), n_freq, VARIANTS[variant], ctypes.byref(p),
+                               _host_ptr(out_power), _host_ptr(out_best_period))
+    _check(rc)
+    return out_power, out_best_period
+
+
+def ssp_periodogram_device(t, y, dy, n_per_object, freq_grid, out_power, out_best_period,
+                           variant="ss", precision="fp32c", alpha=9.0, spans=None, params=None,
+                           stream=None):
+    """Device-memory entry point.  t, y, dy, freq_grid, out_power and
+    out_best_period are CUDA torch tensors (or raw device addresses as ints);
+    n_per_object is a host array.  Enqueued on `stream` (a torch stream or a
+    raw cudaStream_t address; default: torch's current stream)."""
+    p = params if params is not None else ssp_default_params(precision, alpha, spans)
+    npo = np.ascontiguousarray(n_per_object, dtype=np.int64)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    s = stream if isinstance(stream, int) else stream.cuda_stream
+    n_freq = int(freq_grid.numel()) if hasattr(freq_grid, "numel") else None
+    if n_freq is None:
+        raise ValueError("freq_grid must be a tensor (its length is needed)")
+    rc = lib().ssp_periodogram_device(_dev_ptr(t), _dev_ptr(y), _dev_ptr(dy), _ptr(npo),
+                                      int(npo.size), _dev_ptr(freq_grid), n_freq,
+                                      VARIANTS[variant], ctypes.byref(p), _dev_ptr(out_power),
+                                      _dev_ptr(out_best_period), ctypes.c_void_p(s))
+    _check(rc)
+    return out_power, out_best_period
+
+
+def _numel(a):
+    return int(a.numel()) if hasattr(a, "numel") else int(a.size)
+
+
+def _host_array(a):
+    if hasattr(a, "data_ptr"):  # torch CPU tensor
+        import torch
+        if a.is_cuda:
+            raise ValueError("ssp_periodogram takes host arrays; use ssp_periodogram_device")
+        if a.dtype != torch.float64:
+            raise ValueError("host tensors must be float64")
+        return a.contiguous()
+    return _f64(a)
+
+
+def _host_ptr(a):
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return _ptr(a)
+
+
+def _dev_ptr(a):
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    if not a.is_cuda or not a.is_contiguous():
+        raise ValueError("device entry point needs contiguous CUDA tensors")
+    return ctypes.c_void_p(a.data_ptr())

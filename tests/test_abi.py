@@ -1,0 +1,95 @@
+"""The C ABI library loads without a GPU, exports every function that
+include/ssp.h declares, and rejects invalid arguments before touching CUDA."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2111_07396_gb300 import build as ssp_build
+from paper_2111_07396_gb300 import ssp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    ssp_build.build()
+
+
+def _declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(inc, fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(ssp_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported():
+    names = _declared_functions()
+    assert {"ssp_periodogram", "ssp_periodogram_device", "ssp_default_params"} <= names
+    lib = ctypes.CDLL(ssp.SO)
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_defaults_and_strings():
+    p = ssp.ssp_default_params()
+    assert list(p.spans) == [0.05, 0.2, 0.5]
+    assert p.alpha == 9.0 and p.periodic == 1 and p.precision == ssp.SSP_FP32C
+    assert p.hbm_fraction == 0.75
+    assert ssp.ssp_status_string(ssp.SSP_ERR_ARG) == "invalid argument"
+    assert ssp.ssp_version().startswith("ssp ")
+    assert ctypes.sizeof(ssp.ssp_params) == 48
+
+
+def _call(**kw):
+    args = dict(t=np.arange(8.0), y=np.ones(8), dy=np.ones(8), n_per_object=[8],
+                freq_grid=[0.3, 0.4])
+    args.update(kw)
+    return ssp.ssp_periodogram(**args)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(n_per_object=[3], t=np.arange(3.0), y=np.ones(3), dy=np.ones(3)), ssp.SSP_ERR_ARG),
+    (dict(freq_grid=[0.3, -1.0]), ssp.SSP_ERR_ARG),
+    (dict(freq_grid=[0.3, np.nan]), ssp.SSP_ERR_ARG),
+    (dict(dy=np.r_[np.ones(7), 0.0]), ssp.SSP_ERR_ARG),
+    (dict(y=np.r_[np.ones(7), np.inf]), ssp.SSP_ERR_ARG),
+    (dict(t=np.r_[np.arange(7.0), np.nan]), ssp.SSP_ERR_ARG),
+    (dict(alpha=11.0), ssp.SSP_ERR_ARG),
+    (dict(spans=(0.2, 0.1, 0.5)), ssp.SSP_ERR_ARG),
+    (dict(variant=7), ssp.SSP_ERR_ARG),
+    (dict(dy=np.r_[np.ones(7), 1e-30]), ssp.SSP_ERR_UNSUPPORTED),
+])
+def test_invalid_arguments_rejected_before_cuda(kw, status):
+    if kw.get("variant") == 7:
+        p = ssp.ssp_default_params()
+        rc = ssp.lib().ssp_periodogram(None, None, None, None, 1, None, 1, 7, ctypes.byref(p),
+                                       None, None)
+        assert rc == status
+        return
+    with pytest.raises(ssp.SSPError) as ei:
+        _call(**kw)
+    assert ei.value.status == status
+
+
+def test_periodic_zero_unsupported():
+    p = ssp.ssp_default_params()
+    p.periodic = 0
+    with pytest.raises(ssp.SSPError) as ei:
+        _call(params=p)
+    assert ei.value.status == ssp.SSP_ERR_UNSUPPORTED
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(ssp, "SO", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(ssp, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        ssp.lib()

@@ -1,0 +1,182 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.  Gates: FP64 rel <= 1e-9 on every power value, FP32C rel <= 2e-4
+(absolute 2e-6 where |power| < 1e-2), best frequency identical."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_07396_gb300 import build as ssp_build
+from paper_2111_07396_gb300 import ssp, synth
+from tests.parity import TOL, gate_error, oracle_powers, sample_freqs
+
+pytestmark = pytest.mark.gpu
+VARIANTS = [("ss", oracle.SS), ("sp", oracle.SP)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    ssp_build.build()
+    ssp.lib()
+
+
+_cache = {}
+
+
+def _oracle_full(cat, code, key):
+    k = (key, code)
+    if k not in _cache:
+        _cache[k] = oracle.periodogram(cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq, code)
+    return _cache[k]
+
+
+@pytest.mark.parametrize("variant,code", VARIANTS)
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_config1_full(variant, code, precision):
+    cat = synth.config1()
+    ref, ref_best = _oracle_full(cat, code, "c1")
+    got, best = ssp.ssp_periodogram(cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq,
+                                    variant=variant, precision=precision)
+    assert gate_error(got, ref) <= TOL[precision]
+    assert np.argmax(got[0]) == np.argmax(ref[0])
+    assert best[0] == ref_best[0]
+
+
+@pytest.mark.parametrize("variant,code", VARIANTS)
+def test_config1_small_grid_tiles(variant, code):
+    # a grid whose length is not a multiple of any work-item size
+    cat = synth.config1(n_freq=1999)
+    ref, _ = oracle.periodogram(cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq, code)
+    for precision in ("fp64", "fp32c"):
+        got, _ = ssp.ssp_periodogram(cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq,
+                                     variant=variant, precision=precision)
+        assert gate_error(got, ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("variant,code", VARIANTS)
+def test_config2_full_size_sampled(variant, code):
+    # the full 3,000-point, 100,000-frequency workload in the benchmark's
+    # launch configuration; the oracle computes sampled frequencies one by one
+    cat = synth.config2()
+    t, y, dy = cat.obj(0)
+    got = {p: ssp.ssp_periodogram(cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq,
+                                  variant=variant, precision=p) for p in ("fp32c", "fp64")}
+    q_best = int(np.argmax(got["fp64"][0][0]))
+    qs = sample_freqs(cat.freq.size, 24, seed=2, include=[q_best - 1, q_best, q_best + 1,
+                                                          int(np.argmax(got["fp32c"][0][0]))])
+    ref = oracle_powers(t, y, dy, cat.freq[qs], code)
+    for precision, (pw, best) in got.items():
+        assert gate_error(pw[0, qs], ref) <= TOL[precision], precision
+    assert got["fp64"][1][0] == 1.0 / cat.freq[q_best]
+    assert int(np.argmax(got["fp32c"][0][0])) == q_best
+
+
+@pytest.mark.parametrize("variant,code", VARIANTS)
+def test_config3_subset_batched(variant, code):
+    # 120 objects of the sparse catalog (n 30..500 spans three length buckets)
+    full = synth.config3(n_objects=120, n_freq=600)
+    ref, ref_best = oracle.periodogram(full.t, full.y, full.dy, full.n_per_object, full.freq, code)
+    for precision in ("fp64", "fp32c"):
+        got, best = ssp.ssp_periodogram(full.t, full.y, full.dy, full.n_per_object, full.freq,
+                                        variant=variant, precision=precision)
+        assert gate_error(got, ref) <= TOL[precision], precision
+        same = np.mean(np.argmax(got, axis=1) == np.argmax(ref, axis=1))
+        assert same >= (1.0 if precision == "fp64" else 0.99)
+        if precision == "fp64":
+            np.testing.assert_array_equal(best, ref_best)
+
+
+@pytest.mark.parametrize("variant,code", VARIANTS)
+def test_config4_large_objects_sampled(variant, code):
+    # two dense objects (n > 10,000: frames in global memory) on the full grid
+    cat = synth.config4(n_objects=2)
+    got = {p: ssp.ssp_periodogram(cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq,
+                                  variant=variant, precision=p)[0] for p in ("fp32c", "fp64")}
+    for o in range(2):
+        t, y, dy = cat.obj(o)
+        qb = int(np.argmax(got["fp64"][o]))
+        qs = sample_freqs(cat.freq.size, 2, seed=40 + o, include=[qb])
+        ref = oracle_powers(t, y, dy, cat.freq[qs], code)
+        for precision, pw in got.items():
+            assert gate_error(pw[o, qs], ref) <= TOL[precision], (precision, o)
+
+
+def _edge_catalog():
+    g = np.random.default_rng(99)
+    objs = []
+    # minimum size
+    objs.append((np.array([0.0, 0.31, 1.7, 2.2]), np.array([1.0, 2.0, 0.5, 1.5]),
+                 np.full(4, 0.1)))
+    # duplicated times (ties in phase at every frequency)
+    t = np.sort(g.uniform(0, 50, 40))
+    t[10:14] = t[10]
+    t[25:27] = t[25]
+    objs.append((t, np.sin(t) + g.normal(0, 0.1, 40), g.uniform(0.05, 0.2, 40)))
+    # integer-day sampling: every phase equal at integer frequencies (degenerate)
+    t = np.arange(12.0)
+    objs.append((t, g.normal(0, 1, 12), np.full(12, 0.3)))
+    # ragged sizes around the length-bucket boundaries
+    for n in (5, 31, 33, 385, 769, 1537):
+        t = np.sort(g.uniform(0, 300, n))
+        objs.append((t, np.cos(t / 1.3) + g.normal(0, 0.2, n), g.uniform(0.1, 0.3, n)))
+    # clustered phases: one-night cadence, integer-day multiples
+    t = np.sort(np.concatenate([np.arange(30) + g.uniform(0, 0.05, 30), g.uniform(0, 30, 5)]))
+    objs.append((t, g.normal(0, 1, t.size), np.full(t.size, 0.5)))
+    freq = np.concatenate([[1.0, 2.0, 0.5], synth.uniform_grid(0.05, 3.0, 97)])
+    return synth.concat([synth.single_object(*o, freq) for o in objs])
+
+
+@pytest.mark.parametrize("variant,code", VARIANTS)
+def test_edge_cases(variant, code):
+    cat = _edge_catalog()
+    ref, ref_best = oracle.periodogram(cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq, code)
+    for precision in ("fp64", "fp32c"):
+        got, best = ssp.ssp_periodogram(cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq,
+                                        variant=variant, precision=precision)
+        assert gate_error(got, ref) <= TOL[precision], precision
+        if precision == "fp64":
+            np.testing.assert_array_equal(best, ref_best)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_batch_composition_invariance(precision):
+    full = synth.config3(n_objects=40, n_freq=300)
+    mix, _ = ssp.ssp_periodogram(full.t, full.y, full.dy, full.n_per_object, full.freq,
+                                 variant="ss", precision=precision)
+    for o in (0, 7, 39):
+        one = full.subset([o])
+        alone, _ = ssp.ssp_periodogram(one.t, one.y, one.dy, one.n_per_object, one.freq,
+                                       variant="ss", precision=precision)
+        np.testing.assert_array_equal(alone[0], mix[o])
+
+
+def test_device_entry_matches_host_entry():
+    import torch
+    cat = synth.config3(n_objects=12, n_freq=257)
+    for precision, dt in (("fp64", torch.float64), ("fp32c", torch.float32)):
+        host, hbest = ssp.ssp_periodogram(cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq,
+                                          variant="sp", precision=precision)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        pw = torch.empty((cat.n_objects, cat.freq.size), dtype=dt, device="cuda")
+        bp = torch.empty(cat.n_objects, dtype=torch.float64, device="cuda")
+        ssp.ssp_periodogram_device(dev(cat.t), dev(cat.y), dev(cat.dy), cat.n_per_object,
+                                   dev(cat.freq), pw, bp, variant="sp", precision=precision)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(pw.cpu().numpy(), host)
+        np.testing.assert_array_equal(bp.cpu().numpy(), hbest)
+
+
+def test_device_entry_marks_invalid_object_nan():
+    import torch
+    cat = synth.config3(n_objects=3, n_freq=50)
+    y = cat.y.copy()
+    a = cat.offsets[1]
+    y[a + 2] = np.nan  # object 1 invalid
+    dev = lambda arr: torch.from_numpy(np.ascontiguousarray(arr)).cuda()
+    pw = torch.empty((3, 50), dtype=torch.float32, device="cuda")
+    bp = torch.empty(3, dtype=torch.float64, device="cuda")
+    ssp.ssp_periodogram_device(dev(cat.t), dev(y), dev(cat.dy), cat.n_per_object, dev(cat.freq),
+                               pw, bp, variant="ss", precision="fp32c")
+    torch.cuda.synchronize()
+    p = pw.cpu().numpy()
+    assert np.all(np.isnan(p[1])) and np.isnan(bp[1].item())
+    assert np.all(np.isfinite(p[0])) and np.all(np.isfinite(p[2]))
