@@ -113,6 +113,17 @@ int ssp_periodogram_device(const double *t, const double *y, const double *dy,
                            const ssp_params *params, void *out_power,
                            double *out_best_period, void *stream);
 
+/*
+ * The phase fold of Alg. 1 (computePhasedTime) exactly as the SSP_FP32C
+ * kernels compute it, evaluated on the host (no GPU needed):
+ *     out[i] = floor(frac(fl(tt[i] * f)) * 2^64)
+ * where fl() is the binary64 product rounded to nearest even.  The kernels
+ * obtain it with integer arithmetic (no FP64 instructions); for phases >=
+ * 2^-11 it carries the binary64 phase exactly.  tt[i] must be finite and
+ * >= 0, f finite and > 0 (else SSP_ERR_ARG).  out is caller-owned, u64 [n].
+ */
+int ssp_fold_fixed(const double *tt, int64_t n, double f, uint64_t *out);
+
 /* Static text for a status code. */
 const char *ssp_status_string(int status);
 /* Detail of the last error returned on the calling thread ("" if none). */
@@ -127,16 +138,19 @@ const char *ssp_version(void);
  * recorded on the launching stream.  ssp_profile_read waits for the recorded
  * events, fills out[k] for k = SSP_PHASE_PREP (Alg. 1 compute_chi0_tt_weights),
  * SSP_PHASE_PGRAM_SS / SSP_PHASE_PGRAM_SP (fold + sort + smoother + chi2 of
- * that variant, one launch per length bucket) and SSP_PHASE_ARGMAX
- * (findPeriod), and clears them if reset != 0.  Off by default; enabling
- * adds two event records per launch.
+ * that variant, one launch per length bucket), SSP_PHASE_REDO (SSP_FP32C
+ * only: the FP64 launch that recomputes the frequencies whose FP32 decisions
+ * came within their margins) and SSP_PHASE_ARGMAX (findPeriod), and clears
+ * them if reset != 0.  Off by default; enabling adds two event records per
+ * launch.
  */
 enum {
     SSP_PHASE_PREP = 0,
     SSP_PHASE_PGRAM_SS = 1,
     SSP_PHASE_PGRAM_SP = 2,
-    SSP_PHASE_ARGMAX = 3,
-    SSP_N_PHASES = 4
+    SSP_PHASE_REDO = 3,
+    SSP_PHASE_ARGMAX = 4,
+    SSP_N_PHASES = 5
 };
 typedef struct {
     int64_t launches; /* launches recorded */

@@ -5,12 +5,14 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
 
 #include "../../include/ssp.h"
+#include "ssp_fold.h"
 #include "ssp_launch.h"
 
 namespace ssp {
@@ -131,11 +133,15 @@ int group_size(int n)
     return 256;
 }
 
-struct Bucket {
-    int G = 32, n_max = 0;
+struct LaunchCfg {
     bool gmem = false;
     size_t smem = 0, slab_bytes = 0;
     int grid = 0;
+};
+
+struct Bucket {
+    int G = 32, n_max = 0;
+    LaunchCfg main, redo;   // redo: FP64 recompute of flagged FP32C frequencies
     std::vector<int> objects;
     std::vector<int4> items;
 };
@@ -143,6 +149,7 @@ struct Bucket {
 struct Plan {
     std::vector<Bucket> buckets;
     size_t items_total = 0, slab_total = 0;
+    bool redo = false;
 };
 
 int device_limits(int *num_sms, size_t *max_smem)
@@ -156,6 +163,23 @@ int device_limits(int *num_sms, size_t *max_smem)
     return SSP_OK;
 }
 
+// frame placement and persistent grid of one kernel for one bucket
+int configure(int precision, int variant, int G, int n_max, int sms, size_t max_smem,
+              LaunchCfg &c)
+{
+    const size_t small = align16(pgram_small_bytes(precision, G));
+    const size_t frame = align16(pgram_frame_bytes(precision, n_max));
+    c.gmem = small + frame + 1024 > max_smem;
+    c.smem = c.gmem ? small : small + frame;
+    c.slab_bytes = c.gmem ? frame : 0;
+    int bps = 0;
+    cudaError_t e = pgram_occupancy(precision, variant, c.gmem, G, c.smem, &bps);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+    if (bps < 1) return fail(SSP_ERR_NOMEM, "a CTA frame for n = %d does not fit", n_max);
+    c.grid = bps * sms;
+    return SSP_OK;
+}
+
 // Length buckets (one launch each, sized for the bucket's largest object),
 // work items (object, frequency range) ordered longest first.
 int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision, int variant,
@@ -166,6 +190,7 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
     int rc = device_limits(&sms, &max_smem);
     if (rc) return rc;
     plan.buckets.clear();
+    plan.redo = precision == SSP_FP32C;
     for (int G : {32, 64, 128, 256}) {
         Bucket b;
         b.G = G;
@@ -179,16 +204,13 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
     plan.items_total = 0;
     plan.slab_total = 0;
     for (Bucket &b : plan.buckets) {
-        const size_t small = align16(pgram_small_bytes(precision, b.G));
-        const size_t frame = align16(pgram_frame_bytes(precision, b.n_max));
-        b.gmem = small + frame + 1024 > max_smem;
-        b.smem = b.gmem ? small : small + frame;
-        b.slab_bytes = b.gmem ? frame : 0;
-        int bps = 0;
-        cudaError_t e = pgram_occupancy(precision, variant, b.gmem, b.G, b.smem, &bps);
-        if (e != cudaSuccess) return cuda_fail(e, "occupancy");
-        if (bps < 1) return fail(SSP_ERR_NOMEM, "a CTA frame for n = %d does not fit", b.n_max);
-        const int resident = bps * sms;
+        rc = configure(precision, variant, b.G, b.n_max, sms, max_smem, b.main);
+        if (rc) return rc;
+        if (plan.redo) {
+            rc = configure(SSP_FP64, variant, b.G, b.n_max, sms, max_smem, b.redo);
+            if (rc) return rc;
+        }
+        const int resident = b.main.grid;
         // enough items for dynamic balance: ~8 per resident CTA
         const int64_t want = std::max<int64_t>(8LL * resident, (int64_t)b.objects.size());
         int64_t per_obj = (want + (int64_t)b.objects.size() - 1) / (int64_t)b.objects.size();
@@ -204,26 +226,44 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
                          [](const auto &x, const auto &y) { return x.first < y.first; });
         b.items.resize(keyed.size());
         for (size_t k = 0; k < keyed.size(); ++k) b.items[k] = keyed[k].second;
-        b.grid = (int)std::min<int64_t>((int64_t)b.items.size(), resident);
+        b.main.grid = (int)std::min<int64_t>((int64_t)b.items.size(), b.main.grid);
+        b.redo.grid = (int)std::min<int64_t>((int64_t)b.items.size(), b.redo.grid);
         plan.items_total += b.items.size();
-        plan.slab_total += b.gmem ? b.slab_bytes * (size_t)b.grid : 0;
+        plan.slab_total += b.main.gmem ? b.main.slab_bytes * (size_t)b.main.grid : 0;
+        if (plan.redo && b.redo.gmem) plan.slab_total += b.redo.slab_bytes * (size_t)b.redo.grid;
     }
     return SSP_OK;
 }
 
 size_t rsize(int precision) { return precision == SSP_FP64 ? 8 : 4; }
 
+// margins below which FP32C span choices count as contested; SSP_NEAR_SS
+// and SSP_NEAR_SP override them (calibration of the FP64 recompute; a
+// negative value disables that test)
+float near_margin(const char *env, float dflt)
+{
+    const char *e = std::getenv(env);
+    if (e && *e) {
+        const double v = std::atof(e);
+        if (v < 1.0) return (float)v;
+    }
+    return dflt;
+}
+
 // device bytes of one batch apart from the caller's arrays
-size_t workspace_bytes(const Plan &plan, int64_t n_obj, int64_t n_points, int precision)
+size_t workspace_bytes(const Plan &plan, int64_t n_obj, int64_t n_points, int64_t n_freq,
+                       int precision)
 {
     size_t b = 0;
-    b += align16(8 * (size_t)(n_obj + 1));               // off
-    b += align16(8 * (size_t)n_points);                  // tt or tfix
-    b += align16(4 * (size_t)n_obj) * 2;                 // texp, bad
+    b += align16(8 * (size_t)(n_obj + 1));                  // off
+    b += align16(8 * (size_t)n_points);                     // tt
+    b += align16(4 * (size_t)n_obj);                        // bad
     b += align16(rsize(precision) * (size_t)n_points) * 2;  // yc, wv
-    b += align16(8 * (size_t)n_obj);                     // chi0
+    if (plan.redo) b += align16(8 * (size_t)n_points) * 2;  // FP64 copies
+    b += align16(8 * (size_t)n_obj);                        // chi0
     b += align16(sizeof(int4) * plan.items_total);
-    b += align16(4 * plan.buckets.size() + 4);
+    b += align16(8 * plan.buckets.size() + 8);              // two counters per bucket
+    if (plan.redo) b += align16((size_t)n_obj * (size_t)n_freq);  // near flags
     b += plan.slab_total;
     return b;
 }
@@ -282,7 +322,7 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
     std::vector<int64_t> off((size_t)n_obj + 1, 0);
     for (int64_t o = 0; o < n_obj; ++o) off[o + 1] = off[o] + npo[o];
     const int64_t N = off[n_obj];
-    const size_t ws = workspace_bytes(plan, n_obj, N, prec);
+    const size_t ws = workspace_bytes(plan, n_obj, N, n_freq, prec);
     unsigned char *base = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&base, ws, s);
     if (e != cudaSuccess) {
@@ -296,14 +336,18 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
         return p;
     };
     int64_t *d_off = (int64_t *)take(8 * (size_t)(n_obj + 1));
-    void *d_tt = take(8 * (size_t)N);
-    int *d_texp = (int *)take(4 * (size_t)n_obj);
+    double *d_tt = (double *)take(8 * (size_t)N);
     int *d_bad = (int *)take(4 * (size_t)n_obj);
     void *d_yc = take(rsize(prec) * (size_t)N);
     void *d_wv = take(rsize(prec) * (size_t)N);
+    double *d_yc64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
+    double *d_wv64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
     double *d_chi0 = (double *)take(8 * (size_t)n_obj);
     int4 *d_items = (int4 *)take(sizeof(int4) * plan.items_total);
-    int *d_counters = (int *)take(4 * plan.buckets.size() + 4);
+    const size_t n_counters = 2 * plan.buckets.size() + 2;
+    int *d_counters = (int *)take(4 * n_counters);
+    unsigned char *d_near =
+        plan.redo ? (unsigned char *)take((size_t)n_obj * (size_t)n_freq) : nullptr;
     unsigned char *d_slab = base + cur;
 
     std::vector<int4> items;
@@ -315,17 +359,18 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
         if ((e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(),
                                  cudaMemcpyHostToDevice, s)))
             break;
-        if ((e = cudaMemsetAsync(d_counters, 0, 4 * plan.buckets.size() + 4, s))) break;
+        if ((e = cudaMemsetAsync(d_counters, 0, 4 * n_counters, s))) break;
+        if (d_near && (e = cudaMemsetAsync(d_near, 0, (size_t)n_obj * (size_t)n_freq, s))) break;
         PrepArgs pa{};
         pa.t = t;
         pa.y = y;
         pa.dy = dy;
         pa.off = d_off;
-        pa.tt = (double *)d_tt;
-        pa.tfix = (uint64_t *)d_tt;
-        pa.texp = d_texp;
+        pa.tt = d_tt;
         pa.yc = d_yc;
         pa.wv = d_wv;
+        pa.yc64 = d_yc64;
+        pa.wv64 = d_wv64;
         pa.chi0 = d_chi0;
         pa.bad = d_bad;
         Mark mk;
@@ -337,28 +382,51 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
             const Bucket &b = plan.buckets[k];
             PgramArgs ga{};
             ga.off = d_off;
-            ga.tt = (const double *)d_tt;
-            ga.tfix = (const uint64_t *)d_tt;
-            ga.texp = d_texp;
+            ga.tt = d_tt;
             ga.yc = d_yc;
             ga.wv = d_wv;
             ga.chi0 = d_chi0;
+            ga.yc64 = d_yc64;
+            ga.wv64 = d_wv64;
             ga.bad = d_bad;
             ga.freq = freq;
             ga.n_freq = n_freq;
             ga.items = d_items + item_base;
             ga.n_items = (int)b.items.size();
-            ga.item_counter = d_counters + k;
+            ga.item_counter = d_counters + 2 * k;
             ga.power = out_power;
+            ga.power_f32 = prec == SSP_FP32C;
             for (int i = 0; i < 3; ++i) ga.spans[i] = P.spans[i];
             ga.alpha = P.alpha;
-            ga.slab = b.gmem ? d_slab + slab_cur : nullptr;
-            ga.slab_bytes = b.slab_bytes;
-            on = prof_begin(variant == SSP_SP ? SSP_PHASE_PGRAM_SP : SSP_PHASE_PGRAM_SS, s, mk);
-            if ((e = pgram_launch(prec, (int)variant, b.gmem, b.grid, b.G, b.smem, ga, s))) break;
+            ga.slab = b.main.gmem ? d_slab + slab_cur : nullptr;
+            ga.slab_bytes = b.main.slab_bytes;
+            ga.near = d_near;
+            ga.near_ss = near_margin("SSP_NEAR_SS", ssp::kNearSS);
+            ga.near_sp = near_margin("SSP_NEAR_SP", ssp::kNearSP);
+            ga.recompute = 0;
+            slab_cur += b.main.gmem ? b.main.slab_bytes * (size_t)b.main.grid : 0;
+            const int ph = variant == SSP_SP ? SSP_PHASE_PGRAM_SP : SSP_PHASE_PGRAM_SS;
+            on = prof_begin(ph, s, mk);
+            if ((e = pgram_launch(prec, (int)variant, b.main.gmem, b.main.grid, b.G, b.main.smem,
+                                  ga, s)))
+                break;
             prof_end(on, mk, s);
+            if (plan.redo) {
+                // the same items through the FP64 kernel, flagged frequencies only
+                ga.yc = d_yc64;
+                ga.wv = d_wv64;
+                ga.item_counter = d_counters + 2 * k + 1;
+                ga.slab = b.redo.gmem ? d_slab + slab_cur : nullptr;
+                ga.slab_bytes = b.redo.slab_bytes;
+                ga.recompute = 1;
+                slab_cur += b.redo.gmem ? b.redo.slab_bytes * (size_t)b.redo.grid : 0;
+                on = prof_begin(SSP_PHASE_REDO, s, mk);
+                if ((e = pgram_launch(SSP_FP64, (int)variant, b.redo.gmem, b.redo.grid, b.G,
+                                      b.redo.smem, ga, s)))
+                    break;
+                prof_end(on, mk, s);
+            }
             item_base += b.items.size();
-            slab_cur += b.gmem ? b.slab_bytes * (size_t)b.grid : 0;
         }
         if (e) break;
         ArgmaxArgs aa{};
@@ -411,6 +479,19 @@ const char *ssp_status_string(int status)
 const char *ssp_last_error(void) { return g_err.c_str(); }
 
 const char *ssp_version(void) { return "ssp 0.1 sm_103a"; }
+
+int ssp_fold_fixed(const double *tt, int64_t n, double f, uint64_t *out)
+{
+    g_err.clear();
+    if (n < 0 || (n > 0 && (!tt || !out))) return fail(SSP_ERR_ARG, "bad array arguments");
+    if (!std::isfinite(f) || !(f > 0.0)) return fail(SSP_ERR_ARG, "f must be finite and > 0");
+    for (int64_t i = 0; i < n; ++i) {
+        if (!std::isfinite(tt[i]) || tt[i] < 0.0)
+            return fail(SSP_ERR_ARG, "tt[%lld] must be finite and >= 0", (long long)i);
+        out[i] = ssp::fold_fixed64(tt[i], f);
+    }
+    return SSP_OK;
+}
 
 void ssp_profile_enable(int on)
 {

@@ -6,12 +6,12 @@
 // each frequency everything stays in the CTA's frame (shared memory, or a
 // per-CTA global slab for objects too large for shared memory):
 //
-//   fold    phase = frac(tt*f) (Alg. 1, computePhasedTime).  FP64 path: the
-//           rounded binary64 product, bit-identical to the paper's formula.
-//           FP32C path: the exact 128-bit product of fixed-point time and
-//           frequency, top 32 fraction bits.
+//   fold    phase = frac(tt*f) (Alg. 1, computePhasedTime), bit-identical to
+//           the rounded binary64 product: the FP64 path multiplies in FP64,
+//           the FP32C path emulates the same IEEE multiply with integers
+//           (ssp_fold.h) and keeps the phase as a 64-bit fixed-point number.
 //   sort    stable argsort by phase (Alg. 1, argsort + mapArgsort): one
-//           counting pass into ~n buckets by the top phase bits, then each
+//           counting pass into ~n/2 buckets by the top phase bits, then each
 //           element ranks itself inside its bucket; CTA-wide bitonic sort if
 //           a bucket is crowded.
 //   smooth  running lines (the `smoothkernel` of Listing 1; Friedman 1984):
@@ -28,20 +28,38 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ssp_fold.h"
+
 namespace ssp {
 
 enum { VAR_SS = 0, VAR_SP = 1 };
 constexpr int kMaxThreads = 512;
 constexpr int kBucketRankMax = 64;   // larger buckets switch to the bitonic sort
 
+// FP32C decisions closer than these margins to their thresholds are re-taken
+// in FP64: the frequency is flagged and recomputed by the FP64 kernel.
+//  - SS: tweeter vs midrange smoothed residuals closer than
+//    kNearSS * min(1, 256/n) * min(1, 512/n) relative (the FP32 error of a
+//    smoothed residual, and the effect of one flipped choice on the power,
+//    both fall as the windows grow with n);
+//  - a cross-validated residual whose 1 - leverage is below kNearLev, and a
+//    window spread within kNearSlope of vsmlsq.
+// SP choices are settled in place instead: where the tweeter and midrange
+// generalized-validation residuals are closer than kNearSP * eps_fp32 times
+// the magnitude scale at that point, the warp refits those two windows in
+// binary64 from the exact phases and binary64 inputs and decides from those.
+constexpr float kNearSS = 1e-6f;
+constexpr float kNearSP = 64.f;
+constexpr float kNearLev = 1e-4f;
+constexpr float kNearSlope = 1e-4f;
+
 struct PgramArgs {
     const int64_t *off;     // [n_obj + 1] CSR offsets
-    const double *tt;       // [N] t - min t (FP64 path)
-    const uint64_t *tfix;   // [N] fixed-point tt (FP32C path)
-    const int *texp;        // [n_obj] tt < 2^texp
+    const double *tt;       // [N] t - min t (binary64, both paths)
     const void *yc;         // [N] centred magnitudes, R
     const void *wv;         // [N] weights dy^-2, R
     const double *chi0;     // [n_obj]
+    const double *yc64, *wv64;  // [N] binary64 inputs (FP32C: exact SP refits)
     const int *bad;         // [n_obj] nonzero: invalid input, NaN output
     const double *freq;     // [n_freq]
     int64_t n_freq;
@@ -53,55 +71,94 @@ struct PgramArgs {
     double alpha;
     unsigned char *slab;    // per-CTA frames when they do not fit shared memory
     size_t slab_bytes;
+    unsigned char *near;    // [n_obj][n_freq] FP32C: decision near a threshold
+    int recompute;          // FP64 kernel: only flagged (o, q), float power out
+    int power_f32;          // power array holds float
+    float near_ss;          // SS margin for n <= 256 (scaled down above)
+    float near_sp;          // SP margin in units of eps_fp32 * magnitude scale
 };
 
 // ---------------------------------------------------------------------------
 // frame layout (per CTA, sized for the largest n of a launch)
 // ---------------------------------------------------------------------------
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+// counting-sort buckets: a power of two >= n/2 (about two keys per bucket)
 __host__ __device__ inline int bucket_count(int n)
 {
     int nb = 32;
-    while (nb < n) nb <<= 1;
+    while (2 * nb < n) nb <<= 1;
     return nb;
+}
+__host__ __device__ inline int pow2_at_least(int n)
+{
+    int p = 32;
+    while (p < n) p <<= 1;
+    return p;
 }
 
 template <typename R>
 struct Frame {
     R *X, *WT, *Y;          // sorted phase, weight, centred magnitude
     R *C[7];                // smoother columns
-    uint32_t *key, *slot, *tmp, *perm, *cnt;  // sort scratch (aliases C)
-    double *ph;             // FP64 phase by original index (aliases C)
+    uint32_t *tie;          // bit j: sorted points j and j+1 have the same
+                            // folded phase (exact fold output, not rounded X)
+    uint32_t *key, *klo;    // phase as 64-bit fixed point, high / low word
+    uint16_t *slot, *tmp, *perm;  // sort scratch (n <= 65535)
+    uint32_t *cnt;          // bucket counts / starts
+    double *ph;             // FP64 phase by original index
 };
+
+__host__ __device__ inline size_t tie_words(int n) { return ((size_t)n + 31) / 32; }
+
+// Frame layout: X, WT, Y and the seven columns, each align16(sizeof(R) n);
+// the sort scratch (key, klo, slot, tmp, perm, cnt and, for FP64, the phases
+// by original index) overlays the columns from C0 on; the tie bitmask
+// follows whichever of the two ends later, because the gather writes it
+// while it still reads the sort's output.
+template <typename R>
+__host__ __device__ inline size_t sort_end(int n)
+{
+    const size_t col = align16(sizeof(R) * (size_t)n);
+    size_t s = col * 3 + align16(4 * (size_t)n) * 2 + align16(2 * (size_t)n) * 2 +
+               align16(2 * (size_t)pow2_at_least(n)) + align16(4 * (size_t)bucket_count(n));
+    if (sizeof(R) == 8) s += align16(8 * (size_t)n);
+    return s;
+}
+
+template <typename R>
+__host__ __device__ inline size_t tie_offset(int n)
+{
+    const size_t cols = align16(sizeof(R) * (size_t)n) * 10;
+    const size_t s = sort_end<R>(n);
+    return cols > s ? cols : s;
+}
 
 template <typename R>
 __host__ __device__ inline size_t frame_bytes(int n)
 {
-    size_t cols = align16(sizeof(R) * (size_t)n) * 10;
-    size_t s = align16(sizeof(R) * (size_t)n) * 3;
-    size_t nb = (size_t)bucket_count(n);
-    s += align16(4 * (size_t)n) * 3 + align16(4 * nb) * 2;
-    if (sizeof(R) == 8) s += align16(8 * (size_t)n);
-    return cols > s ? cols : s;
+    return tie_offset<R>(n) + align16(4 * tie_words(n));
 }
 
 template <typename R>
 __device__ inline Frame<R> carve_frame(unsigned char *base, int n)
 {
     Frame<R> f;
-    size_t col = align16(sizeof(R) * (size_t)n);
+    const size_t col = align16(sizeof(R) * (size_t)n);
     f.X = (R *)base;
     f.WT = (R *)(base + col);
     f.Y = (R *)(base + 2 * col);
     for (int k = 0; k < 7; ++k) f.C[k] = (R *)(base + (3 + k) * col);
+    f.tie = (uint32_t *)(base + tie_offset<R>(n));
     unsigned char *s = base + 3 * col;
-    size_t a4 = align16(4 * (size_t)n), nb4 = align16(4 * (size_t)bucket_count(n));
+    const size_t a4 = align16(4 * (size_t)n), a2 = align16(2 * (size_t)n);
+    const size_t ap = align16(2 * (size_t)pow2_at_least(n));
     f.key = (uint32_t *)s;
-    f.slot = (uint32_t *)(s + a4);
-    f.tmp = (uint32_t *)(s + 2 * a4);
-    f.perm = (uint32_t *)(s + 3 * a4);
-    f.cnt = (uint32_t *)(s + 3 * a4 + nb4);
-    f.ph = (double *)(s + 3 * a4 + 2 * nb4);
+    f.klo = (uint32_t *)(s + a4);
+    f.slot = (uint16_t *)(s + 2 * a4);
+    f.tmp = (uint16_t *)(s + 2 * a4 + a2);
+    f.perm = (uint16_t *)(s + 2 * a4 + 2 * a2);
+    f.cnt = (uint32_t *)(s + 2 * a4 + 2 * a2 + ap);
+    f.ph = (double *)(s + 2 * a4 + 2 * a2 + ap + align16(4 * (size_t)bucket_count(n)));
     return f;
 }
 
@@ -110,7 +167,7 @@ template <typename R>
 struct Small {
     int *cs;                // [G + 1] chunk starts
     R *org, *aW, *aA, *aB;  // [G] chunk origin and x-moments
-    R *aC, *aD;             // [3][G] channel moments
+    R *aC, *aD;             // [4][G] channel moments
     double *red;            // [32] reduction scratch
     int *ired;              // [32]
     int *flags;             // [4]
@@ -120,14 +177,14 @@ template <typename R>
 __host__ __device__ inline size_t small_bytes(int G)
 {
     return align16(4 * (size_t)(G + 1)) + align16(sizeof(R) * (size_t)G) * 4 +
-           align16(sizeof(R) * 3 * (size_t)G) * 2 + 32 * 8 + 32 * 4 + 16;
+           align16(sizeof(R) * 4 * (size_t)G) * 2 + 32 * 8 + 32 * 4 + 16;
 }
 
 template <typename R>
 __device__ inline Small<R> carve_small(unsigned char *base, int G)
 {
     Small<R> s;
-    size_t g = align16(sizeof(R) * (size_t)G), g3 = align16(sizeof(R) * 3 * (size_t)G);
+    size_t g = align16(sizeof(R) * (size_t)G), g3 = align16(sizeof(R) * 4 * (size_t)G);
     s.cs = (int *)base;
     base += align16(4 * (size_t)(G + 1));
     s.org = (R *)base;
@@ -213,49 +270,40 @@ __device__ inline double fold_fp64(double tt, double f)
     return __dsub_rn(p, floor(p));
 }
 
-// FP32C: T = tt * 2^(63-E) (u64), F = f * 2^(63-Ef) exactly; the 128-bit
-// product has its binary point at bit 126-E-Ef, so the top 32 fraction bits
-// start at bit s = 94-E-Ef (0 <= s is checked on the host).
-__device__ inline uint32_t fold_fixed(uint64_t T, uint64_t F, int s)
-{
-    uint64_t lo = T * F, hi = __umul64hi(T, F);
-    if (s >= 128) return 0u;
-    if (s >= 64) return (uint32_t)(hi >> (s - 64));
-    if (s == 0) return (uint32_t)lo;
-    return (uint32_t)((hi << (64 - s)) | (lo >> s));
-}
-
 // ---------------------------------------------------------------------------
 // stable argsort of the folded phases: perm[j] = index of the j-th smallest
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ inline bool key_less(const Frame<R> &fr, uint32_t i, uint32_t j)
 {
-    uint32_t ki = fr.key[i], kj = fr.key[j];
+    const uint32_t ki = fr.key[i], kj = fr.key[j];
     if (ki != kj) return ki < kj;
+    const uint32_t li = fr.klo[i], lj = fr.klo[j];
+    if (li != lj) return li < lj;
     if (sizeof(R) == 8) {
-        double a = fr.ph[i], b = fr.ph[j];
-        if (a != b) return a < b;
+        const double a = fr.ph[i], b = fr.ph[j];
+        if (a != b) return a < b;   // phases below 2^-64 apart (tiny phases only)
     }
     return i < j;
 }
 
 template <typename R>
-__device__ void bitonic_argsort(const Frame<R> &fr, int n, int nb)
+__device__ void bitonic_argsort(const Frame<R> &fr, int n)
 {
     const int tid = threadIdx.x, G = blockDim.x;
-    for (int p = tid; p < nb; p += G) fr.perm[p] = (p < n) ? (uint32_t)p : 0xffffffffu;
+    const int np2 = pow2_at_least(n);
+    for (int p = tid; p < np2; p += G) fr.perm[p] = (p < n) ? (uint16_t)p : (uint16_t)0xffff;
     __syncthreads();
-    for (int k = 2; k <= nb; k <<= 1) {
+    for (int k = 2; k <= np2; k <<= 1) {
         for (int jj = k >> 1; jj > 0; jj >>= 1) {
-            for (int p = tid; p < nb; p += G) {
-                int q = p ^ jj;
+            for (int p = tid; p < np2; p += G) {
+                const int q = p ^ jj;
                 if (q > p) {
-                    uint32_t a = fr.perm[p], b = fr.perm[q];
-                    bool up = ((p & k) == 0);
-                    // padding (0xffffffff) sorts last
-                    bool a_gt_b = (a == 0xffffffffu) ? (b != 0xffffffffu)
-                                : (b == 0xffffffffu) ? false : key_less(fr, b, a);
+                    const uint16_t a = fr.perm[p], b = fr.perm[q];
+                    const bool up = ((p & k) == 0);
+                    // padding (0xffff, never a real index since n <= 65535) sorts last
+                    const bool a_gt_b = (a == 0xffff) ? (b != 0xffff)
+                                      : (b == 0xffff) ? false : key_less(fr, b, a);
                     if (a_gt_b == up) {
                         fr.perm[p] = b;
                         fr.perm[q] = a;
@@ -272,30 +320,32 @@ __device__ void argsort_phases(const Frame<R> &fr, int n, const Small<R> &sm)
 {
     const int tid = threadIdx.x, G = blockDim.x;
     const int nb = bucket_count(n);
-    const int lb = 31 - __clz(nb);
-    const int shift = 32 - lb;
+    const int shift = 32 - (31 - __clz(nb));
     for (int b = tid; b < nb; b += G) fr.cnt[b] = 0u;
     __syncthreads();
-    for (int i = tid; i < n; i += G) fr.slot[i] = atomicAdd(&fr.cnt[fr.key[i] >> shift], 1u);
+    for (int i = tid; i < n; i += G)
+        fr.slot[i] = (uint16_t)atomicAdd(&fr.cnt[fr.key[i] >> shift], 1u);
     __syncthreads();
     const int crowd = block_exclusive_scan(fr.cnt, nb, sm.ired);
     if (crowd > kBucketRankMax) {
-        bitonic_argsort(fr, n, nb);
+        bitonic_argsort(fr, n);
         return;
     }
-    for (int i = tid; i < n; i += G) fr.tmp[fr.cnt[fr.key[i] >> shift] + fr.slot[i]] = (uint32_t)i;
+    for (int i = tid; i < n; i += G)
+        fr.tmp[fr.cnt[fr.key[i] >> shift] + fr.slot[i]] = (uint16_t)i;
     __syncthreads();
     for (int p = tid; p < n; p += G) {
-        uint32_t i = fr.tmp[p];
-        uint32_t b = fr.key[i] >> shift;
-        int lo = (int)fr.cnt[b];
-        int hi = (b + 1 < (uint32_t)nb) ? (int)fr.cnt[b + 1] : n;
+        const uint32_t i = fr.tmp[p];
+        const uint32_t b = fr.key[i] >> shift;
+        const int lo = (int)fr.cnt[b];
+        const int hi = (b + 1 < (uint32_t)nb) ? (int)fr.cnt[b + 1] : n;
         int rank = 0;
         for (int q = lo; q < hi; ++q) rank += key_less(fr, fr.tmp[q], i) ? 1 : 0;
-        fr.perm[lo + rank] = i;
+        fr.perm[lo + rank] = (uint16_t)i;
     }
     __syncthreads();
 }
+
 
 // ---------------------------------------------------------------------------
 // running-line machinery
@@ -316,9 +366,10 @@ __device__ inline int half_width(int n, double span)
 template <typename R, int NCH>
 struct Win {
     R W, A, B, C[NCH], D[NCH];
+    R hiB;   // largest B the sums have held: the scale of their rounding error
     __device__ inline void zero()
     {
-        W = A = B = R(0);
+        W = A = B = hiB = R(0);
 #pragma unroll
         for (int c = 0; c < NCH; ++c) C[c] = D[c] = R(0);
     }
@@ -333,7 +384,17 @@ __device__ inline int slot_point(int e, int n, int &sh)
     return e;
 }
 
-template <typename R, int NCH>
+// Channel c at point p.  With DIFF the last channel is not stored: it is
+// channel 0 minus channel 1, smoothed directly so that its sign is exact where
+// the two smooths round to the same value (the running line is linear).
+template <typename R, int NCH, bool DIFF>
+__device__ inline R chan(const R *const *v, int c, int p)
+{
+    if (DIFF && c == NCH - 1) return v[0][p] - v[1][p];
+    return v[c][p];
+}
+
+template <typename R, int NCH, bool DIFF = false>
 __device__ inline void win_add(Win<R, NCH> &s, const Frame<R> &fr, const R *const *v, int e,
                                int n, R o, R sign)
 {
@@ -345,9 +406,10 @@ __device__ inline void win_add(Win<R, NCH> &s, const Frame<R> &fr, const R *cons
     s.W += w;
     s.A += wdx;
     s.B += wdx * dx;
+    if (sizeof(R) == 4) s.hiB = fmax(s.hiB, s.B);
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
-        R vc = v[c][p];
+        R vc = chan<R, NCH, DIFF>(v, c, p);
         s.C[c] += w * vc;
         s.D[c] += wdx * vc;
     }
@@ -367,7 +429,7 @@ __device__ inline int find_chunk(const int *cs, int G, int p)
 // Sums of the window [c - h, c + h] about origin o, from whole-chunk
 // aggregates where a chunk lies inside the window and single points at the
 // ragged ends.
-template <typename R, int NCH>
+template <typename R, int NCH, bool DIFF = false>
 __device__ void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R> &sm,
                          const R *const *v, int c, int h, int n, R o)
 {
@@ -389,6 +451,7 @@ __device__ void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R> &sm,
             s.W += aW;
             s.A += aA + d * aW;
             s.B += sm.aB[u] + d * (R(2) * aA + d * aW);
+            if (sizeof(R) == 4) s.hiB = fmax(s.hiB, s.B);
 #pragma unroll
             for (int ch = 0; ch < NCH; ++ch) {
                 const R cC = sm.aC[ch * G + u];
@@ -397,14 +460,14 @@ __device__ void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R> &sm,
             }
             e += len;
         } else {
-            win_add<R, NCH>(s, fr, v, e, n, o, R(1));
+            win_add<R, NCH, DIFF>(s, fr, v, e, n, o, R(1));
             e += 1;
         }
     }
 }
 
 // per-thread chunk aggregates of the channels (about the chunk origin)
-template <typename R, int NCH>
+template <typename R, int NCH, bool DIFF = false>
 __device__ void channel_aggregates(const Frame<R> &fr, const Small<R> &sm, const R *const *v)
 {
     const int tid = threadIdx.x, G = blockDim.x;
@@ -414,7 +477,7 @@ __device__ void channel_aggregates(const Frame<R> &fr, const Small<R> &sm, const
     for (int ch = 0; ch < NCH; ++ch) {
         R sc = R(0), sd = R(0);
         for (int j = c0; j < c1; ++j) {
-            R wv = fr.WT[j] * v[ch][j];
+            R wv = fr.WT[j] * chan<R, NCH, DIFF>(v, ch, j);
             sc += wv;
             sd += wv * (fr.X[j] - o);
         }
@@ -447,9 +510,11 @@ __device__ inline void win_fit(Fit<R, NCH> &f, const Win<R, NCH> &s, R xj_minus_
     }
 }
 
-// FP32C guard: when the centred spread is a tiny remainder of the raw moment
-// (more than 12 bits cancelled), refit this centre's window directly in FP64.
-template <typename R, int NCH>
+// FP32C guard: the sliding sums carry absolute errors of order eps times the
+// largest moment they have held; where the centred spread is below 1/128 of
+// that (a tight cluster after wide windows, or a far origin), this centre's
+// window is refitted directly in FP64.
+template <typename R, int NCH, bool DIFF = false>
 __device__ void win_refit_fp64(Fit<R, NCH> &f, const Frame<R> &fr, const R *const *v, int j,
                                int h, int n, double vsmlsq)
 {
@@ -463,7 +528,7 @@ __device__ void win_refit_fp64(Fit<R, NCH> &f, const Frame<R> &fr, const R *cons
         sw += w;
         swx += w * x;
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) swv[c] += w * (double)v[c][p];
+        for (int c = 0; c < NCH; ++c) swv[c] += w * (double)chan<R, NCH, DIFF>(v, c, p);
     }
     const double xm = swx / sw;
     double sxx = 0.0, sxv[NCH];
@@ -475,7 +540,7 @@ __device__ void win_refit_fp64(Fit<R, NCH> &f, const Frame<R> &fr, const R *cons
         double w = (double)fr.WT[p], dx = (double)fr.X[p] + sh - xm;
         sxx += w * dx * dx;
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) sxv[c] += w * dx * (double)v[c][p];
+        for (int c = 0; c < NCH; ++c) sxv[c] += w * dx * (double)chan<R, NCH, DIFF>(v, c, p);
     }
     const bool slope = sxx > vsmlsq;
     const double dxj = (double)fr.X[j] - xm;
@@ -488,39 +553,57 @@ __device__ void win_refit_fp64(Fit<R, NCH> &f, const Frame<R> &fr, const R *cons
         f.s[c] = (R)(swv[c] / sw + (slope ? sxv[c] / sxx : 0.0) * dxj);
 }
 
-template <typename R, int NCH>
+template <typename R, int NCH, bool DIFF = false>
 __device__ inline void win_fit_checked(Fit<R, NCH> &f, const Win<R, NCH> &s, const Frame<R> &fr,
-                                       const R *const *v, int j, int h, int n, R o, R vsmlsq)
+                                       const R *const *v, int j, int h, int n, R o, R vsmlsq,
+                                       bool &near)
 {
     win_fit<R, NCH>(f, s, fr.X[j] - o, vsmlsq);
     if (sizeof(R) == 4) {
         const R sxx = s.B - (s.A / s.W) * s.A;
-        if (sxx < s.B * R(1.0 / 4096.0) && s.B > R(0))
-            win_refit_fp64<R, NCH>(f, fr, v, j, h, n, (double)vsmlsq);
+        if (sxx < s.hiB * R(1.0 / 128.0) && s.hiB > R(0))
+            win_refit_fp64<R, NCH, DIFF>(f, fr, v, j, h, n, (double)vsmlsq);
+        if (fabs(sxx - vsmlsq) <= (R)kNearSlope * vsmlsq) near = true;
     }
 }
 
 // slide a window from centre j to j + 1
-template <typename R, int NCH>
+template <typename R, int NCH, bool DIFF = false>
 __device__ inline void win_slide(Win<R, NCH> &s, const Frame<R> &fr, const R *const *v, int j,
                                  int h, int n, R o)
 {
-    win_add<R, NCH>(s, fr, v, j - h, n, o, R(-1));
-    win_add<R, NCH>(s, fr, v, j + h + 1, n, o, R(1));
+    win_add<R, NCH, DIFF>(s, fr, v, j - h, n, o, R(-1));
+    win_add<R, NCH, DIFF>(s, fr, v, j + h + 1, n, o, R(1));
 }
 
 // ---------------------------------------------------------------------------
 // Listing 1 pieces shared by SS and SP
 // ---------------------------------------------------------------------------
+// Span choice at one centre: first strict minimum of the three residuals,
+// then bass enhancement toward the woofer span.  Listing 1 enhances only when
+// the minimum is strictly below the woofer's residual; as the two approach,
+// the enhanced span tends to the woofer's, and exactly at equality it drops
+// back.  Two different windows agree exactly only by rounding, and FP32
+// rounds far more often than binary64, so for R = float an exact tie between
+// different windows (lim_k: window k differs from the woofer's) takes the
+// limit value instead.
+// d01 (when use_d01) is the directly smoothed r0 - r1: it settles tweeter
+// against midrange where r0 and r1 round to the same value.
 template <typename R>
 __device__ inline R choose_span(const double *spans, R r0, R r1, R r2, R res_woof, double alpha,
-                                R fallback)
+                                R fallback, bool lim0, bool lim1, bool use_d01 = false,
+                                R d01 = R(0))
 {
     R resmin = R(1.0e20), s = fallback;
-    if (r0 < resmin) { resmin = r0; s = (R)spans[0]; }
-    if (r1 < resmin) { resmin = r1; s = (R)spans[1]; }
-    if (r2 < resmin) { resmin = r2; s = (R)spans[2]; }
-    if (alpha > 0.0 && alpha <= 10.0 && resmin < res_woof && resmin > R(0)) {
+    int k = -1;
+    if (r0 < resmin) { resmin = r0; s = (R)spans[0]; k = 0; }
+    const bool mid_wins = (use_d01 && k == 0 && r1 < R(1.0e20)) ? (d01 > R(0)) : (r1 < resmin);
+    if (mid_wins) { resmin = r1; s = (R)spans[1]; k = 1; }
+    if (r2 < resmin) { resmin = r2; s = (R)spans[2]; k = 2; }
+    bool below = resmin < res_woof;
+    if (sizeof(R) == 4 && !below && resmin == res_woof && ((k == 0 && lim0) || (k == 1 && lim1)))
+        below = true;
+    if (alpha > 0.0 && alpha <= 10.0 && below && resmin > R(0)) {
         R tmp = resmin / res_woof;
         if (tmp < R(1.0e-7)) tmp = R(1.0e-7);
         const R ex = (R)(10.0 - alpha);
@@ -528,6 +611,13 @@ __device__ inline R choose_span(const double *spans, R r0, R r1, R r2, R res_woo
         s += ((R)spans[2] - s) * pw;
     }
     return s;
+}
+
+// tweeter and midrange residuals so close that FP32 rounding could reorder them
+template <typename R>
+__device__ inline bool span_contested(R diff, R r0, R r1, float margin)
+{
+    return sizeof(R) == 4 && fabs(diff) <= (R)margin * fmax(r0, r1);
 }
 
 template <typename R>
@@ -561,8 +651,8 @@ struct KSum {
 };
 
 // Run bookkeeping for the averaging step of every running line: centres with
-// equal abscissae get the weighted mean of their values.  Chunks never split
-// a run, so a thread sees each run whole.
+// equal phases get the weighted mean of their values.  Chunks never split a
+// run, so a thread sees each run whole.
 template <typename R, int K>
 struct RunAvg {
     int start;
@@ -576,8 +666,14 @@ struct RunAvg {
     }
 };
 
+template <typename R>
+__device__ inline bool tie_next(const Frame<R> &fr, int j)
+{
+    return (fr.tie[j >> 5] >> (j & 31)) & 1u;
+}
+
 template <typename R, int K, typename Emit>
-__device__ inline void run_push(RunAvg<R, K> &ra, const Frame<R> &fr, int j, int n, bool ties,
+__device__ inline void run_push(RunAvg<R, K> &ra, const Frame<R> &fr, int j, bool ties,
                                 const R (&vals)[K], Emit &&emit)
 {
     if (!ties) {
@@ -588,7 +684,7 @@ __device__ inline void run_push(RunAvg<R, K> &ra, const Frame<R> &fr, int j, int
     ra.w += wj;
 #pragma unroll
     for (int k = 0; k < K; ++k) ra.s[k] += wj * vals[k];
-    if (j + 1 < n && fr.X[j + 1] == fr.X[j]) return;   // run continues
+    if (tie_next(fr, j)) return;   // run continues
     if (ra.start == j) {
         emit(j, vals);
     } else {
@@ -600,33 +696,73 @@ __device__ inline void run_push(RunAvg<R, K> &ra, const Frame<R> &fr, int j, int
     ra.reset(j + 1);
 }
 
+
+// Binary64 line fit of window [j - h, j + h] at centre j, summed by the 32
+// lanes of a warp: exact phases (the fold's 64-bit fixed-point output by
+// original index) and binary64 magnitudes and weights read through perm.
+// Every lane returns the fit; all lanes of the warp must call it together.
+template <typename R>
+__device__ double warp_fit_fp64(const Frame<R> &fr, const double *y64, const double *w64, int j,
+                                int h, int n, double vsmlsq64, double xj)
+{
+    const int lane = threadIdx.x & 31;
+    double sw = 0.0, sa = 0.0, sb = 0.0, sc = 0.0, sd = 0.0;
+    for (int e = j - h + lane; e <= j + h; e += 32) {
+        int sh;
+        const int p = slot_point(e, n, sh);
+        const uint32_t i = fr.perm[p];
+        const double x = (double)(((uint64_t)fr.key[i] << 32) | fr.klo[i]) * 5.421010862427522e-20 + sh;
+        const double w = w64[i], y = y64[i], dx = x - xj;
+        sw += w;
+        sa += w * dx;
+        sb += w * dx * dx;
+        sc += w * y;
+        sd += w * dx * y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sw += __shfl_xor_sync(0xffffffffu, sw, o);
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+    }
+    const double xb = sa / sw;              // xbar - x_j
+    const double sxx = sb - xb * sa;
+    const double sxv = sd - xb * sc;
+    const double a = sxx > vsmlsq64 ? sxv / sxx : 0.0;
+    return sc / sw + a * (0.0 - xb);
+}
+
+struct FreqResult {
+    double chi2;
+    bool near;   // FP32C: some decision fell within its margin
+};
+
 // ---------------------------------------------------------------------------
-// one (object, frequency): returns chi2 (block-uniform)
+// one (object, frequency)
 // ---------------------------------------------------------------------------
 template <typename R, int VARIANT>
-__device__ double process_frequency(const PgramArgs &a, int obj, int n, double f, const Frame<R> &fr,
-                                    const Small<R> &sm)
+__device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, double f,
+                                        const Frame<R> &fr, const Small<R> &sm)
 {
     const int tid = threadIdx.x, G = blockDim.x;
     const int64_t base = a.off[obj];
     const R *yc = (const R *)a.yc + base;
     const R *wv = (const R *)a.wv + base;
+    const double *tt = a.tt + base;
 
-    // ---- fold ----
-    if (sizeof(R) == 8) {
-        const double *tt = a.tt + base;
-        for (int i = tid; i < n; i += G) {
-            double ph = fold_fp64(tt[i], f);
+    // ---- fold: phase bits as a 64-bit fixed-point fraction ----
+    for (int i = tid; i < n; i += G) {
+        uint64_t fx;
+        if (sizeof(R) == 8) {
+            const double ph = fold_fp64(tt[i], f);
             fr.ph[i] = ph;
-            fr.key[i] = __double2uint_rz(ph * 4294967296.0);
+            fx = __double2ull_rz(ph * 18446744073709551616.0);
+        } else {
+            fx = fold_fixed64(tt[i], f);
         }
-    } else {
-        int ef;
-        frexp(f, &ef);
-        const uint64_t F = (uint64_t)ldexp(f, 63 - ef);
-        const int s = 94 - a.texp[obj] - ef;
-        const uint64_t *tf = a.tfix + base;
-        for (int i = tid; i < n; i += G) fr.key[i] = fold_fixed(tf[i], F, s);
+        fr.key[i] = (uint32_t)(fx >> 32);
+        fr.klo[i] = (uint32_t)fx;
     }
     __syncthreads();
 
@@ -634,22 +770,41 @@ __device__ double process_frequency(const PgramArgs &a, int obj, int n, double f
     argsort_phases<R>(fr, n, sm);
 
     // ---- gather ----
-    for (int j = tid; j < n; j += G) {
-        const uint32_t i = fr.perm[j];
-        R x;
-        if (sizeof(R) == 8) x = (R)fr.ph[i];
-        else x = (R)(__uint2float_rz(fr.key[i]) * 2.3283064365386963e-10f);
-        fr.X[j] = x;
-        fr.WT[j] = wv[i];
-        fr.Y[j] = yc[i];
-    }
-    __syncthreads();
+    // tie bits and the degenerate test use the exact fold output, so runs of
+    // equal abscissae are those of the binary64 phases, whatever X rounds to
     int tie = 0;
-    for (int j = tid; j + 1 < n; j += G) tie |= (fr.X[j + 1] == fr.X[j]);
+    for (int j0 = tid - (tid & 31); j0 < n; j0 += G) {
+        const int j = j0 + (tid & 31);
+        bool tj = false;
+        if (j < n) {
+            const uint32_t i = fr.perm[j];
+            R x;
+            if (sizeof(R) == 8) {
+                x = (R)fr.ph[i];
+            } else {
+                const uint64_t fx = ((uint64_t)fr.key[i] << 32) | fr.klo[i];
+                x = (R)(__ull2float_rz(fx) * 5.421010862427522e-20f);   // * 2^-64
+            }
+            fr.X[j] = x;
+            fr.WT[j] = wv[i];
+            fr.Y[j] = yc[i];
+            if (j + 1 < n) {
+                const uint32_t i2 = fr.perm[j + 1];
+                tj = (sizeof(R) == 8) ? (fr.ph[i] == fr.ph[i2])
+                                      : (fr.key[i] == fr.key[i2] && fr.klo[i] == fr.klo[i2]);
+            }
+        }
+        const uint32_t word = __ballot_sync(0xffffffffu, tj);
+        if ((tid & 31) == 0) fr.tie[j0 >> 5] = word;
+        tie |= tj;
+    }
     const bool ties = __syncthreads_or(tie) != 0;
+    const uint32_t pf = fr.perm[0], pl = fr.perm[n - 1];
+    const bool flat = (sizeof(R) == 8) ? !(fr.ph[pl] > fr.ph[pf])
+                                       : (fr.key[pl] == fr.key[pf] && fr.klo[pl] == fr.klo[pf]);
 
     // ---- degenerate abscissae: weighted mean (Listing 1) ----
-    if (!(fr.X[n - 1] > fr.X[0])) {
+    if (flat) {
         double sw = 0.0, swy = 0.0;
         for (int j = tid; j < n; j += G) {
             sw += (double)fr.WT[j];
@@ -663,7 +818,7 @@ __device__ double process_frequency(const PgramArgs &a, int obj, int n, double f
             const double d = (double)(fr.Y[j] - m);
             c2 += (double)fr.WT[j] * d * d;
         }
-        return block_sum(c2, sm.red);
+        return FreqResult{block_sum(c2, sm.red), false};
     }
 
     const int qi = n / 4 - 1, qj = 3 * (qi + 1) - 1;
@@ -672,12 +827,13 @@ __device__ double process_frequency(const PgramArgs &a, int obj, int n, double f
     const int h0 = half_width(n, a.spans[0]);
     const int h1 = half_width(n, a.spans[1]);
     const int h2 = half_width(n, a.spans[2]);
+    const bool lim0 = h0 != h2, lim1 = h1 != h2;
 
     // ---- chunks: contiguous centre ranges that never split a run of ties ----
     {
         int c = (int)(((long long)tid * n) / G);
         if (ties)
-            while (c > 0 && c < n && fr.X[c] == fr.X[c - 1]) ++c;
+            while (c > 0 && c < n && tie_next(fr, c - 1)) ++c;
         sm.cs[tid] = c;
         if (tid == 0) sm.cs[G] = n;
     }
@@ -699,36 +855,91 @@ __device__ double process_frequency(const PgramArgs &a, int obj, int n, double f
     }
 
     KSum<R> chi2;
+    bool near = false;
 
     if (VARIANT == VAR_SP) {
         // one sweep, three windows on y, generalized validation (Sec. 3)
         const R *vy[1] = {fr.Y};
         channel_aggregates<R, 1>(fr, sm, vy);
         __syncthreads();
-        if (c0 < c1) {
-            Win<R, 1> w0, w1, w2;
+        const int lane = tid & 31;
+        const int len = c1 - c0;
+        // warp-uniform trip count: contested centres are settled by the warp
+        const int kmax = __reduce_max_sync(0xffffffffu, len);
+        Win<R, 1> w0, w1, w2;
+        if (len > 0) {
             win_init<R, 1>(w0, fr, sm, vy, c0, h0, n, o);
             win_init<R, 1>(w1, fr, sm, vy, c0, h1, n, o);
             win_init<R, 1>(w2, fr, sm, vy, c0, h2, n, o);
-            const R m0 = (R)(2 * h0 + 1), m1 = (R)(2 * h1 + 1), m2 = (R)(2 * h2 + 1);
-            RunAvg<R, 1> ra;
-            ra.reset(c0);
-            auto emit = [&](int i, const R (&v)[1]) {
-                const R d = fr.Y[i] - v[0];
-                chi2.add(fr.WT[i] * d * d);
-            };
-            for (int j = c0; j < c1; ++j) {
+        }
+        const R m0 = (R)(2 * h0 + 1), m1 = (R)(2 * h1 + 1), m2 = (R)(2 * h2 + 1);
+        const double *y64 = a.yc64 ? a.yc64 + base : nullptr;
+        const double *w64 = a.wv64 ? a.wv64 + base : nullptr;
+        double vsm64 = 0.0;
+        if (sizeof(R) == 4 && y64) {
+            const uint32_t pi = fr.perm[qi], pj = fr.perm[qj];
+            const double xi = (double)(((uint64_t)fr.key[pi] << 32) | fr.klo[pi]) * 5.421010862427522e-20;
+            const double xq = (double)(((uint64_t)fr.key[pj] << 32) | fr.klo[pj]) * 5.421010862427522e-20;
+            vsm64 = 1.0e-6 * (xq - xi) * (xq - xi);
+        }
+        RunAvg<R, 1> ra;
+        ra.reset(c0);
+        auto emit = [&](int i, const R (&v)[1]) {
+            const R d = fr.Y[i] - v[0];
+            chi2.add(fr.WT[i] * d * d);
+        };
+        for (int k = 0; k < kmax; ++k) {
+            const bool act = k < len;
+            const int j = c0 + k;
+            R val[1] = {R(0)};
+            bool contested = false;
+            R s0 = R(0), s1 = R(0), s2 = R(0), g2 = R(0);
+            bool sl0 = false, sl1 = false;
+            if (act) {
                 Fit<R, 1> f0, f1, f2;
-                win_fit_checked<R, 1>(f0, w0, fr, vy, j, h0, n, o, vsmlsq);
-                win_fit_checked<R, 1>(f1, w1, fr, vy, j, h1, n, o, vsmlsq);
-                win_fit_checked<R, 1>(f2, w2, fr, vy, j, h2, n, o, vsmlsq);
+                win_fit_checked<R, 1>(f0, w0, fr, vy, j, h0, n, o, vsmlsq, near);
+                win_fit_checked<R, 1>(f1, w1, fr, vy, j, h1, n, o, vsmlsq, near);
+                win_fit_checked<R, 1>(f2, w2, fr, vy, j, h2, n, o, vsmlsq, near);
                 const R yj = fr.Y[j];
-                const R g0 = fabs(yj - f0.s[0]) / (R(1) - (f0.slope ? R(2) : R(1)) / m0);
-                const R g1 = fabs(yj - f1.s[0]) / (R(1) - (f1.slope ? R(2) : R(1)) / m1);
-                const R g2 = fabs(yj - f2.s[0]) / (R(1) - (f2.slope ? R(2) : R(1)) / m2);
-                const R sp = choose_span<R>(a.spans, g0, g1, g2, g2, a.alpha, (R)a.spans[2]);
-                const R val[1] = {interpolate_span<R>(a.spans, sp, f0.s[0], f1.s[0], f2.s[0])};
-                run_push<R, 1>(ra, fr, j, n, ties, val, emit);
+                s0 = f0.s[0];
+                s1 = f1.s[0];
+                s2 = f2.s[0];
+                sl0 = f0.slope;
+                sl1 = f1.slope;
+                const R g0 = fabs(yj - s0) / (R(1) - (f0.slope ? R(2) : R(1)) / m0);
+                const R g1 = fabs(yj - s1) / (R(1) - (f1.slope ? R(2) : R(1)) / m1);
+                g2 = fabs(yj - s2) / (R(1) - (f2.slope ? R(2) : R(1)) / m2);
+                const R sp = choose_span<R>(a.spans, g0, g1, g2, g2, a.alpha, (R)a.spans[2],
+                                            lim0, lim1);
+                val[0] = interpolate_span<R>(a.spans, sp, s0, s1, s2);
+                if (sizeof(R) == 4 && y64) {
+                    const R scale = fmax(fmax(fabs(yj), fabs(s0)), fabs(s1));
+                    contested = fabs(g0 - g1) <= (R)a.near_sp * (R)1.1920929e-7 * scale;
+                }
+            }
+            unsigned todo = __ballot_sync(0xffffffffu, contested);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int je = __shfl_sync(0xffffffffu, j, src);
+                const uint32_t pe = fr.perm[je];
+                const double xe = (double)(((uint64_t)fr.key[pe] << 32) | fr.klo[pe]) * 5.421010862427522e-20;
+                const double t0 = warp_fit_fp64<R>(fr, y64, w64, je, h0, n, vsm64, xe);
+                const double t1 = warp_fit_fp64<R>(fr, y64, w64, je, h1, n, vsm64, xe);
+                if (lane == src) {
+                    // the choice in binary64; the woofer's residual stays FP32
+                    // (near it the choice is continuous)
+                    const double ye = y64[pe];
+                    const double d0 = 1.0 - (sl0 ? 2.0 : 1.0) / (double)m0;
+                    const double d1 = 1.0 - (sl1 ? 2.0 : 1.0) / (double)m1;
+                    const double e0 = fabs(ye - t0) / d0, e1 = fabs(ye - t1) / d1;
+                    const double sp = choose_span<double>(a.spans, e0, e1, (double)g2, (double)g2,
+                                                          a.alpha, a.spans[2], lim0, lim1);
+                    val[0] = (R)interpolate_span<double>(a.spans, sp, t0, t1, (double)s2);
+                }
+            }
+            if (act) {
+                run_push<R, 1>(ra, fr, j, ties, val, emit);
                 if (j + 1 < c1) {
                     win_slide<R, 1>(w0, fr, vy, j, h0, n, o);
                     win_slide<R, 1>(w1, fr, vy, j, h1, n, o);
@@ -736,7 +947,8 @@ __device__ double process_frequency(const PgramArgs &a, int obj, int n, double f
                 }
             }
         }
-        return block_sum(chi2.value(), sm.red);
+        near = __syncthreads_or(near) != 0;
+        return FreqResult{block_sum(chi2.value(), sm.red), near};
     }
 
     // ===== SS, Listing 1 =====
@@ -761,18 +973,20 @@ __device__ double process_frequency(const PgramArgs &a, int obj, int n, double f
             };
             for (int j = c0; j < c1; ++j) {
                 Fit<R, 1> f0, f1, f2;
-                win_fit_checked<R, 1>(f0, w0, fr, vy, j, h0, n, o, vsmlsq);
-                win_fit_checked<R, 1>(f1, w1, fr, vy, j, h1, n, o, vsmlsq);
-                win_fit_checked<R, 1>(f2, w2, fr, vy, j, h2, n, o, vsmlsq);
+                win_fit_checked<R, 1>(f0, w0, fr, vy, j, h0, n, o, vsmlsq, near);
+                win_fit_checked<R, 1>(f1, w1, fr, vy, j, h1, n, o, vsmlsq, near);
+                win_fit_checked<R, 1>(f2, w2, fr, vy, j, h2, n, o, vsmlsq, near);
                 const R yj = fr.Y[j], wj = fr.WT[j];
                 const R d0 = R(1) - wj * (f0.rW + f0.dxj * f0.dxj * f0.rS);
                 const R d1 = R(1) - wj * (f1.rW + f1.dxj * f1.dxj * f1.rS);
                 const R d2 = R(1) - wj * (f2.rW + f2.dxj * f2.dxj * f2.rS);
+                if (sizeof(R) == 4 && fmin(fmin(fabs(d0), fabs(d1)), fabs(d2)) < (R)kNearLev)
+                    near = true;
                 fr.C[1][j] = d0 > R(0) ? fabs(yj - f0.s[0]) / d0 : R(-1);
                 fr.C[3][j] = d1 > R(0) ? fabs(yj - f1.s[0]) / d1 : R(-1);
                 fr.C[5][j] = d2 > R(0) ? fabs(yj - f2.s[0]) / d2 : R(-1);
                 const R val[3] = {f0.s[0], f1.s[0], f2.s[0]};
-                run_push<R, 3>(ra, fr, j, n, ties, val, emit);
+                run_push<R, 3>(ra, fr, j, ties, val, emit);
                 if (j + 1 < c1) {
                     win_slide<R, 1>(w0, fr, vy, j, h0, n, o);
                     win_slide<R, 1>(w1, fr, vy, j, h1, n, o);
@@ -797,28 +1011,37 @@ __device__ double process_frequency(const PgramArgs &a, int obj, int n, double f
     }
     __syncthreads();
 
-    // pass B: midrange smooth of the three residual columns, span choice with
-    // bass enhancement -> C6
+    // pass B: midrange smooth of the three residual columns (and, FP32C, of the
+    // tweeter-minus-midrange difference), span choice with bass enhancement
+    // -> C6
     {
+        constexpr bool DIFF = sizeof(R) == 4;
+        constexpr int NB = DIFF ? 4 : 3;
         const R *vr[3] = {fr.C[1], fr.C[3], fr.C[5]};
-        channel_aggregates<R, 3>(fr, sm, vr);
+        const float margin = a.near_ss * fminf(1.f, 256.f / (float)n) * fminf(1.f, 512.f / (float)n);
+        channel_aggregates<R, NB, DIFF>(fr, sm, vr);
         __syncthreads();
         if (c0 < c1) {
-            Win<R, 3> w1;
-            win_init<R, 3>(w1, fr, sm, vr, c0, h1, n, o);
-            RunAvg<R, 3> ra;
+            Win<R, NB> w1;
+            win_init<R, NB, DIFF>(w1, fr, sm, vr, c0, h1, n, o);
+            RunAvg<R, NB> ra;
             ra.reset(c0);
-            auto emit = [&](int i, const R (&v)[3]) {
+            auto emit = [&](int i, const R (&v)[NB]) {
+                const R d01 = DIFF ? v[NB - 1] : v[0] - v[1];
+                if (span_contested(d01, v[0], v[1], margin)) near = true;
                 // when no residual is below 1e20 the span column keeps the
                 // woofer's CV residual, as Listing 1's column 6 does
-                fr.C[6][i] = choose_span<R>(a.spans, v[0], v[1], v[2], v[2], a.alpha, fr.C[5][i]);
+                fr.C[6][i] = choose_span<R>(a.spans, v[0], v[1], v[2], v[2], a.alpha, fr.C[5][i],
+                                            lim0, lim1, DIFF, d01);
             };
             for (int j = c0; j < c1; ++j) {
-                Fit<R, 3> f1;
-                win_fit_checked<R, 3>(f1, w1, fr, vr, j, h1, n, o, vsmlsq);
-                const R val[3] = {f1.s[0], f1.s[1], f1.s[2]};
-                run_push<R, 3>(ra, fr, j, n, ties, val, emit);
-                if (j + 1 < c1) win_slide<R, 3>(w1, fr, vr, j, h1, n, o);
+                Fit<R, NB> f1;
+                win_fit_checked<R, NB, DIFF>(f1, w1, fr, vr, j, h1, n, o, vsmlsq, near);
+                R val[NB];
+#pragma unroll
+                for (int c = 0; c < NB; ++c) val[c] = f1.s[c];
+                run_push<R, NB>(ra, fr, j, ties, val, emit);
+                if (j + 1 < c1) win_slide<R, NB, DIFF>(w1, fr, vr, j, h1, n, o);
             }
         }
     }
@@ -839,9 +1062,9 @@ __device__ double process_frequency(const PgramArgs &a, int obj, int n, double f
             };
             for (int j = c0; j < c1; ++j) {
                 Fit<R, 1> f1;
-                win_fit_checked<R, 1>(f1, w1, fr, vs, j, h1, n, o, vsmlsq);
+                win_fit_checked<R, 1>(f1, w1, fr, vs, j, h1, n, o, vsmlsq, near);
                 const R val[1] = {f1.s[0]};
-                run_push<R, 1>(ra, fr, j, n, ties, val, emit);
+                run_push<R, 1>(ra, fr, j, ties, val, emit);
                 if (j + 1 < c1) win_slide<R, 1>(w1, fr, vs, j, h1, n, o);
             }
         }
@@ -864,19 +1087,24 @@ __device__ double process_frequency(const PgramArgs &a, int obj, int n, double f
             };
             for (int j = c0; j < c1; ++j) {
                 Fit<R, 1> f0;
-                win_fit_checked<R, 1>(f0, w0, fr, vv, j, h0, n, o, vsmlsq);
+                win_fit_checked<R, 1>(f0, w0, fr, vv, j, h0, n, o, vsmlsq, near);
                 const R val[1] = {f0.s[0]};
-                run_push<R, 1>(ra, fr, j, n, ties, val, emit);
+                run_push<R, 1>(ra, fr, j, ties, val, emit);
                 if (j + 1 < c1) win_slide<R, 1>(w0, fr, vv, j, h0, n, o);
             }
         }
     }
-    return block_sum(chi2.value(), sm.red);
+    near = __syncthreads_or(near) != 0;
+    return FreqResult{block_sum(chi2.value(), sm.red), near};
 }
 
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
+// Persistent CTAs take work items (object, frequency range) from a counter.
+// FP32C launches flag frequencies whose decisions came within their margins;
+// the FP64 kernel's recompute launch then redoes exactly those frequencies
+// and overwrites their (float) power.
 template <typename R, int VARIANT, bool GMEM>
 __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
 {
@@ -886,7 +1114,6 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
     Small<R> sm = carve_small<R>(smem, G);
     unsigned char *big = GMEM ? a.slab + (size_t)blockIdx.x * a.slab_bytes
                               : smem + align16(small_bytes<R>(G));
-    R *power = (R *)a.power;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(a.item_counter, 1);
         __syncthreads();
@@ -899,15 +1126,23 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
         const Frame<R> fr = carve_frame<R>(big, n);
         const bool bad = a.bad[o] != 0;
         for (int q = item.y; q < item.z; ++q) {
+            const int64_t at = (int64_t)o * a.n_freq + q;
+            if (a.recompute && (bad || a.near[at] == 0)) continue;   // block-uniform
             double pw;
+            bool near = false;
             if (bad) {
                 pw = __longlong_as_double(0x7ff8000000000000LL);
             } else {
-                const double c2 = process_frequency<R, VARIANT>(a, o, n, a.freq[q], fr, sm);
+                const FreqResult r = process_frequency<R, VARIANT>(a, o, n, a.freq[q], fr, sm);
                 const double c0 = a.chi0[o];
-                pw = (c0 > 0.0) ? 1.0 - c2 / c0 : 0.0;
+                pw = (c0 > 0.0) ? 1.0 - r.chi2 / c0 : 0.0;
+                near = r.near;
             }
-            if (threadIdx.x == 0) power[(int64_t)o * a.n_freq + q] = (R)pw;
+            if (threadIdx.x == 0) {
+                if (a.power_f32) ((float *)a.power)[at] = (float)pw;
+                else ((double *)a.power)[at] = pw;
+                if (near && a.near) a.near[at] = 1;
+            }
             __syncthreads();
         }
     }

@@ -18,8 +18,8 @@ __device__ inline double warp_sum(double v)
 // Alg. 1 compute_chi0_tt_weights, one CTA per object: tt = t - min t,
 // w = dy^-2, ybar = sum w y / sum w, chi0 = sum w (y - ybar)^2; the smoother's
 // inputs are stored in R (magnitudes centred on ybar, which leaves chi2
-// unchanged because every running line reproduces constants), and for the
-// FP32C fold tt becomes the fixed-point integer tt * 2^(63-E), tt < 2^E.
+// unchanged because every running line reproduces constants) and, for the
+// FP32C path, also in binary64 for the recompute of flagged frequencies.
 template <typename R>
 __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a)
 {
@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a)
     const int o = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t base = a.off[o];
     const int n = (int)(a.off[o + 1] - base);
-    double tmin = INFINITY, tmax = -INFINITY, sw = 0.0, swy = 0.0;
+    double tmin = INFINITY, sw = 0.0, swy = 0.0;
     int bad = 0;
     for (int i = tid; i < n; i += blockDim.x) {
         const double t = a.t[base + i], y = a.y[base + i], dy = a.dy[base + i];
@@ -37,20 +37,15 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a)
         if (!(w > 0.0) || !isfinite(w)) bad = 1;
         if (sizeof(R) == 4 && !(w >= (double)FLT_MIN && w <= (double)FLT_MAX)) bad = 1;
         tmin = fmin(tmin, t);
-        tmax = fmax(tmax, t);
         sw += w;
         swy += w * y;
     }
-    for (int off = 16; off > 0; off >>= 1) {
-        tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, off));
-        tmax = fmax(tmax, __shfl_xor_sync(0xffffffffu, tmax, off));
-    }
+    for (int off = 16; off > 0; off >>= 1) tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, off));
     sw = warp_sum(sw);
     swy = warp_sum(swy);
     bad = __any_sync(0xffffffffu, bad);
     if (lane == 0) {
         s_red[0][warp] = tmin;
-        s_red[1][warp] = tmax;
         s_red[2][warp] = sw;
         s_red[3][warp] = swy;
         s_bad[warp] = bad;
@@ -58,22 +53,17 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a)
     __syncthreads();
     const int nw = blockDim.x >> 5;
     tmin = s_red[0][0];
-    tmax = s_red[1][0];
     sw = 0.0;
     swy = 0.0;
     bad = 0;
     for (int k = 0; k < nw; ++k) {
         tmin = fmin(tmin, s_red[0][k]);
-        tmax = fmax(tmax, s_red[1][k]);
         sw += s_red[2][k];
         swy += s_red[3][k];
         bad |= s_bad[k];
     }
     __syncthreads();
     const double ybar = swy / sw;
-    const double span = tmax - tmin;
-    int E = 0;
-    if (span > 0.0) frexp(span, &E);
     double c0 = 0.0;
     R *yc = (R *)a.yc + base;
     R *wv = (R *)a.wv + base;
@@ -83,10 +73,13 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a)
         const double tt = __dsub_rn(t, tmin);
         const double d = y - ybar;
         c0 += w * d * d;
-        if (sizeof(R) == 8) a.tt[base + i] = tt;
-        else a.tfix[base + i] = __double2ull_rn(ldexp(tt, 63 - E));
+        a.tt[base + i] = tt;
         yc[i] = (R)d;
         wv[i] = (R)w;
+        if (a.yc64) {
+            a.yc64[base + i] = d;
+            a.wv64[base + i] = w;
+        }
     }
     c0 = warp_sum(c0);
     if (lane == 0) s_red[0][warp] = c0;
@@ -95,7 +88,6 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a)
         double c = 0.0;
         for (int k = 0; k < nw; ++k) c += s_red[0][k];
         a.chi0[o] = c;
-        a.texp[o] = E;
         a.bad[o] = bad;
     }
 }

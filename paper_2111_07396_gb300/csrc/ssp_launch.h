@@ -12,10 +12,9 @@ namespace ssp {
 struct PrepArgs {
     const double *t, *y, *dy;  // [N] caller's device arrays
     const int64_t *off;        // [n_obj + 1]
-    double *tt;                // [N] FP64 path
-    uint64_t *tfix;            // [N] FP32C path
-    int *texp;                 // [n_obj]
-    void *yc, *wv;             // [N] R
+    double *tt;                // [N] t - min t, binary64 (both paths)
+    void *yc, *wv;             // [N] R: centred magnitudes, weights
+    double *yc64, *wv64;       // [N] FP64 copies for the FP32C recompute (or null)
     double *chi0;              // [n_obj]
     int *bad;                  // [n_obj]
 };

@@ -33,7 +33,7 @@ class ssp_phase_time(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
 
 
-PHASES = ("prep", "pgram_ss", "pgram_sp", "argmax")
+PHASES = ("prep", "pgram_ss", "pgram_sp", "redo", "argmax")
 
 
 class SSPError(RuntimeError):
@@ -68,6 +68,8 @@ def lib():
         L.ssp_last_error.restype = ctypes.c_char_p
         L.ssp_version.argtypes = []
         L.ssp_version.restype = ctypes.c_char_p
+        L.ssp_fold_fixed.argtypes = [P, i64, ctypes.c_double, P]
+        L.ssp_fold_fixed.restype = ctypes.c_int
         L.ssp_profile_enable.argtypes = [ctypes.c_int]
         L.ssp_profile_enable.restype = None
         L.ssp_profile_read.argtypes = [ctypes.POINTER(ssp_phase_time), ctypes.c_int]
@@ -100,6 +102,14 @@ def ssp_last_error() -> str:
 
 def ssp_version() -> str:
     return lib().ssp_version().decode()
+
+
+def ssp_fold_fixed(tt, f):
+    """The kernels' FP32C phase fold on the host: floor(frac(fl(tt*f)) * 2^64)."""
+    tt = _f64(tt)
+    out = np.empty(tt.size, dtype=np.uint64)
+    _check(lib().ssp_fold_fixed(_ptr(tt), tt.size, float(f), _ptr(out)))
+    return out
 
 
 def ssp_profile_enable(on: bool = True) -> None:
