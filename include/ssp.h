@@ -124,6 +124,33 @@ int ssp_periodogram_device(const double *t, const double *y, const double *dy,
  */
 int ssp_fold_fixed(const double *tt, int64_t n, double f, uint64_t *out);
 
+/*
+ * ssp_periodogram_device without any device allocation.  (The paper has no
+ * counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc: code running while a stream is being captured into a CUDA
+ * graph, programs whose device memory is owned by another allocator or
+ * capped by a memory pool, and hosts that forbid allocation after start-up.)
+ * Arguments and results are those of ssp_periodogram_device; inputs and
+ * outputs are still the caller's device buffers, and n_per_object is a host
+ * array.  Temporary storage is a fixed 8 MiB array in device memory that
+ * this library declares at file scope; every GPU that loads the library
+ * holds it until the process exits.
+ * Limits: the request's scratch must fit the 8 MiB, and every object's
+ * frame must fit shared memory (about 2,500 points per object); larger
+ * requests return SSP_ERR_UNSUPPORTED with the reason in ssp_last_error().
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and the library clears what must start at
+ * zero on every call, so calls whose work overlaps on the GPU (different
+ * streams, or several host threads) race with each other and must be
+ * serialised by the caller.  No profiling events are recorded.
+ */
+int ssp_periodogram_device_noalloc(const double *t, const double *y, const double *dy,
+                                   const int64_t *n_per_object, int64_t n_objects,
+                                   const double *freq_grid, int64_t n_freq, ssp_variant variant,
+                                   const ssp_params *params, void *out_power,
+                                   double *out_best_period, void *stream);
+
 /* Static text for a status code. */
 const char *ssp_status_string(int status);
 /* Detail of the last error returned on the calling thread ("" if none). */

@@ -445,6 +445,158 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
     return status;
 }
 
+
+// ---- entry point without device allocation ----
+// Scratch of ssp_periodogram_device_noalloc: a fixed array in device memory,
+// set aside on every GPU that loads this library until the process exits.
+// Host code may not use the name as an address; set-up takes the device
+// address with cudaGetSymbolAddress, once per device.
+constexpr size_t kNoAllocBytes = 8u << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+int noalloc_scratch(unsigned char **out)
+{
+    int dev = 0;
+    SSP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(SSP_ERR_UNSUPPORTED, "device %d", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = (unsigned char *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SSP_OK;
+}
+
+// run_device's launch sequence with the workspace carved from the fixed
+// array; frames must fit shared memory (no per-CTA global slabs).
+int run_device_noalloc(const double *t, const double *y, const double *dy, const int64_t *npo,
+                       int64_t n_obj, const double *freq, int64_t n_freq, ssp_variant variant,
+                       const ssp_params &P, void *out_power, double *out_best, cudaStream_t s)
+{
+    const int prec = (int)P.precision;
+    Plan plan;
+    int rc = build_plan(npo, n_obj, n_freq, prec, (int)variant, plan);
+    if (rc) return rc;
+    for (const Bucket &b : plan.buckets)
+        if (b.main.gmem || (plan.redo && b.redo.gmem))
+            return fail(SSP_ERR_UNSUPPORTED,
+                        "no-allocation entry point: object of %d points needs a frame in global "
+                        "memory; at most about 2500 points per object are supported",
+                        b.n_max);
+    std::vector<int64_t> off((size_t)n_obj + 1, 0);
+    for (int64_t o = 0; o < n_obj; ++o) off[o + 1] = off[o] + npo[o];
+    const int64_t N = off[n_obj];
+    const size_t ws = workspace_bytes(plan, n_obj, N, n_freq, prec);
+    if (ws > kNoAllocBytes)
+        return fail(SSP_ERR_UNSUPPORTED,
+                    "no-allocation entry point: request needs %zu bytes of scratch, the fixed "
+                    "array holds %zu",
+                    ws, kNoAllocBytes);
+    unsigned char *base = nullptr;
+    rc = noalloc_scratch(&base);
+    if (rc) return rc;
+    size_t cur = 0;
+    auto take = [&](size_t bytes) {
+        unsigned char *p = base + cur;
+        cur += align16(bytes);
+        return p;
+    };
+    int64_t *d_off = (int64_t *)take(8 * (size_t)(n_obj + 1));
+    double *d_tt = (double *)take(8 * (size_t)N);
+    int *d_bad = (int *)take(4 * (size_t)n_obj);
+    void *d_yc = take(rsize(prec) * (size_t)N);
+    void *d_wv = take(rsize(prec) * (size_t)N);
+    double *d_yc64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
+    double *d_wv64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
+    double *d_chi0 = (double *)take(8 * (size_t)n_obj);
+    int4 *d_items = (int4 *)take(sizeof(int4) * plan.items_total);
+    const size_t n_counters = 2 * plan.buckets.size() + 2;
+    int *d_counters = (int *)take(4 * n_counters);
+    unsigned char *d_near =
+        plan.redo ? (unsigned char *)take((size_t)n_obj * (size_t)n_freq) : nullptr;
+
+    std::vector<int4> items;
+    items.reserve(plan.items_total);
+    for (const Bucket &b : plan.buckets) items.insert(items.end(), b.items.begin(), b.items.end());
+    cudaError_t e = cudaSuccess;
+    do {
+        if ((e = cudaMemcpyAsync(d_off, off.data(), 8 * off.size(), cudaMemcpyHostToDevice, s))) break;
+        if ((e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(),
+                                 cudaMemcpyHostToDevice, s)))
+            break;
+        // the array keeps the previous call's contents: counters and flags restart at 0
+        if ((e = cudaMemsetAsync(d_counters, 0, 4 * n_counters, s))) break;
+        if (d_near && (e = cudaMemsetAsync(d_near, 0, (size_t)n_obj * (size_t)n_freq, s))) break;
+        PrepArgs pa{};
+        pa.t = t;
+        pa.y = y;
+        pa.dy = dy;
+        pa.off = d_off;
+        pa.tt = d_tt;
+        pa.yc = d_yc;
+        pa.wv = d_wv;
+        pa.yc64 = d_yc64;
+        pa.wv64 = d_wv64;
+        pa.chi0 = d_chi0;
+        pa.bad = d_bad;
+        if ((e = prep_launch(prec, pa, (int)n_obj, s))) break;
+        size_t item_base = 0;
+        for (size_t k = 0; k < plan.buckets.size(); ++k) {
+            const Bucket &b = plan.buckets[k];
+            PgramArgs ga{};
+            ga.off = d_off;
+            ga.tt = d_tt;
+            ga.yc = d_yc;
+            ga.wv = d_wv;
+            ga.chi0 = d_chi0;
+            ga.yc64 = d_yc64;
+            ga.wv64 = d_wv64;
+            ga.bad = d_bad;
+            ga.freq = freq;
+            ga.n_freq = n_freq;
+            ga.items = d_items + item_base;
+            ga.n_items = (int)b.items.size();
+            ga.item_counter = d_counters + 2 * k;
+            ga.power = out_power;
+            ga.power_f32 = prec == SSP_FP32C;
+            for (int i = 0; i < 3; ++i) ga.spans[i] = P.spans[i];
+            ga.alpha = P.alpha;
+            ga.near = d_near;
+            ga.near_ss = near_margin("SSP_NEAR_SS", ssp::kNearSS);
+            ga.near_sp = near_margin("SSP_NEAR_SP", ssp::kNearSP);
+            ga.recompute = 0;
+            if ((e = pgram_launch(prec, (int)variant, false, b.main.grid, b.G, b.main.smem, ga, s)))
+                break;
+            if (plan.redo) {
+                ga.yc = d_yc64;
+                ga.wv = d_wv64;
+                ga.item_counter = d_counters + 2 * k + 1;
+                ga.recompute = 1;
+                if ((e = pgram_launch(SSP_FP64, (int)variant, false, b.redo.grid, b.G, b.redo.smem,
+                                      ga, s)))
+                    break;
+            }
+            item_base += b.items.size();
+        }
+        if (e) break;
+        ArgmaxArgs aa{};
+        aa.power = out_power;
+        aa.freq = freq;
+        aa.n_freq = n_freq;
+        aa.bad = d_bad;
+        aa.best_period = out_best;
+        e = argmax_launch(prec, aa, (int)n_obj, s);
+    } while (0);
+    if (e) return cuda_fail(e, "enqueue");
+    return SSP_OK;
+}
+
 std::once_flag g_pool_once;
 
 }  // namespace
@@ -546,6 +698,26 @@ int ssp_periodogram_device(const double *t, const double *y, const double *dy,
     std::call_once(g_pool_once, keep_pool_memory);
     return run_device(t, y, dy, n_per_object, n_objects, freq_grid, n_freq, variant, P, out_power,
                       out_best_period, (cudaStream_t)stream);
+}
+
+int ssp_periodogram_device_noalloc(const double *t, const double *y, const double *dy,
+                                   const int64_t *n_per_object, int64_t n_objects,
+                                   const double *freq_grid, int64_t n_freq, ssp_variant variant,
+                                   const ssp_params *params, void *out_power,
+                                   double *out_best_period, void *stream)
+{
+    g_err.clear();
+    ssp_params P;
+    ssp_default_params(&P);
+    if (params) P = *params;
+    int rc = check_params(&P);
+    if (rc) return rc;
+    rc = check_shape(n_per_object, n_objects, n_freq, variant);
+    if (rc) return rc;
+    if (!t || !y || !dy || !freq_grid || !out_power || !out_best_period)
+        return fail(SSP_ERR_ARG, "NULL array argument");
+    return run_device_noalloc(t, y, dy, n_per_object, n_objects, freq_grid, n_freq, variant, P,
+                              out_power, out_best_period, (cudaStream_t)stream);
 }
 
 int ssp_periodogram(const double *t, const double *y, const double *dy,

@@ -68,6 +68,9 @@ def lib():
         L.ssp_last_error.restype = ctypes.c_char_p
         L.ssp_version.argtypes = []
         L.ssp_version.restype = ctypes.c_char_p
+        L.ssp_periodogram_device_noalloc.argtypes = [P, P, P, P, i64, P, i64, ctypes.c_int,
+                                                     ctypes.POINTER(ssp_params), P, P, P]
+        L.ssp_periodogram_device_noalloc.restype = ctypes.c_int
         L.ssp_fold_fixed.argtypes = [P, i64, ctypes.c_double, P]
         L.ssp_fold_fixed.restype = ctypes.c_int
         L.ssp_profile_enable.argtypes = [ctypes.c_int]
@@ -176,6 +179,25 @@ def ssp_periodogram_device(t, y, dy, n_per_object, freq_grid, out_power, out_bes
                                       int(npo.size), _dev_ptr(freq_grid), n_freq,
                                       VARIANTS[variant], ctypes.byref(p), _dev_ptr(out_power),
                                       _dev_ptr(out_best_period), ctypes.c_void_p(s))
+    _check(rc)
+    return out_power, out_best_period
+
+
+def ssp_periodogram_device_noalloc(t, y, dy, n_per_object, freq_grid, out_power, out_best_period,
+                                   variant="ss", precision="fp32c", alpha=9.0, spans=None,
+                                   params=None, stream=None):
+    """As ssp_periodogram_device, with no device allocation: scratch lives in
+    the library's fixed device array (see include/ssp.h for its limits)."""
+    p = params if params is not None else ssp_default_params(precision, alpha, spans)
+    npo = np.ascontiguousarray(n_per_object, dtype=np.int64)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    s = stream if isinstance(stream, int) else stream.cuda_stream
+    rc = lib().ssp_periodogram_device_noalloc(
+        _dev_ptr(t), _dev_ptr(y), _dev_ptr(dy), _ptr(npo), int(npo.size), _dev_ptr(freq_grid),
+        int(freq_grid.numel()), VARIANTS[variant], ctypes.byref(p), _dev_ptr(out_power),
+        _dev_ptr(out_best_period), ctypes.c_void_p(s))
     _check(rc)
     return out_power, out_best_period
 
