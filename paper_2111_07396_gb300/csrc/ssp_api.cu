@@ -26,8 +26,8 @@ cudaError_t pgram_launch_fp32(int, bool, int, int, size_t, const PgramArgs &, cu
 cudaError_t pgram_launch_fp64(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
 size_t pgram_small_bytes_fp32(int);
 size_t pgram_small_bytes_fp64(int);
-size_t pgram_frame_bytes_fp32(int);
-size_t pgram_frame_bytes_fp64(int);
+size_t pgram_frame_bytes_fp32(int, int);
+size_t pgram_frame_bytes_fp64(int, int);
 
 cudaError_t prep_launch(int p, const PrepArgs &a, int n, cudaStream_t s)
 {
@@ -52,9 +52,9 @@ size_t pgram_small_bytes(int p, int G)
 {
     return p == SSP_FP64 ? pgram_small_bytes_fp64(G) : pgram_small_bytes_fp32(G);
 }
-size_t pgram_frame_bytes(int p, int n)
+size_t pgram_frame_bytes(int p, int n, int variant)
 {
-    return p == SSP_FP64 ? pgram_frame_bytes_fp64(n) : pgram_frame_bytes_fp32(n);
+    return p == SSP_FP64 ? pgram_frame_bytes_fp64(n, variant) : pgram_frame_bytes_fp32(n, variant);
 }
 }  // namespace ssp
 
@@ -125,7 +125,23 @@ int check_shape(const int64_t *n_per_object, int64_t n_objects, int64_t n_freq, 
 }
 
 // threads per CTA for an object of n points: about a dozen centres per thread
+// (SSP_GROUP_SCALE, a power of two, scales the choice for calibration)
+int group_size_base(int n);
+
 int group_size(int n)
+{
+    static const int scale = [] {
+        const char *e = std::getenv("SSP_GROUP_SCALE");
+        const int v = e ? std::atoi(e) : 0;
+        return (v == 2 || v == 4 || v == -2 || v == -4) ? v : 1;
+    }();
+    int g = group_size_base(n);
+    if (scale > 1) g = std::min(512, g * scale);
+    if (scale < 0) g = std::max(32, g / -scale);
+    return g;
+}
+
+int group_size_base(int n)
 {
     if (n <= 384) return 32;
     if (n <= 768) return 64;
@@ -168,7 +184,7 @@ int configure(int precision, int variant, int G, int n_max, int sms, size_t max_
               LaunchCfg &c)
 {
     const size_t small = align16(pgram_small_bytes(precision, G));
-    const size_t frame = align16(pgram_frame_bytes(precision, n_max));
+    const size_t frame = align16(pgram_frame_bytes(precision, n_max, variant));
     c.gmem = small + frame + 1024 > max_smem;
     c.smem = c.gmem ? small : small + frame;
     c.slab_bytes = c.gmem ? frame : 0;
@@ -191,7 +207,7 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
     if (rc) return rc;
     plan.buckets.clear();
     plan.redo = precision == SSP_FP32C;
-    for (int G : {32, 64, 128, 256}) {
+    for (int G : {32, 64, 128, 256, 512}) {
         Bucket b;
         b.G = G;
         for (int64_t o = 0; o < n_obj; ++o)
@@ -245,7 +261,7 @@ float near_margin(const char *env, float dflt)
     const char *e = std::getenv(env);
     if (e && *e) {
         const double v = std::atof(e);
-        if (v < 1.0) return (float)v;
+        if (v < 1e6) return (float)v;
     }
     return dflt;
 }
@@ -403,6 +419,9 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
             ga.near = d_near;
             ga.near_ss = near_margin("SSP_NEAR_SS", ssp::kNearSS);
             ga.near_sp = near_margin("SSP_NEAR_SP", ssp::kNearSP);
+            ga.refit_frac = near_margin("SSP_REFIT_FRAC", ssp::kRefitFrac);
+            ga.sens_ulps = near_margin("SSP_SENS_ULPS", ssp::kSensUlps);
+            ga.sens_tau = near_margin("SSP_SENS_TAU", (float)ssp::kSensTau);
             ga.recompute = 0;
             slab_cur += b.main.gmem ? b.main.slab_bytes * (size_t)b.main.grid : 0;
             const int ph = variant == SSP_SP ? SSP_PHASE_PGRAM_SP : SSP_PHASE_PGRAM_SS;
@@ -570,6 +589,9 @@ int run_device_noalloc(const double *t, const double *y, const double *dy, const
             ga.near = d_near;
             ga.near_ss = near_margin("SSP_NEAR_SS", ssp::kNearSS);
             ga.near_sp = near_margin("SSP_NEAR_SP", ssp::kNearSP);
+            ga.refit_frac = near_margin("SSP_REFIT_FRAC", ssp::kRefitFrac);
+            ga.sens_ulps = near_margin("SSP_SENS_ULPS", ssp::kSensUlps);
+            ga.sens_tau = near_margin("SSP_SENS_TAU", (float)ssp::kSensTau);
             ga.recompute = 0;
             if ((e = pgram_launch(prec, (int)variant, false, b.main.grid, b.G, b.main.smem, ga, s)))
                 break;

@@ -35,6 +35,7 @@ namespace ssp {
 enum { VAR_SS = 0, VAR_SP = 1 };
 constexpr int kMaxThreads = 512;
 constexpr int kBucketRankMax = 64;   // larger buckets switch to the bitonic sort
+constexpr int kGroupMinThreads = 128;  // CTAs this large also merge groups of 8 chunks
 
 // FP32C decisions closer than these margins to their thresholds are re-taken
 // in FP64: the frequency is flagged and recomputed by the FP64 kernel.
@@ -52,6 +53,14 @@ constexpr float kNearSS = 1e-6f;
 constexpr float kNearSP = 64.f;
 constexpr float kNearLev = 1e-4f;
 constexpr float kNearSlope = 1e-4f;
+constexpr float kRefitFrac = 1.f / 128.f;  // history guard of the sliding sums
+// SP: a point whose fit could move the power by more than kSensTau through
+// the FP32 error of its residuals (bass enhancement divides by the smallest;
+// each residual is taken to err by its slope times the rounding of X plus
+// kSensUlps ulps of its magnitude scale) is settled by the warp's binary64
+// refit as well
+constexpr double kSensTau = 1e-6;
+constexpr float kSensUlps = 2.f;
 
 struct PgramArgs {
     const int64_t *off;     // [n_obj + 1] CSR offsets
@@ -76,6 +85,9 @@ struct PgramArgs {
     int power_f32;          // power array holds float
     float near_ss;          // SS margin for n <= 256 (scaled down above)
     float near_sp;          // SP margin in units of eps_fp32 * magnitude scale
+    float refit_frac;       // refit windows whose spread fell below this part of hiB
+    float sens_ulps;        // SP sensitivity: rounding of a residual, in ulps of its scale
+    double sens_tau;        // SP sensitivity: power budget per point
 };
 
 // ---------------------------------------------------------------------------
@@ -126,21 +138,24 @@ __host__ __device__ inline size_t sort_end(int n)
 }
 
 template <typename R>
-__host__ __device__ inline size_t tie_offset(int n)
+__host__ __device__ inline size_t tie_offset(int n, int ncols)
 {
-    const size_t cols = align16(sizeof(R) * (size_t)n) * 10;
+    const size_t cols = align16(sizeof(R) * (size_t)n) * ncols;
     const size_t s = sort_end<R>(n);
     return cols > s ? cols : s;
 }
 
+// columns a variant keeps: SS uses X, WT, Y and C0..C6; SP only X, WT, Y
+__host__ __device__ inline int frame_cols(int variant) { return variant == VAR_SP ? 3 : 10; }
+
 template <typename R>
-__host__ __device__ inline size_t frame_bytes(int n)
+__host__ __device__ inline size_t frame_bytes(int n, int variant)
 {
-    return tie_offset<R>(n) + align16(4 * tie_words(n));
+    return tie_offset<R>(n, frame_cols(variant)) + align16(4 * tie_words(n));
 }
 
 template <typename R>
-__device__ inline Frame<R> carve_frame(unsigned char *base, int n)
+__device__ inline Frame<R> carve_frame(unsigned char *base, int n, int variant)
 {
     Frame<R> f;
     const size_t col = align16(sizeof(R) * (size_t)n);
@@ -148,7 +163,7 @@ __device__ inline Frame<R> carve_frame(unsigned char *base, int n)
     f.WT = (R *)(base + col);
     f.Y = (R *)(base + 2 * col);
     for (int k = 0; k < 7; ++k) f.C[k] = (R *)(base + (3 + k) * col);
-    f.tie = (uint32_t *)(base + tie_offset<R>(n));
+    f.tie = (uint32_t *)(base + tie_offset<R>(n, frame_cols(variant)));
     unsigned char *s = base + 3 * col;
     const size_t a4 = align16(4 * (size_t)n), a2 = align16(2 * (size_t)n);
     const size_t ap = align16(2 * (size_t)pow2_at_least(n));
@@ -168,6 +183,8 @@ struct Small {
     int *cs;                // [G + 1] chunk starts
     R *org, *aW, *aA, *aB;  // [G] chunk origin and x-moments
     R *aC, *aD;             // [4][G] channel moments
+    R *qorg, *qW, *qA, *qB; // [G/8] moments of groups of 8 chunks
+    R *qC, *qD;             // [4][G/8]
     double *red;            // [32] reduction scratch
     int *ired;              // [32]
     int *flags;             // [4]
@@ -177,7 +194,8 @@ template <typename R>
 __host__ __device__ inline size_t small_bytes(int G)
 {
     return align16(4 * (size_t)(G + 1)) + align16(sizeof(R) * (size_t)G) * 4 +
-           align16(sizeof(R) * 4 * (size_t)G) * 2 + 32 * 8 + 32 * 4 + 16;
+           align16(sizeof(R) * 4 * (size_t)G) * 2 + align16(sizeof(R) * (size_t)(G / 8)) * 4 +
+           align16(sizeof(R) * 4 * (size_t)(G / 8)) * 2 + 32 * 8 + 32 * 4 + 16;
 }
 
 template <typename R>
@@ -195,6 +213,15 @@ __device__ inline Small<R> carve_small(unsigned char *base, int G)
     s.aC = (R *)base;
     s.aD = (R *)(base + g3);
     base += 2 * g3;
+    const size_t q = align16(sizeof(R) * (size_t)(G / 8)), q4 = align16(sizeof(R) * 4 * (size_t)(G / 8));
+    s.qorg = (R *)base;
+    s.qW = (R *)(base + q);
+    s.qA = (R *)(base + 2 * q);
+    s.qB = (R *)(base + 3 * q);
+    base += 4 * q;
+    s.qC = (R *)base;
+    s.qD = (R *)(base + q4);
+    base += 2 * q4;
     s.red = (double *)base;
     s.ired = (int *)(base + 256);
     s.flags = (int *)(base + 256 + 128);
@@ -375,6 +402,12 @@ struct Win {
     }
 };
 
+// FP32C divides with the approximate reciprocal (about 1 ulp), far cheaper
+// than an IEEE division and inside the path's error budget; FP64 divides
+// exactly.
+__device__ inline float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ inline double fdiv(double a, double b) { return a / b; }
+
 // window slot e (may lie one period before 0 or after n-1) -> point, shift
 __device__ inline int slot_point(int e, int n, int &sh)
 {
@@ -382,6 +415,13 @@ __device__ inline int slot_point(int e, int n, int &sh)
     if (e >= n) { sh = 1; return e - n; }
     sh = 0;
     return e;
+}
+template <typename R>
+__device__ inline int slot_point_r(int e, int n, R &shift)
+{
+    const int lo = e < 0, hi = e >= n;
+    shift = lo ? R(-1) : (hi ? R(1) : R(0));
+    return e + (lo ? n : 0) - (hi ? n : 0);
 }
 
 // Channel c at point p.  With DIFF the last channel is not stored: it is
@@ -398,11 +438,11 @@ template <typename R, int NCH, bool DIFF = false>
 __device__ inline void win_add(Win<R, NCH> &s, const Frame<R> &fr, const R *const *v, int e,
                                int n, R o, R sign)
 {
-    int sh;
-    int p = slot_point(e, n, sh);
-    R dx = (fr.X[p] - o) + (R)sh;
-    R w = sign * fr.WT[p];
-    R wdx = w * dx;
+    R shf;
+    const int p = slot_point_r<R>(e, n, shf);
+    const R dx = (fr.X[p] - o) + shf;
+    const R w = sign * fr.WT[p];
+    const R wdx = w * dx;
     s.W += w;
     s.A += wdx;
     s.B += wdx * dx;
@@ -426,9 +466,10 @@ __device__ inline int find_chunk(const int *cs, int G, int p)
     return lo;
 }
 
-// Sums of the window [c - h, c + h] about origin o, from whole-chunk
-// aggregates where a chunk lies inside the window and single points at the
-// ragged ends.
+// Sums of the window [c - h, c + h] about origin o, from the moments of
+// whole groups of 8 chunks and of whole chunks lying inside the window, and
+// single points at the ragged ends.  Every merge only adds (no moment is
+// subtracted), so no cancellation enters here.
 template <typename R, int NCH, bool DIFF = false>
 __device__ void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R> &sm,
                          const R *const *v, int c, int h, int n, R o)
@@ -444,6 +485,26 @@ __device__ void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R> &sm,
         p = slot_point(e, n, sh);
         if (p < sm.cs[u]) u = 0;                 // wrapped past n-1
         while (sm.cs[u + 1] <= p) ++u;           // skips empty chunks
+        if (G >= kGroupMinThreads && (u & 7) == 0 && p == sm.cs[u]) {
+            const int U = u >> 3;
+            const int glen = sm.cs[u + 8] - sm.cs[u];
+            if (e + glen - 1 <= e_end) {
+                const R d = (sm.qorg[U] - o) + (R)sh;
+                const R qW = sm.qW[U], qA = sm.qA[U];
+                s.W += qW;
+                s.A += qA + d * qW;
+                s.B += sm.qB[U] + d * (R(2) * qA + d * qW);
+                if (sizeof(R) == 4) s.hiB = fmax(s.hiB, s.B);
+#pragma unroll
+                for (int ch = 0; ch < NCH; ++ch) {
+                    const R cC = sm.qC[ch * (G / 8) + U];
+                    s.C[ch] += cC;
+                    s.D[ch] += sm.qD[ch * (G / 8) + U] + d * cC;
+                }
+                e += glen;
+                continue;
+            }
+        }
         const int len = sm.cs[u + 1] - sm.cs[u];
         if (p == sm.cs[u] && e + len - 1 <= e_end) {
             const R d = (sm.org[u] - o) + (R)sh;
@@ -462,6 +523,44 @@ __device__ void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R> &sm,
         } else {
             win_add<R, NCH, DIFF>(s, fr, v, e, n, o, R(1));
             e += 1;
+        }
+    }
+}
+
+// moments of groups of 8 chunks (about the group's first point), from the
+// chunk moments; threads 0..G/8-1 each build one group
+template <typename R, int NCH>
+__device__ void group_aggregates(const Frame<R> &fr, const Small<R> &sm, int n)
+{
+    const int G = blockDim.x, U = threadIdx.x;
+    if (G >= kGroupMinThreads && U < G / 8) {
+        const int u0 = 8 * U;
+        const R og = (sm.cs[u0] < n) ? fr.X[sm.cs[u0]] : R(0);
+        R W = R(0), A = R(0), B = R(0), C[NCH], D[NCH];
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) C[ch] = D[ch] = R(0);
+        for (int u = u0; u < u0 + 8; ++u) {
+            if (sm.cs[u + 1] == sm.cs[u]) continue;
+            const R d = sm.org[u] - og;
+            const R aW = sm.aW[u], aA = sm.aA[u];
+            W += aW;
+            A += aA + d * aW;
+            B += sm.aB[u] + d * (R(2) * aA + d * aW);
+#pragma unroll
+            for (int ch = 0; ch < NCH; ++ch) {
+                const R cC = sm.aC[ch * G + u];
+                C[ch] += cC;
+                D[ch] += sm.aD[ch * G + u] + d * cC;
+            }
+        }
+        sm.qorg[U] = og;
+        sm.qW[U] = W;
+        sm.qA[U] = A;
+        sm.qB[U] = B;
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+            sm.qC[ch * (G / 8) + U] = C[ch];
+            sm.qD[ch * (G / 8) + U] = D[ch];
         }
     }
 }
@@ -490,30 +589,34 @@ __device__ void channel_aggregates(const Frame<R> &fr, const Small<R> &sm, const
 template <typename R, int NCH>
 struct Fit {
     R rW, rS, dxj;   // 1/W, 1/Sxx (0 when the slope is dropped), x_j - xbar
+    R sxx;
     bool slope;
-    R s[NCH];
+    R s[NCH];        // fit at the centre
+    R b[NCH];        // its slope
 };
 
 template <typename R, int NCH>
 __device__ inline void win_fit(Fit<R, NCH> &f, const Win<R, NCH> &s, R xj_minus_o, R vsmlsq)
 {
-    f.rW = R(1) / s.W;
+    f.rW = fdiv(R(1), s.W);
     const R xb = s.A * f.rW;
     const R sxx = s.B - xb * s.A;
     f.slope = sxx > vsmlsq;
-    f.rS = f.slope ? R(1) / sxx : R(0);
+    f.rS = f.slope ? fdiv(R(1), sxx) : R(0);
+    f.sxx = sxx;
     f.dxj = xj_minus_o - xb;
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
         const R sxv = s.D[c] - xb * s.C[c];
-        f.s[c] = s.C[c] * f.rW + (sxv * f.rS) * f.dxj;
+        f.b[c] = sxv * f.rS;
+        f.s[c] = s.C[c] * f.rW + f.b[c] * f.dxj;
     }
 }
 
 // FP32C guard: the sliding sums carry absolute errors of order eps times the
-// largest moment they have held; where the centred spread is below 1/128 of
-// that (a tight cluster after wide windows, or a far origin), this centre's
-// window is refitted directly in FP64.
+// largest moment they have held; where the centred spread is below a fixed
+// part of that (a tight cluster after wide windows, or a far origin), this
+// centre's window is refitted directly in FP64.
 template <typename R, int NCH, bool DIFF = false>
 __device__ void win_refit_fp64(Fit<R, NCH> &f, const Frame<R> &fr, const R *const *v, int j,
                                int h, int n, double vsmlsq)
@@ -549,19 +652,21 @@ __device__ void win_refit_fp64(Fit<R, NCH> &f, const Frame<R> &fr, const R *cons
     f.rS = slope ? (R)(1.0 / sxx) : R(0);
     f.dxj = (R)dxj;
 #pragma unroll
-    for (int c = 0; c < NCH; ++c)
+    for (int c = 0; c < NCH; ++c) {
+        f.b[c] = (R)(slope ? sxv[c] / sxx : 0.0);
         f.s[c] = (R)(swv[c] / sw + (slope ? sxv[c] / sxx : 0.0) * dxj);
+    }
 }
 
 template <typename R, int NCH, bool DIFF = false>
 __device__ inline void win_fit_checked(Fit<R, NCH> &f, const Win<R, NCH> &s, const Frame<R> &fr,
                                        const R *const *v, int j, int h, int n, R o, R vsmlsq,
-                                       bool &near)
+                                       bool &near, R refit_frac)
 {
     win_fit<R, NCH>(f, s, fr.X[j] - o, vsmlsq);
     if (sizeof(R) == 4) {
-        const R sxx = s.B - (s.A / s.W) * s.A;
-        if (sxx < s.hiB * R(1.0 / 128.0) && s.hiB > R(0))
+        const R sxx = f.sxx;
+        if (sxx < s.hiB * refit_frac && s.hiB > R(0))
             win_refit_fp64<R, NCH, DIFF>(f, fr, v, j, h, n, (double)vsmlsq);
         if (fabs(sxx - vsmlsq) <= (R)kNearSlope * vsmlsq) near = true;
     }
@@ -579,6 +684,27 @@ __device__ inline void win_slide(Win<R, NCH> &s, const Frame<R> &fr, const R *co
 // ---------------------------------------------------------------------------
 // Listing 1 pieces shared by SS and SP
 // ---------------------------------------------------------------------------
+// Span constants of one frequency in the compute precision (built once, so
+// the per-centre code does no binary64 arithmetic in the FP32C kernels).
+template <typename R>
+struct SpanK {
+    R s0, s1, s2, inv01, inv21, ex;
+    bool bass;   // 0 < alpha <= 10
+};
+template <typename R>
+__device__ inline SpanK<R> span_consts(const double *spans, double alpha)
+{
+    SpanK<R> k;
+    k.s0 = (R)spans[0];
+    k.s1 = (R)spans[1];
+    k.s2 = (R)spans[2];
+    k.inv01 = R(1) / (k.s0 - k.s1);
+    k.inv21 = R(1) / (k.s2 - k.s1);
+    k.ex = (R)(10.0 - alpha);
+    k.bass = alpha > 0.0 && alpha <= 10.0;
+    return k;
+}
+
 // Span choice at one centre: first strict minimum of the three residuals,
 // then bass enhancement toward the woofer span.  Listing 1 enhances only when
 // the minimum is strictly below the woofer's residual; as the two approach,
@@ -590,25 +716,23 @@ __device__ inline void win_slide(Win<R, NCH> &s, const Frame<R> &fr, const R *co
 // d01 (when use_d01) is the directly smoothed r0 - r1: it settles tweeter
 // against midrange where r0 and r1 round to the same value.
 template <typename R>
-__device__ inline R choose_span(const double *spans, R r0, R r1, R r2, R res_woof, double alpha,
-                                R fallback, bool lim0, bool lim1, bool use_d01 = false,
-                                R d01 = R(0))
+__device__ inline R choose_span(const SpanK<R> &K, R r0, R r1, R r2, R res_woof, R fallback,
+                                bool lim0, bool lim1, bool use_d01 = false, R d01 = R(0))
 {
     R resmin = R(1.0e20), s = fallback;
     int k = -1;
-    if (r0 < resmin) { resmin = r0; s = (R)spans[0]; k = 0; }
+    if (r0 < resmin) { resmin = r0; s = K.s0; k = 0; }
     const bool mid_wins = (use_d01 && k == 0 && r1 < R(1.0e20)) ? (d01 > R(0)) : (r1 < resmin);
-    if (mid_wins) { resmin = r1; s = (R)spans[1]; k = 1; }
-    if (r2 < resmin) { resmin = r2; s = (R)spans[2]; k = 2; }
+    if (mid_wins) { resmin = r1; s = K.s1; k = 1; }
+    if (r2 < resmin) { resmin = r2; s = K.s2; k = 2; }
     bool below = resmin < res_woof;
     if (sizeof(R) == 4 && !below && resmin == res_woof && ((k == 0 && lim0) || (k == 1 && lim1)))
         below = true;
-    if (alpha > 0.0 && alpha <= 10.0 && below && resmin > R(0)) {
-        R tmp = resmin / res_woof;
+    if (K.bass && below && resmin > R(0)) {
+        R tmp = fdiv(resmin, res_woof);
         if (tmp < R(1.0e-7)) tmp = R(1.0e-7);
-        const R ex = (R)(10.0 - alpha);
-        const R pw = (ex == R(1)) ? tmp : pow(tmp, ex);
-        s += ((R)spans[2] - s) * pw;
+        const R pw = (K.ex == R(1)) ? tmp : pow(tmp, K.ex);
+        s += (K.s2 - s) * pw;
     }
     return s;
 }
@@ -621,17 +745,16 @@ __device__ inline bool span_contested(R diff, R r0, R r1, float margin)
 }
 
 template <typename R>
-__device__ inline R interpolate_span(const double *spans, R s, R tw, R mid, R woof)
+__device__ inline R interpolate_span(const SpanK<R> &K, R s, R tw, R mid, R woof)
 {
-    const R s0 = (R)spans[0], s1 = (R)spans[1], s2 = (R)spans[2];
-    if (s <= s0) s = s0;
-    if (s >= s2) s = s2;
-    R f = s - s1;
+    if (s <= K.s0) s = K.s0;
+    if (s >= K.s2) s = K.s2;
+    R f = s - K.s1;
     if (f < R(0)) {
-        f /= s0 - s1;
+        f = (sizeof(R) == 8) ? f / (K.s0 - K.s1) : f * K.inv01;
         return (R(1) - f) * mid + f * tw;
     }
-    f /= s2 - s1;
+    f = (sizeof(R) == 8) ? f / (K.s2 - K.s1) : f * K.inv21;
     return (R(1) - f) * mid + f * woof;
 }
 
@@ -828,6 +951,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
     const int h1 = half_width(n, a.spans[1]);
     const int h2 = half_width(n, a.spans[2]);
     const bool lim0 = h0 != h2, lim1 = h1 != h2;
+    const SpanK<R> K = span_consts<R>(a.spans, a.alpha);
 
     // ---- chunks: contiguous centre ranges that never split a run of ties ----
     {
@@ -856,12 +980,17 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
 
     KSum<R> chi2;
     bool near = false;
+    const R rf = (R)a.refit_frac;
 
     if (VARIANT == VAR_SP) {
         // one sweep, three windows on y, generalized validation (Sec. 3)
         const R *vy[1] = {fr.Y};
         channel_aggregates<R, 1>(fr, sm, vy);
         __syncthreads();
+        if (G >= kGroupMinThreads) {
+            group_aggregates<R, 1>(fr, sm, n);
+            __syncthreads();
+        }
         const int lane = tid & 31;
         const int len = c1 - c0;
         // warp-uniform trip count: contested centres are settled by the warp
@@ -873,6 +1002,10 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
             win_init<R, 1>(w2, fr, sm, vy, c0, h2, n, o);
         }
         const R m0 = (R)(2 * h0 + 1), m1 = (R)(2 * h1 + 1), m2 = (R)(2 * h2 + 1);
+        // 1 / (1 - nu/m) for a line (nu = 2) and a constant (nu = 1)
+        const R gl0 = R(1) / (R(1) - R(2) / m0), gc0 = R(1) / (R(1) - R(1) / m0);
+        const R gl1 = R(1) / (R(1) - R(2) / m1), gc1 = R(1) / (R(1) - R(1) / m1);
+        const R gl2 = R(1) / (R(1) - R(2) / m2), gc2 = R(1) / (R(1) - R(1) / m2);
         const double *y64 = a.yc64 ? a.yc64 + base : nullptr;
         const double *w64 = a.wv64 ? a.wv64 + base : nullptr;
         double vsm64 = 0.0;
@@ -894,27 +1027,48 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
             R val[1] = {R(0)};
             bool contested = false;
             R s0 = R(0), s1 = R(0), s2 = R(0), g2 = R(0);
-            bool sl0 = false, sl1 = false;
+            bool sl0 = false, sl1 = false, sl2 = false;
             if (act) {
                 Fit<R, 1> f0, f1, f2;
-                win_fit_checked<R, 1>(f0, w0, fr, vy, j, h0, n, o, vsmlsq, near);
-                win_fit_checked<R, 1>(f1, w1, fr, vy, j, h1, n, o, vsmlsq, near);
-                win_fit_checked<R, 1>(f2, w2, fr, vy, j, h2, n, o, vsmlsq, near);
+                win_fit_checked<R, 1>(f0, w0, fr, vy, j, h0, n, o, vsmlsq, near, rf);
+                win_fit_checked<R, 1>(f1, w1, fr, vy, j, h1, n, o, vsmlsq, near, rf);
+                win_fit_checked<R, 1>(f2, w2, fr, vy, j, h2, n, o, vsmlsq, near, rf);
                 const R yj = fr.Y[j];
                 s0 = f0.s[0];
                 s1 = f1.s[0];
                 s2 = f2.s[0];
                 sl0 = f0.slope;
                 sl1 = f1.slope;
-                const R g0 = fabs(yj - s0) / (R(1) - (f0.slope ? R(2) : R(1)) / m0);
-                const R g1 = fabs(yj - s1) / (R(1) - (f1.slope ? R(2) : R(1)) / m1);
-                g2 = fabs(yj - s2) / (R(1) - (f2.slope ? R(2) : R(1)) / m2);
-                const R sp = choose_span<R>(a.spans, g0, g1, g2, g2, a.alpha, (R)a.spans[2],
-                                            lim0, lim1);
-                val[0] = interpolate_span<R>(a.spans, sp, s0, s1, s2);
+                sl2 = f2.slope;
+                const R g0 = fabs(yj - s0) * (f0.slope ? gl0 : gc0);
+                const R g1 = fabs(yj - s1) * (f1.slope ? gl1 : gc1);
+                g2 = fabs(yj - s2) * (f2.slope ? gl2 : gc2);
+                const R sp = choose_span<R>(K, g0, g1, g2, g2, K.s2, lim0, lim1);
+                val[0] = interpolate_span<R>(K, sp, s0, s1, s2);
                 if (sizeof(R) == 4 && y64) {
                     const R scale = fmax(fmax(fabs(yj), fabs(s0)), fabs(s1));
                     contested = fabs(g0 - g1) <= (R)a.near_sp * (R)1.1920929e-7 * scale;
+                    // bound on the power change from the FP32 error of the
+                    // residuals through bass enhancement and interpolation:
+                    // each residual's error is its slope times the rounding
+                    // of X plus the sums' rounding at the magnitude scale
+                    const R gm = fmin(g0, g1);
+                    if (!contested && K.bass && gm < g2 && gm > R(0)) {
+                        const R eps = (R)1.1920929e-7;
+                        const R ul = (R)a.sens_ulps;
+                        const R ge = (gm == g0) ? (fabs(f0.b[0]) * eps + ul * eps * scale) * (sl0 ? gl0 : gc0)
+                                                : (fabs(f1.b[0]) * eps + ul * eps * scale) * (sl1 ? gl1 : gc1);
+                        const R sc2 = fmax(fabs(yj), fabs(s2));
+                        const R we = (fabs(f2.b[0]) * eps + ul * eps * sc2) * (sl2 ? gl2 : gc2);
+                        const R tmp = gm / g2;
+                        const R sk = (gm == g0) ? K.s0 : K.s1;
+                        const R sp_ = sp;
+                        const R dvds = (sp_ - K.s1 < R(0)) ? fabs(s0 - s1) * (-K.inv01)
+                                                           : fabs(s2 - s1) * K.inv21;
+                        const double E = 2.0 * (double)fr.WT[j] * fabs((double)(yj - val[0])) *
+                                         (double)((K.s2 - sk) * dvds * tmp * (ge / gm + we / g2));
+                        if (E > a.sens_tau * a.chi0[obj]) contested = true;
+                    }
                 }
             }
             unsigned todo = __ballot_sync(0xffffffffu, contested);
@@ -926,16 +1080,18 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
                 const double xe = (double)(((uint64_t)fr.key[pe] << 32) | fr.klo[pe]) * 5.421010862427522e-20;
                 const double t0 = warp_fit_fp64<R>(fr, y64, w64, je, h0, n, vsm64, xe);
                 const double t1 = warp_fit_fp64<R>(fr, y64, w64, je, h1, n, vsm64, xe);
+                const double t2 = warp_fit_fp64<R>(fr, y64, w64, je, h2, n, vsm64, xe);
                 if (lane == src) {
-                    // the choice in binary64; the woofer's residual stays FP32
-                    // (near it the choice is continuous)
+                    // the choice and the fit in binary64 from exact inputs
                     const double ye = y64[pe];
                     const double d0 = 1.0 - (sl0 ? 2.0 : 1.0) / (double)m0;
                     const double d1 = 1.0 - (sl1 ? 2.0 : 1.0) / (double)m1;
+                    const double d2 = 1.0 - (sl2 ? 2.0 : 1.0) / (double)m2;
                     const double e0 = fabs(ye - t0) / d0, e1 = fabs(ye - t1) / d1;
-                    const double sp = choose_span<double>(a.spans, e0, e1, (double)g2, (double)g2,
-                                                          a.alpha, a.spans[2], lim0, lim1);
-                    val[0] = (R)interpolate_span<double>(a.spans, sp, t0, t1, (double)s2);
+                    const double e2 = fabs(ye - t2) / d2;
+                    const SpanK<double> K64 = span_consts<double>(a.spans, a.alpha);
+                    const double sp = choose_span<double>(K64, e0, e1, e2, e2, K64.s2, lim0, lim1);
+                    val[0] = (R)interpolate_span<double>(K64, sp, t0, t1, t2);
                 }
             }
             if (act) {
@@ -959,6 +1115,10 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
         const R *vy[1] = {fr.Y};
         channel_aggregates<R, 1>(fr, sm, vy);
         __syncthreads();
+        if (G >= kGroupMinThreads) {
+            group_aggregates<R, 1>(fr, sm, n);
+            __syncthreads();
+        }
         if (c0 < c1) {
             Win<R, 1> w0, w1, w2;
             win_init<R, 1>(w0, fr, sm, vy, c0, h0, n, o);
@@ -973,18 +1133,18 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
             };
             for (int j = c0; j < c1; ++j) {
                 Fit<R, 1> f0, f1, f2;
-                win_fit_checked<R, 1>(f0, w0, fr, vy, j, h0, n, o, vsmlsq, near);
-                win_fit_checked<R, 1>(f1, w1, fr, vy, j, h1, n, o, vsmlsq, near);
-                win_fit_checked<R, 1>(f2, w2, fr, vy, j, h2, n, o, vsmlsq, near);
+                win_fit_checked<R, 1>(f0, w0, fr, vy, j, h0, n, o, vsmlsq, near, rf);
+                win_fit_checked<R, 1>(f1, w1, fr, vy, j, h1, n, o, vsmlsq, near, rf);
+                win_fit_checked<R, 1>(f2, w2, fr, vy, j, h2, n, o, vsmlsq, near, rf);
                 const R yj = fr.Y[j], wj = fr.WT[j];
                 const R d0 = R(1) - wj * (f0.rW + f0.dxj * f0.dxj * f0.rS);
                 const R d1 = R(1) - wj * (f1.rW + f1.dxj * f1.dxj * f1.rS);
                 const R d2 = R(1) - wj * (f2.rW + f2.dxj * f2.dxj * f2.rS);
                 if (sizeof(R) == 4 && fmin(fmin(fabs(d0), fabs(d1)), fabs(d2)) < (R)kNearLev)
                     near = true;
-                fr.C[1][j] = d0 > R(0) ? fabs(yj - f0.s[0]) / d0 : R(-1);
-                fr.C[3][j] = d1 > R(0) ? fabs(yj - f1.s[0]) / d1 : R(-1);
-                fr.C[5][j] = d2 > R(0) ? fabs(yj - f2.s[0]) / d2 : R(-1);
+                fr.C[1][j] = d0 > R(0) ? fdiv(fabs(yj - f0.s[0]), d0) : R(-1);
+                fr.C[3][j] = d1 > R(0) ? fdiv(fabs(yj - f1.s[0]), d1) : R(-1);
+                fr.C[5][j] = d2 > R(0) ? fdiv(fabs(yj - f2.s[0]), d2) : R(-1);
                 const R val[3] = {f0.s[0], f1.s[0], f2.s[0]};
                 run_push<R, 3>(ra, fr, j, ties, val, emit);
                 if (j + 1 < c1) {
@@ -1021,6 +1181,10 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
         const float margin = a.near_ss * fminf(1.f, 256.f / (float)n) * fminf(1.f, 512.f / (float)n);
         channel_aggregates<R, NB, DIFF>(fr, sm, vr);
         __syncthreads();
+        if (G >= kGroupMinThreads) {
+            group_aggregates<R, NB>(fr, sm, n);
+            __syncthreads();
+        }
         if (c0 < c1) {
             Win<R, NB> w1;
             win_init<R, NB, DIFF>(w1, fr, sm, vr, c0, h1, n, o);
@@ -1031,12 +1195,12 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
                 if (span_contested(d01, v[0], v[1], margin)) near = true;
                 // when no residual is below 1e20 the span column keeps the
                 // woofer's CV residual, as Listing 1's column 6 does
-                fr.C[6][i] = choose_span<R>(a.spans, v[0], v[1], v[2], v[2], a.alpha, fr.C[5][i],
-                                            lim0, lim1, DIFF, d01);
+                fr.C[6][i] = choose_span<R>(K, v[0], v[1], v[2], v[2], fr.C[5][i], lim0, lim1,
+                                            DIFF, d01);
             };
             for (int j = c0; j < c1; ++j) {
                 Fit<R, NB> f1;
-                win_fit_checked<R, NB, DIFF>(f1, w1, fr, vr, j, h1, n, o, vsmlsq, near);
+                win_fit_checked<R, NB, DIFF>(f1, w1, fr, vr, j, h1, n, o, vsmlsq, near, rf);
                 R val[NB];
 #pragma unroll
                 for (int c = 0; c < NB; ++c) val[c] = f1.s[c];
@@ -1052,17 +1216,21 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
         const R *vs[1] = {fr.C[6]};
         channel_aggregates<R, 1>(fr, sm, vs);
         __syncthreads();
+        if (G >= kGroupMinThreads) {
+            group_aggregates<R, 1>(fr, sm, n);
+            __syncthreads();
+        }
         if (c0 < c1) {
             Win<R, 1> w1;
             win_init<R, 1>(w1, fr, sm, vs, c0, h1, n, o);
             RunAvg<R, 1> ra;
             ra.reset(c0);
             auto emit = [&](int i, const R (&v)[1]) {
-                fr.C[1][i] = interpolate_span<R>(a.spans, v[0], fr.C[0][i], fr.C[2][i], fr.C[4][i]);
+                fr.C[1][i] = interpolate_span<R>(K, v[0], fr.C[0][i], fr.C[2][i], fr.C[4][i]);
             };
             for (int j = c0; j < c1; ++j) {
                 Fit<R, 1> f1;
-                win_fit_checked<R, 1>(f1, w1, fr, vs, j, h1, n, o, vsmlsq, near);
+                win_fit_checked<R, 1>(f1, w1, fr, vs, j, h1, n, o, vsmlsq, near, rf);
                 const R val[1] = {f1.s[0]};
                 run_push<R, 1>(ra, fr, j, ties, val, emit);
                 if (j + 1 < c1) win_slide<R, 1>(w1, fr, vs, j, h1, n, o);
@@ -1076,6 +1244,10 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
         const R *vv[1] = {fr.C[1]};
         channel_aggregates<R, 1>(fr, sm, vv);
         __syncthreads();
+        if (G >= kGroupMinThreads) {
+            group_aggregates<R, 1>(fr, sm, n);
+            __syncthreads();
+        }
         if (c0 < c1) {
             Win<R, 1> w0;
             win_init<R, 1>(w0, fr, sm, vv, c0, h0, n, o);
@@ -1087,7 +1259,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
             };
             for (int j = c0; j < c1; ++j) {
                 Fit<R, 1> f0;
-                win_fit_checked<R, 1>(f0, w0, fr, vv, j, h0, n, o, vsmlsq, near);
+                win_fit_checked<R, 1>(f0, w0, fr, vv, j, h0, n, o, vsmlsq, near, rf);
                 const R val[1] = {f0.s[0]};
                 run_push<R, 1>(ra, fr, j, ties, val, emit);
                 if (j + 1 < c1) win_slide<R, 1>(w0, fr, vv, j, h0, n, o);
@@ -1123,7 +1295,7 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
         const int4 item = a.items[it];
         const int o = item.x;
         const int n = (int)(a.off[o + 1] - a.off[o]);
-        const Frame<R> fr = carve_frame<R>(big, n);
+        const Frame<R> fr = carve_frame<R>(big, n, VARIANT);
         const bool bad = a.bad[o] != 0;
         for (int q = item.y; q < item.z; ++q) {
             const int64_t at = (int64_t)o * a.n_freq + q;

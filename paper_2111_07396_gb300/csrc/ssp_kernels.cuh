@@ -168,5 +168,5 @@ __global__ void __launch_bounds__(256) argmax_kernel(ArgmaxArgs a)
         return cudaGetLastError();                                                            \
     }                                                                                         \
     size_t pgram_small_bytes_##PREC(int G) { return small_bytes<R>(G); }                      \
-    size_t pgram_frame_bytes_##PREC(int n) { return frame_bytes<R>(n); }                      \
+    size_t pgram_frame_bytes_##PREC(int n, int variant) { return frame_bytes<R>(n, variant); }                      \
     }

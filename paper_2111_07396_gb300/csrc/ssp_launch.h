@@ -37,6 +37,6 @@ cudaError_t pgram_launch(int precision, int variant, bool gmem, int grid, int G,
                          const PgramArgs &a, cudaStream_t s);
 
 size_t pgram_small_bytes(int precision, int G);
-size_t pgram_frame_bytes(int precision, int n);
+size_t pgram_frame_bytes(int precision, int n, int variant);
 
 }  // namespace ssp
