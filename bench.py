@@ -345,7 +345,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": desc, "e2e": e2e,
-            "gpu_launches": 6 * args.steps, "roofline": roof, "clocks": clocks,
+            "gpu_launches": sum(v[0] for v in prof.values()), "roofline": roof, "clocks": clocks,
             "breakdown_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
             "per_variant_ptf_s": {"ss": ptf_step / 2 / (ss_ms / ss_launches / 1e3),
                                   "sp": ptf_step / 2 / (sp_ms / sp_launches / 1e3)},

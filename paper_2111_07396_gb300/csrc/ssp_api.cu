@@ -22,12 +22,16 @@ cudaError_t argmax_launch_fp32(const ArgmaxArgs &, int, cudaStream_t);
 cudaError_t argmax_launch_fp64(const ArgmaxArgs &, int, cudaStream_t);
 cudaError_t pgram_occupancy_fp32(int, bool, int, size_t, int *);
 cudaError_t pgram_occupancy_fp64(int, bool, int, size_t, int *);
+cudaError_t pgram_occupancy_redo(int, bool, int, size_t, int *);
 cudaError_t pgram_launch_fp32(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
 cudaError_t pgram_launch_fp64(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
-size_t pgram_small_bytes_fp32(int);
-size_t pgram_small_bytes_fp64(int);
+cudaError_t pgram_launch_redo(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+size_t pgram_small_bytes_fp32(int, int);
+size_t pgram_small_bytes_fp64(int, int);
+size_t pgram_small_bytes_redo(int, int);
 size_t pgram_frame_bytes_fp32(int, int);
 size_t pgram_frame_bytes_fp64(int, int);
+size_t pgram_frame_bytes_redo(int, int);
 
 cudaError_t prep_launch(int p, const PrepArgs &a, int n, cudaStream_t s)
 {
@@ -40,21 +44,27 @@ cudaError_t argmax_launch(int p, const ArgmaxArgs &a, int n, cudaStream_t s)
 cudaError_t pgram_occupancy(int p, int v, bool g, int G, size_t smem, int *bps)
 {
     return p == SSP_FP64 ? pgram_occupancy_fp64(v, g, G, smem, bps)
-                         : pgram_occupancy_fp32(v, g, G, smem, bps);
+         : p == kPrecRedo ? pgram_occupancy_redo(v, g, G, smem, bps)
+                          : pgram_occupancy_fp32(v, g, G, smem, bps);
 }
 cudaError_t pgram_launch(int p, int v, bool g, int grid, int G, size_t smem, const PgramArgs &a,
                          cudaStream_t s)
 {
     return p == SSP_FP64 ? pgram_launch_fp64(v, g, grid, G, smem, a, s)
-                         : pgram_launch_fp32(v, g, grid, G, smem, a, s);
+         : p == kPrecRedo ? pgram_launch_redo(v, g, grid, G, smem, a, s)
+                          : pgram_launch_fp32(v, g, grid, G, smem, a, s);
 }
-size_t pgram_small_bytes(int p, int G)
+size_t pgram_small_bytes(int p, int G, int variant)
 {
-    return p == SSP_FP64 ? pgram_small_bytes_fp64(G) : pgram_small_bytes_fp32(G);
+    return p == SSP_FP64 ? pgram_small_bytes_fp64(G, variant)
+         : p == kPrecRedo ? pgram_small_bytes_redo(G, variant)
+                          : pgram_small_bytes_fp32(G, variant);
 }
 size_t pgram_frame_bytes(int p, int n, int variant)
 {
-    return p == SSP_FP64 ? pgram_frame_bytes_fp64(n, variant) : pgram_frame_bytes_fp32(n, variant);
+    return p == SSP_FP64 ? pgram_frame_bytes_fp64(n, variant)
+         : p == kPrecRedo ? pgram_frame_bytes_redo(n, variant)
+                          : pgram_frame_bytes_fp32(n, variant);
 }
 }  // namespace ssp
 
@@ -183,7 +193,7 @@ int device_limits(int *num_sms, size_t *max_smem)
 int configure(int precision, int variant, int G, int n_max, int sms, size_t max_smem,
               LaunchCfg &c)
 {
-    const size_t small = align16(pgram_small_bytes(precision, G));
+    const size_t small = align16(pgram_small_bytes(precision, G, variant));
     const size_t frame = align16(pgram_frame_bytes(precision, n_max, variant));
     c.gmem = small + frame + 1024 > max_smem;
     c.smem = c.gmem ? small : small + frame;
@@ -223,7 +233,7 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
         rc = configure(precision, variant, b.G, b.n_max, sms, max_smem, b.main);
         if (rc) return rc;
         if (plan.redo) {
-            rc = configure(SSP_FP64, variant, b.G, b.n_max, sms, max_smem, b.redo);
+            rc = configure(kPrecRedo, variant, b.G, b.n_max, sms, max_smem, b.redo);
             if (rc) return rc;
         }
         const int resident = b.main.grid;
@@ -440,7 +450,7 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
                 ga.recompute = 1;
                 slab_cur += b.redo.gmem ? b.redo.slab_bytes * (size_t)b.redo.grid : 0;
                 on = prof_begin(SSP_PHASE_REDO, s, mk);
-                if ((e = pgram_launch(SSP_FP64, (int)variant, b.redo.gmem, b.redo.grid, b.G,
+                if ((e = pgram_launch(kPrecRedo, (int)variant, b.redo.gmem, b.redo.grid, b.G,
                                       b.redo.smem, ga, s)))
                     break;
                 prof_end(on, mk, s);
@@ -600,7 +610,7 @@ int run_device_noalloc(const double *t, const double *y, const double *dy, const
                 ga.wv = d_wv64;
                 ga.item_counter = d_counters + 2 * k + 1;
                 ga.recompute = 1;
-                if ((e = pgram_launch(SSP_FP64, (int)variant, false, b.redo.grid, b.G, b.redo.smem,
+                if ((e = pgram_launch(kPrecRedo, (int)variant, false, b.redo.grid, b.G, b.redo.smem,
                                       ga, s)))
                     break;
             }

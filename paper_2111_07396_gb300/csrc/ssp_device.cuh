@@ -35,7 +35,6 @@ namespace ssp {
 enum { VAR_SS = 0, VAR_SP = 1 };
 constexpr int kMaxThreads = 512;
 constexpr int kBucketRankMax = 64;   // larger buckets switch to the bitonic sort
-constexpr int kGroupMinThreads = 128;  // CTAs this large also merge groups of 8 chunks
 
 // FP32C decisions closer than these margins to their thresholds are re-taken
 // in FP64: the frequency is flagged and recomputed by the FP64 kernel.
@@ -177,51 +176,127 @@ __device__ inline Frame<R> carve_frame(unsigned char *base, int n, int variant)
     return f;
 }
 
-// per-thread chunk table and block-reduction scratch (always shared memory)
-template <typename R>
-struct Small {
-    int *cs;                // [G + 1] chunk starts
-    R *org, *aW, *aA, *aB;  // [G] chunk origin and x-moments
-    R *aC, *aD;             // [4][G] channel moments
-    R *qorg, *qW, *qA, *qB; // [G/8] moments of groups of 8 chunks
-    R *qC, *qD;             // [4][G/8]
-    double *red;            // [32] reduction scratch
-    int *ired;              // [32]
-    int *flags;             // [4]
+// ---------------------------------------------------------------------------
+// extended-precision accumulator for the window prefixes: an unevaluated sum
+// hi + lo of two numbers of the working type (double-float, ~48 bits, on the
+// FP32 path; double-double, ~104 bits, on the FP64 path), added with Knuth's
+// two-sum and multiplied with an FMA-exact product (Dekker's error-free
+// transformations)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct xacc {
+    T hi, lo;
 };
-
-template <typename R>
-__host__ __device__ inline size_t small_bytes(int G)
+typedef xacc<float> df;
+typedef xacc<double> dd;
+__device__ inline float fma_x(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ inline double fma_x(double a, double b, double c) { return fma(a, b, c); }
+template <typename T>
+__device__ inline xacc<T> x_two_sum(T a, T b)
 {
-    return align16(4 * (size_t)(G + 1)) + align16(sizeof(R) * (size_t)G) * 4 +
-           align16(sizeof(R) * 4 * (size_t)G) * 2 + align16(sizeof(R) * (size_t)(G / 8)) * 4 +
-           align16(sizeof(R) * 4 * (size_t)(G / 8)) * 2 + 32 * 8 + 32 * 4 + 16;
+    const T s = a + b;
+    const T bb = s - a;
+    return xacc<T>{s, (a - (s - bb)) + (b - bb)};
+}
+template <typename T>
+__device__ inline xacc<T> x_fast(T a, T b)
+{
+    const T s = a + b;
+    return xacc<T>{s, b - (s - a)};
+}
+template <typename T>
+__device__ inline xacc<T> acc_add(xacc<T> x, xacc<T> y)
+{
+    xacc<T> s = x_two_sum(x.hi, y.hi);
+    s.lo += x.lo + y.lo;
+    return x_fast(s.hi, s.lo);
+}
+template <typename T>
+__device__ inline xacc<T> acc_neg(xacc<T> x) { return xacc<T>{-x.hi, -x.lo}; }
+template <typename T>
+__device__ inline xacc<T> acc_mul(xacc<T> x, T b)
+{
+    const T p = x.hi * b;
+    const T e = fma_x(x.hi, b, -p);
+    return x_fast(p, fma_x(x.lo, b, e));
+}
+template <typename T>
+__device__ inline T acc_to(xacc<T> x) { return x.hi + x.lo; }
+template <typename T>
+__device__ inline xacc<T> acc_shfl_up(xacc<T> x, int k)
+{
+    return xacc<T>{__shfl_up_sync(0xffffffffu, x.hi, k), __shfl_up_sync(0xffffffffu, x.lo, k)};
 }
 
-template <typename R>
-__device__ inline Small<R> carve_small(unsigned char *base, int G)
+// plain accumulator (the FP64 recompute of flagged FP32C frequencies, whose
+// results only have to meet the FP32C tolerance)
+__device__ inline double acc_add(double x, double y) { return x + y; }
+__device__ inline double acc_neg(double x) { return -x; }
+__device__ inline double acc_mul(double x, double b) { return x * b; }
+__device__ inline double acc_to(double x) { return x; }
+__device__ inline double acc_shfl_up(double x, int k) { return __shfl_up_sync(0xffffffffu, x, k); }
+
+// smallest window B / total weight whose prefix-based sums keep the accuracy
+// stated in win_init
+template <typename A> __device__ constexpr double acc_keep();
+template <> __device__ constexpr double acc_keep<xacc<float> >() { return 16.0 / 16777216.0; }
+template <> __device__ constexpr double acc_keep<xacc<double> >() { return 16.0 / 17592186044416.0; }
+template <> __device__ constexpr double acc_keep<double>() { return 16.0 / 8388608.0; }
+
+// accumulator of a kernel: extended unless PLAIN
+template <typename R, bool PLAIN> struct AccSel { typedef xacc<R> T; };
+template <typename R> struct AccSel<R, true> { typedef R T; };
+template <typename A> struct R_of { typedef A type; };
+template <typename T> struct R_of<xacc<T> > { typedef T type; };
+template <typename A> struct AccFrom {
+    __device__ static A get(typename R_of<A>::type a) { return A{a, typename R_of<A>::type(0)}; }
+};
+template <> struct AccFrom<double> {
+    __device__ static double get(double a) { return a; }
+};
+template <typename A>
+__device__ inline A acc_from(typename R_of<A>::type a) { return AccFrom<A>::get(a); }
+
+// per-frequency chunk table, window prefixes and reduction scratch (always
+// shared memory).  px: exclusive prefixes over chunks of the raw moments
+// sum w, sum w x, sum w x^2 (x about 0); pc: per channel sum w v and
+// sum w x v.  Entry u is the sum over chunks 0..u-1; entry G the total.
+template <typename R, typename A>
+struct Small {
+    int *cs;       // [G + 1] chunk starts
+    A *px;         // [3][G + 1]
+    A *pc;         // [2 * nch][G + 1]
+    A *scan;       // [16][8] warp totals of a scan
+    double *red;   // [32] reduction scratch
+    int *ired;     // [32]
+    int *flags;    // [4]
+};
+
+// channels a variant smooths at once: SS pass B smooths three residual
+// columns and their difference; SP only y
+__host__ __device__ inline int max_channels(int variant) { return variant == VAR_SP ? 1 : 4; }
+
+template <typename A>
+__host__ __device__ inline size_t small_bytes(int G, int variant)
 {
-    Small<R> s;
-    size_t g = align16(sizeof(R) * (size_t)G), g3 = align16(sizeof(R) * 4 * (size_t)G);
+    const size_t a = sizeof(A);
+    return align16(4 * (size_t)(G + 1)) + align16(a * 3 * (size_t)(G + 1)) +
+           align16(a * 2 * (size_t)max_channels(variant) * (size_t)(G + 1)) + 16 * 8 * a +
+           32 * 8 + 32 * 4 + 16;
+}
+
+template <typename R, typename A>
+__device__ inline Small<R, A> carve_small(unsigned char *base, int G, int variant)
+{
+    Small<R, A> s;
     s.cs = (int *)base;
     base += align16(4 * (size_t)(G + 1));
-    s.org = (R *)base;
-    s.aW = (R *)(base + g);
-    s.aA = (R *)(base + 2 * g);
-    s.aB = (R *)(base + 3 * g);
-    base += 4 * g;
-    s.aC = (R *)base;
-    s.aD = (R *)(base + g3);
-    base += 2 * g3;
-    const size_t q = align16(sizeof(R) * (size_t)(G / 8)), q4 = align16(sizeof(R) * 4 * (size_t)(G / 8));
-    s.qorg = (R *)base;
-    s.qW = (R *)(base + q);
-    s.qA = (R *)(base + 2 * q);
-    s.qB = (R *)(base + 3 * q);
-    base += 4 * q;
-    s.qC = (R *)base;
-    s.qD = (R *)(base + q4);
-    base += 2 * q4;
+    s.px = (A *)base;
+    base += align16(sizeof(A) * 3 * (size_t)(G + 1));
+    s.pc = (A *)base;
+    base += align16(sizeof(A) * 2 * (size_t)max_channels(variant) * (size_t)(G + 1));
+    s.scan = (A *)base;
+    base += 16 * 8 * sizeof(A);
     s.red = (double *)base;
     s.ired = (int *)(base + 256);
     s.flags = (int *)(base + 256 + 128);
@@ -342,8 +417,8 @@ __device__ void bitonic_argsort(const Frame<R> &fr, int n)
     }
 }
 
-template <typename R>
-__device__ void argsort_phases(const Frame<R> &fr, int n, const Small<R> &sm)
+template <typename R, typename A>
+__device__ void argsort_phases(const Frame<R> &fr, int n, const Small<R, A> &sm)
 {
     const int tid = threadIdx.x, G = blockDim.x;
     const int nb = bucket_count(n);
@@ -455,134 +530,191 @@ __device__ inline void win_add(Win<R, NCH> &s, const Frame<R> &fr, const R *cons
     }
 }
 
-// last chunk u with cs[u] <= p (cs non-decreasing, cs[0] = 0 <= p < cs[G] = n)
-__device__ inline int find_chunk(const int *cs, int G, int p)
+// Exclusive block-wide scan of Q accumulator values per thread (one entry per
+// chunk): out[q * (G + 1) + t] = sum over threads < t, out[q * (G + 1) + G] =
+// total.
+template <typename A, int Q>
+__device__ void block_scan_store(A (&v)[Q], A *out, A *scratch)
 {
-    int lo = 0, hi = G - 1;
+    const int G = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = G >> 5;
+    A inc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) inc[q] = v[q];
+#pragma unroll
+    for (int k = 1; k < 32; k <<= 1) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const A y = acc_shfl_up(inc[q], k);
+            if (lane >= k) inc[q] = acc_add(inc[q], y);
+        }
+    }
+    __syncthreads();
+    if (lane == 31) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) scratch[warp * 8 + q] = inc[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        A base = acc_from<A>(typename R_of<A>::type(0));
+        for (int k = 0; k < warp; ++k) base = acc_add(base, scratch[k * 8 + q]);
+        A ex = acc_shfl_up(inc[q], 1);
+        if (lane == 0) ex = acc_from<A>(typename R_of<A>::type(0));
+        out[q * (G + 1) + tid] = acc_add(base, ex);
+        if (tid == G - 1) {
+            A tot = acc_from<A>(typename R_of<A>::type(0));
+            for (int k = 0; k < nw; ++k) tot = acc_add(tot, scratch[k * 8 + q]);
+            out[q * (G + 1) + G] = tot;
+        }
+    }
+}
+
+// x-moment prefixes of the chunks (once per frequency)
+template <typename R, typename A>
+__device__ void build_x_prefix(const Frame<R> &fr, const Small<R, A> &sm, int c0, int c1, R o)
+{
+    R w_ = R(0), a_ = R(0), b_ = R(0);
+    for (int j = c0; j < c1; ++j) {
+        const R w = fr.WT[j], d = fr.X[j] - o;
+        w_ += w;
+        a_ += w * d;
+        b_ += w * d * d;
+    }
+    // about 0: sum w x = a + o W, sum w x^2 = b + 2 o a + o^2 W
+    A v[3];
+    v[0] = acc_from<A>(w_);
+    v[1] = acc_add(acc_from<A>(a_), acc_mul(acc_from<A>(w_), o));
+    v[2] = acc_add(acc_add(acc_from<A>(b_), acc_mul(acc_from<A>(a_), R(2) * o)),
+                   acc_mul(acc_mul(acc_from<A>(w_), o), o));
+    block_scan_store<A, 3>(v, sm.px, sm.scan);
+}
+
+// channel prefixes of the chunks (each pass)
+template <typename R, int NCH, bool DIFF = false, typename A>
+__device__ void build_channel_prefix(const Frame<R> &fr, const Small<R, A> &sm, const R *const *vv,
+                                     int c0, int c1, R o)
+{
+    A v[2 * NCH];
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+        R sc = R(0), sd = R(0);
+        for (int j = c0; j < c1; ++j) {
+            const R wv = fr.WT[j] * chan<R, NCH, DIFF>(vv, ch, j);
+            sc += wv;
+            sd += wv * (fr.X[j] - o);
+        }
+        v[2 * ch] = acc_from<A>(sc);
+        v[2 * ch + 1] = acc_add(acc_from<A>(sd), acc_mul(acc_from<A>(sc), o));  // sum w x v about 0
+    }
+    block_scan_store<A, 2 * NCH>(v, sm.pc, sm.scan);
+}
+
+// first chunk starting at or after p / last boundary at or before p
+__device__ inline int chunk_lower(const int *cs, int G, int p)
+{
+    int lo = 0, hi = G;
     while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
+        const int mid = (lo + hi) >> 1;
+        if (cs[mid] < p) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+__device__ inline int chunk_upper(const int *cs, int G, int p)
+{
+    int lo = 0, hi = G;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
         if (cs[mid] <= p) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
 
-// Sums of the window [c - h, c + h] about origin o, from the moments of
-// whole groups of 8 chunks and of whole chunks lying inside the window, and
-// single points at the ragged ends.  Every merge only adds (no moment is
-// subtracted), so no cancellation enters here.
-template <typename R, int NCH, bool DIFF = false>
-__device__ void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R> &sm,
+// Sums of the window [c - h, c + h] about origin o.  Whole chunks come from
+// the extended-precision prefixes (raw moments about 0, shifted by -1/+1 for
+// the wrapped parts, then moved to origin o), the ragged ends point by point.
+template <typename R, int NCH, bool DIFF = false, typename A>
+__device__ void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R, A> &sm,
                          const R *const *v, int c, int h, int n, R o)
 {
-    const int G = blockDim.x;
+    const int G = blockDim.x, L = G + 1;
+    A W = acc_from<A>(R(0)), S1 = W, S2 = W, C[NCH], D[NCH];
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) C[ch] = D[ch] = W;
     s.zero();
-    int e = c - h;
-    const int e_end = c + h;
-    int sh;
-    int p = slot_point(e, n, sh);
-    int u = find_chunk(sm.cs, G, p);
-    while (e <= e_end) {
-        p = slot_point(e, n, sh);
-        if (p < sm.cs[u]) u = 0;                 // wrapped past n-1
-        while (sm.cs[u + 1] <= p) ++u;           // skips empty chunks
-        if (G >= kGroupMinThreads && (u & 7) == 0 && p == sm.cs[u]) {
-            const int U = u >> 3;
-            const int glen = sm.cs[u + 8] - sm.cs[u];
-            if (e + glen - 1 <= e_end) {
-                const R d = (sm.qorg[U] - o) + (R)sh;
-                const R qW = sm.qW[U], qA = sm.qA[U];
-                s.W += qW;
-                s.A += qA + d * qW;
-                s.B += sm.qB[U] + d * (R(2) * qA + d * qW);
-                if (sizeof(R) == 4) s.hiB = fmax(s.hiB, s.B);
+    // three segments of constant shift: slots before 0, inside, after n-1
+    const int ea = c - h, eb = c + h;
 #pragma unroll
-                for (int ch = 0; ch < NCH; ++ch) {
-                    const R cC = sm.qC[ch * (G / 8) + U];
-                    s.C[ch] += cC;
-                    s.D[ch] += sm.qD[ch * (G / 8) + U] + d * cC;
-                }
-                e += glen;
-                continue;
-            }
-        }
-        const int len = sm.cs[u + 1] - sm.cs[u];
-        if (p == sm.cs[u] && e + len - 1 <= e_end) {
-            const R d = (sm.org[u] - o) + (R)sh;
-            const R aW = sm.aW[u], aA = sm.aA[u];
-            s.W += aW;
-            s.A += aA + d * aW;
-            s.B += sm.aB[u] + d * (R(2) * aA + d * aW);
-            if (sizeof(R) == 4) s.hiB = fmax(s.hiB, s.B);
+    for (int seg = -1; seg <= 1; ++seg) {
+        int pa, pb;
+        if (seg < 0) { pa = ea + n; pb = n - 1; if (ea >= 0) continue; }
+        else if (seg == 0) { pa = ea < 0 ? 0 : ea; pb = eb >= n ? n - 1 : eb; }
+        else { pa = 0; pb = eb - n; if (eb < n) continue; }
+        const int ua = chunk_lower(sm.cs, G, pa);
+        const int ub = chunk_upper(sm.cs, G, pb + 1);
+        int q0 = pa, q1 = pb;   // points left to add one by one: [q0, ..) and (.., q1]
+        if (ua < ub) {
+            // chunks ua..ub-1 lie inside [pa, pb]
+            const A w = acc_add(sm.px[0 * L + ub], acc_neg(sm.px[0 * L + ua]));
+            A s1 = acc_add(sm.px[1 * L + ub], acc_neg(sm.px[1 * L + ua]));
+            A s2 = acc_add(sm.px[2 * L + ub], acc_neg(sm.px[2 * L + ua]));
+            A cc[NCH], dd[NCH];
 #pragma unroll
             for (int ch = 0; ch < NCH; ++ch) {
-                const R cC = sm.aC[ch * G + u];
-                s.C[ch] += cC;
-                s.D[ch] += sm.aD[ch * G + u] + d * cC;
+                cc[ch] = acc_add(sm.pc[(2 * ch) * L + ub], acc_neg(sm.pc[(2 * ch) * L + ua]));
+                dd[ch] = acc_add(sm.pc[(2 * ch + 1) * L + ub], acc_neg(sm.pc[(2 * ch + 1) * L + ua]));
             }
-            e += len;
+            if (seg != 0) {
+                // x -> x + seg: s2 += 2 seg s1 + W, s1 += seg W, D += seg C
+                const R sg = (R)seg;
+                s2 = acc_add(s2, acc_add(acc_mul(s1, R(2) * sg), w));
+                s1 = acc_add(s1, acc_mul(w, sg));
+#pragma unroll
+                for (int ch = 0; ch < NCH; ++ch) dd[ch] = acc_add(dd[ch], acc_mul(cc[ch], sg));
+            }
+            W = acc_add(W, w);
+            S1 = acc_add(S1, s1);
+            S2 = acc_add(S2, s2);
+#pragma unroll
+            for (int ch = 0; ch < NCH; ++ch) {
+                C[ch] = acc_add(C[ch], cc[ch]);
+                D[ch] = acc_add(D[ch], dd[ch]);
+            }
+            // ragged ends
+            const int fa = sm.cs[ua], fb = sm.cs[ub];
+            for (int p = pa; p < fa; ++p) win_add<R, NCH, DIFF>(s, fr, v, seg < 0 ? p - n : (seg > 0 ? p + n : p), n, o, R(1));
+            for (int p = fb; p <= pb; ++p) win_add<R, NCH, DIFF>(s, fr, v, seg < 0 ? p - n : (seg > 0 ? p + n : p), n, o, R(1));
         } else {
-            win_add<R, NCH, DIFF>(s, fr, v, e, n, o, R(1));
-            e += 1;
+            for (int p = q0; p <= q1; ++p) win_add<R, NCH, DIFF>(s, fr, v, seg < 0 ? p - n : (seg > 0 ? p + n : p), n, o, R(1));
         }
     }
-}
-
-// moments of groups of 8 chunks (about the group's first point), from the
-// chunk moments; threads 0..G/8-1 each build one group
-template <typename R, int NCH>
-__device__ void group_aggregates(const Frame<R> &fr, const Small<R> &sm, int n)
-{
-    const int G = blockDim.x, U = threadIdx.x;
-    if (G >= kGroupMinThreads && U < G / 8) {
-        const int u0 = 8 * U;
-        const R og = (sm.cs[u0] < n) ? fr.X[sm.cs[u0]] : R(0);
-        R W = R(0), A = R(0), B = R(0), C[NCH], D[NCH];
-#pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) C[ch] = D[ch] = R(0);
-        for (int u = u0; u < u0 + 8; ++u) {
-            if (sm.cs[u + 1] == sm.cs[u]) continue;
-            const R d = sm.org[u] - og;
-            const R aW = sm.aW[u], aA = sm.aA[u];
-            W += aW;
-            A += aA + d * aW;
-            B += sm.aB[u] + d * (R(2) * aA + d * aW);
-#pragma unroll
-            for (int ch = 0; ch < NCH; ++ch) {
-                const R cC = sm.aC[ch * G + u];
-                C[ch] += cC;
-                D[ch] += sm.aD[ch * G + u] + d * cC;
-            }
-        }
-        sm.qorg[U] = og;
-        sm.qW[U] = W;
-        sm.qA[U] = A;
-        sm.qB[U] = B;
-#pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) {
-            sm.qC[ch * (G / 8) + U] = C[ch];
-            sm.qD[ch * (G / 8) + U] = D[ch];
-        }
+    // about o: A = S1 - o W, B = S2 - 2 o S1 + o^2 W, D = D - o C
+    const A oW = acc_mul(W, o);
+    const R wr = acc_to(W);
+    const R ar = acc_to(acc_add(S1, acc_neg(oW)));
+    const R br = acc_to(acc_add(acc_add(S2, acc_neg(acc_mul(S1, R(2) * o))), acc_mul(oW, o)));
+    // Every prefix term is bounded by 16 x (total weight): |x| <= 2 after a
+    // wrap and |o| < 1.  The accumulator's rounding therefore leaves B with a
+    // relative error below eps_acc * 16 tW / B; where that could exceed about
+    // 2^-24 (double-float), 2^-56 (double-double) or 2^-30 (plain binary64,
+    // FP64 recompute) of B, the window is clustered so tightly that it is
+    // summed point by point about o instead.
+    const R tw = acc_to(sm.px[0 * L + G]);
+    const R keep = R(acc_keep<A>());
+    if (!(br > tw * keep)) {
+        s.zero();
+        for (int e = ea; e <= eb; ++e) win_add<R, NCH, DIFF>(s, fr, v, e, n, o, R(1));
+        return;
     }
-}
-
-// per-thread chunk aggregates of the channels (about the chunk origin)
-template <typename R, int NCH, bool DIFF = false>
-__device__ void channel_aggregates(const Frame<R> &fr, const Small<R> &sm, const R *const *v)
-{
-    const int tid = threadIdx.x, G = blockDim.x;
-    const int c0 = sm.cs[tid], c1 = sm.cs[tid + 1];
-    const R o = sm.org[tid];
+    s.W += wr;
+    s.A += ar;
+    s.B += br;
 #pragma unroll
     for (int ch = 0; ch < NCH; ++ch) {
-        R sc = R(0), sd = R(0);
-        for (int j = c0; j < c1; ++j) {
-            R wv = fr.WT[j] * chan<R, NCH, DIFF>(v, ch, j);
-            sc += wv;
-            sd += wv * (fr.X[j] - o);
-        }
-        sm.aC[ch * G + tid] = sc;
-        sm.aD[ch * G + tid] = sd;
+        s.C[ch] += acc_to(C[ch]);
+        s.D[ch] += acc_to(acc_add(D[ch], acc_neg(acc_mul(C[ch], o))));
     }
+    if (sizeof(R) == 4) s.hiB = fmax(s.hiB, s.B);
 }
 
 // the line fit of a window evaluated at the centre j
@@ -864,9 +996,9 @@ struct FreqResult {
 // ---------------------------------------------------------------------------
 // one (object, frequency)
 // ---------------------------------------------------------------------------
-template <typename R, int VARIANT>
+template <typename R, int VARIANT, typename A>
 __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, double f,
-                                        const Frame<R> &fr, const Small<R> &sm)
+                                        const Frame<R> &fr, const Small<R, A> &sm)
 {
     const int tid = threadIdx.x, G = blockDim.x;
     const int64_t base = a.off[obj];
@@ -964,19 +1096,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
     __syncthreads();
     const int c0 = sm.cs[tid], c1 = sm.cs[tid + 1];
     const R o = (c0 < c1) ? fr.X[c0] : R(0);
-    {
-        R w_ = R(0), a_ = R(0), b_ = R(0);
-        for (int j = c0; j < c1; ++j) {
-            const R w = fr.WT[j], d = fr.X[j] - o;
-            w_ += w;
-            a_ += w * d;
-            b_ += w * d * d;
-        }
-        sm.org[tid] = o;
-        sm.aW[tid] = w_;
-        sm.aA[tid] = a_;
-        sm.aB[tid] = b_;
-    }
+    build_x_prefix(fr, sm, c0, c1, o);
 
     KSum<R> chi2;
     bool near = false;
@@ -985,12 +1105,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
     if (VARIANT == VAR_SP) {
         // one sweep, three windows on y, generalized validation (Sec. 3)
         const R *vy[1] = {fr.Y};
-        channel_aggregates<R, 1>(fr, sm, vy);
+        build_channel_prefix<R, 1>(fr, sm, vy, c0, c1, o);
         __syncthreads();
-        if (G >= kGroupMinThreads) {
-            group_aggregates<R, 1>(fr, sm, n);
-            __syncthreads();
-        }
         const int lane = tid & 31;
         const int len = c1 - c0;
         // warp-uniform trip count: contested centres are settled by the warp
@@ -1113,12 +1229,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
     // whose leverage reached 1; resolved below).
     {
         const R *vy[1] = {fr.Y};
-        channel_aggregates<R, 1>(fr, sm, vy);
+        build_channel_prefix<R, 1>(fr, sm, vy, c0, c1, o);
         __syncthreads();
-        if (G >= kGroupMinThreads) {
-            group_aggregates<R, 1>(fr, sm, n);
-            __syncthreads();
-        }
         if (c0 < c1) {
             Win<R, 1> w0, w1, w2;
             win_init<R, 1>(w0, fr, sm, vy, c0, h0, n, o);
@@ -1179,12 +1291,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
         constexpr int NB = DIFF ? 4 : 3;
         const R *vr[3] = {fr.C[1], fr.C[3], fr.C[5]};
         const float margin = a.near_ss * fminf(1.f, 256.f / (float)n) * fminf(1.f, 512.f / (float)n);
-        channel_aggregates<R, NB, DIFF>(fr, sm, vr);
+        build_channel_prefix<R, NB, DIFF>(fr, sm, vr, c0, c1, o);
         __syncthreads();
-        if (G >= kGroupMinThreads) {
-            group_aggregates<R, NB>(fr, sm, n);
-            __syncthreads();
-        }
         if (c0 < c1) {
             Win<R, NB> w1;
             win_init<R, NB, DIFF>(w1, fr, sm, vr, c0, h1, n, o);
@@ -1214,12 +1322,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
     // pass C: midrange smooth of the chosen spans, clamp and interpolate -> C1
     {
         const R *vs[1] = {fr.C[6]};
-        channel_aggregates<R, 1>(fr, sm, vs);
+        build_channel_prefix<R, 1>(fr, sm, vs, c0, c1, o);
         __syncthreads();
-        if (G >= kGroupMinThreads) {
-            group_aggregates<R, 1>(fr, sm, n);
-            __syncthreads();
-        }
         if (c0 < c1) {
             Win<R, 1> w1;
             win_init<R, 1>(w1, fr, sm, vs, c0, h1, n, o);
@@ -1242,12 +1346,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
     // pass D: final tweeter smooth and chi2
     {
         const R *vv[1] = {fr.C[1]};
-        channel_aggregates<R, 1>(fr, sm, vv);
+        build_channel_prefix<R, 1>(fr, sm, vv, c0, c1, o);
         __syncthreads();
-        if (G >= kGroupMinThreads) {
-            group_aggregates<R, 1>(fr, sm, n);
-            __syncthreads();
-        }
         if (c0 < c1) {
             Win<R, 1> w0;
             win_init<R, 1>(w0, fr, sm, vv, c0, h0, n, o);
@@ -1277,15 +1377,16 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
 // FP32C launches flag frequencies whose decisions came within their margins;
 // the FP64 kernel's recompute launch then redoes exactly those frequencies
 // and overwrites their (float) power.
-template <typename R, int VARIANT, bool GMEM>
+template <typename R, int VARIANT, bool GMEM, bool PLAIN>
 __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
 {
+    typedef typename AccSel<R, PLAIN>::T A;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
     const int G = blockDim.x;
-    Small<R> sm = carve_small<R>(smem, G);
+    Small<R, A> sm = carve_small<R, A>(smem, G, VARIANT);
     unsigned char *big = GMEM ? a.slab + (size_t)blockIdx.x * a.slab_bytes
-                              : smem + align16(small_bytes<R>(G));
+                              : smem + align16(small_bytes<A>(G, VARIANT));
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(a.item_counter, 1);
         __syncthreads();

@@ -1,4 +1,5 @@
 // ssp_fp32.cu -- FP32C instantiation: exact fixed-point fold, FP32 smoothing
-// about local origins, compensated chi2.
+// about local origins from double-float window prefixes, compensated chi2.
 #include "ssp_kernels.cuh"
-SSP_INSTANTIATE(float, fp32)
+SSP_INSTANTIATE_PREP(float, fp32)
+SSP_INSTANTIATE_PGRAM(float, fp32, false)

@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(256) argmax_kernel(ArgmaxArgs a)
 
 }  // namespace ssp
 
-#define SSP_INSTANTIATE(R, PREC)                                                              \
+// prep and argmax kernels of one precision
+#define SSP_INSTANTIATE_PREP(R, PREC)                                                         \
     namespace ssp {                                                                           \
     cudaError_t prep_launch_##PREC(const PrepArgs &a, int n_obj, cudaStream_t s)              \
     {                                                                                         \
@@ -138,15 +139,20 @@ __global__ void __launch_bounds__(256) argmax_kernel(ArgmaxArgs a)
         argmax_kernel<R><<<n_obj, 256, 0, s>>>(a);                                            \
         return cudaGetLastError();                                                            \
     }                                                                                         \
+    }
+
+// periodogram kernels of one precision and accumulator
+#define SSP_INSTANTIATE_PGRAM(R, PREC, PLAIN)                                                 \
+    namespace ssp {                                                                           \
     template <int V, bool GM>                                                                 \
     static cudaError_t occ_##PREC(int G, size_t smem, int *bps)                               \
     {                                                                                         \
-        cudaError_t e = cudaFuncSetAttribute(pgram_kernel<R, V, GM>,                          \
+        cudaError_t e = cudaFuncSetAttribute(pgram_kernel<R, V, GM, PLAIN>,                   \
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                              (int)smem);                                      \
         if (e != cudaSuccess) return e;                                                       \
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, pgram_kernel<R, V, GM>, G,  \
-                                                             smem);                           \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                 \
+            bps, pgram_kernel<R, V, GM, PLAIN>, G, smem);                                     \
     }                                                                                         \
     cudaError_t pgram_occupancy_##PREC(int variant, bool gmem, int G, size_t smem, int *bps)  \
     {                                                                                         \
@@ -159,14 +165,17 @@ __global__ void __launch_bounds__(256) argmax_kernel(ArgmaxArgs a)
                                     const PgramArgs &a, cudaStream_t s)                       \
     {                                                                                         \
         if (variant == VAR_SS) {                                                              \
-            if (gmem) pgram_kernel<R, VAR_SS, true><<<grid, G, smem, s>>>(a);                 \
-            else pgram_kernel<R, VAR_SS, false><<<grid, G, smem, s>>>(a);                     \
+            if (gmem) pgram_kernel<R, VAR_SS, true, PLAIN><<<grid, G, smem, s>>>(a);          \
+            else pgram_kernel<R, VAR_SS, false, PLAIN><<<grid, G, smem, s>>>(a);              \
         } else {                                                                              \
-            if (gmem) pgram_kernel<R, VAR_SP, true><<<grid, G, smem, s>>>(a);                 \
-            else pgram_kernel<R, VAR_SP, false><<<grid, G, smem, s>>>(a);                     \
+            if (gmem) pgram_kernel<R, VAR_SP, true, PLAIN><<<grid, G, smem, s>>>(a);          \
+            else pgram_kernel<R, VAR_SP, false, PLAIN><<<grid, G, smem, s>>>(a);              \
         }                                                                                     \
         return cudaGetLastError();                                                            \
     }                                                                                         \
-    size_t pgram_small_bytes_##PREC(int G) { return small_bytes<R>(G); }                      \
-    size_t pgram_frame_bytes_##PREC(int n, int variant) { return frame_bytes<R>(n, variant); }                      \
+    size_t pgram_small_bytes_##PREC(int G, int variant)                                       \
+    {                                                                                         \
+        return small_bytes<typename AccSel<R, PLAIN>::T>(G, variant);                         \
+    }                                                                                         \
+    size_t pgram_frame_bytes_##PREC(int n, int variant) { return frame_bytes<R>(n, variant); } \
     }

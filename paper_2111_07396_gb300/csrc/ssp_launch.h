@@ -27,7 +27,9 @@ struct ArgmaxArgs {
     double *best_period;       // [n_obj]
 };
 
-// precision: 0 = FP64, 1 = FP32C
+// precision: 0 = FP64, 1 = FP32C, kPrecRedo = the FP64 recompute of flagged
+// FP32C frequencies (plain binary64 window prefixes)
+constexpr int kPrecRedo = 2;
 cudaError_t prep_launch(int precision, const PrepArgs &a, int n_obj, cudaStream_t s);
 cudaError_t argmax_launch(int precision, const ArgmaxArgs &a, int n_obj, cudaStream_t s);
 // sets the dynamic shared-memory limit and returns resident CTAs per SM
@@ -36,7 +38,7 @@ cudaError_t pgram_occupancy(int precision, int variant, bool gmem, int G, size_t
 cudaError_t pgram_launch(int precision, int variant, bool gmem, int grid, int G, size_t smem,
                          const PgramArgs &a, cudaStream_t s);
 
-size_t pgram_small_bytes(int precision, int G);
+size_t pgram_small_bytes(int precision, int G, int variant);
 size_t pgram_frame_bytes(int precision, int n, int variant);
 
 }  // namespace ssp
