@@ -135,27 +135,29 @@ int check_shape(const int64_t *n_per_object, int64_t n_objects, int64_t n_freq, 
 }
 
 // threads per CTA for an object of n points: about a dozen centres per thread
-// (SSP_GROUP_SCALE, a power of two, scales the choice for calibration)
-int group_size_base(int n);
+// (SSP_GROUP_SCALE, a power of two, scales the choice for calibration).  SS
+// objects above 2048 points take 512 threads: the SS frame of such an object
+// leaves room for one CTA per SM, and 16 warps hide more latency than 8.
+int group_size_base(int n, int variant);
 
-int group_size(int n)
+int group_size(int n, int variant)
 {
     static const int scale = [] {
         const char *e = std::getenv("SSP_GROUP_SCALE");
         const int v = e ? std::atoi(e) : 0;
         return (v == 2 || v == 4 || v == -2 || v == -4) ? v : 1;
     }();
-    int g = group_size_base(n);
+    int g = group_size_base(n, variant);
     if (scale > 1) g = std::min(512, g * scale);
     if (scale < 0) g = std::max(32, g / -scale);
     return g;
 }
-
-int group_size_base(int n)
+int group_size_base(int n, int variant)
 {
     if (n <= 384) return 32;
     if (n <= 768) return 64;
     if (n <= 1536) return 128;
+    if (variant == SSP_SS && n > 2048) return 512;
     return 256;
 }
 
@@ -221,7 +223,7 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
         Bucket b;
         b.G = G;
         for (int64_t o = 0; o < n_obj; ++o)
-            if (group_size((int)npo[o]) == G) {
+            if (group_size((int)npo[o], variant) == G) {
                 b.objects.push_back((int)o);
                 b.n_max = std::max(b.n_max, (int)npo[o]);
             }

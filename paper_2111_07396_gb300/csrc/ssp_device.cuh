@@ -390,7 +390,7 @@ __device__ inline bool key_less(const Frame<R> &fr, uint32_t i, uint32_t j)
 }
 
 template <typename R>
-__device__ void bitonic_argsort(const Frame<R> &fr, int n)
+__device__ __noinline__ void bitonic_argsort(const Frame<R> fr, int n)
 {
     const int tid = threadIdx.x, G = blockDim.x;
     const int np2 = pow2_at_least(n);
@@ -531,70 +531,96 @@ __device__ inline void win_add(Win<R, NCH> &s, const Frame<R> &fr, const R *cons
 }
 
 // Exclusive block-wide scan of Q accumulator values per thread (one entry per
-// chunk): out[q * (G + 1) + t] = sum over threads < t, out[q * (G + 1) + G] =
-// total.
+// chunk): out[q][t] = sum over threads < t, out[q][G] = total.  Warps scan
+// with shuffles; warp 0 then scans the warp totals, so no thread adds more
+// than log2(warps) of them.  The caller synchronises before reading out.
 template <typename A, int Q>
-__device__ void block_scan_store(A (&v)[Q], A *out, A *scratch)
+__device__ void block_scan_store(A (&v)[Q], A *const (&out)[Q], A *scratch)
 {
+    typedef typename R_of<A>::type T;
     const int G = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nw = G >> 5;
-    A inc[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) inc[q] = v[q];
 #pragma unroll
     for (int k = 1; k < 32; k <<= 1) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const A y = acc_shfl_up(inc[q], k);
-            if (lane >= k) inc[q] = acc_add(inc[q], y);
+            const A y = acc_shfl_up(v[q], k);
+            if (lane >= k) v[q] = acc_add(v[q], y);
         }
     }
-    __syncthreads();
-    if (lane == 31) {
-#pragma unroll
-        for (int q = 0; q < Q; ++q) scratch[warp * 8 + q] = inc[q];
-    }
-    __syncthreads();
+    A ex[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        A base = acc_from<A>(typename R_of<A>::type(0));
-        for (int k = 0; k < warp; ++k) base = acc_add(base, scratch[k * 8 + q]);
-        A ex = acc_shfl_up(inc[q], 1);
-        if (lane == 0) ex = acc_from<A>(typename R_of<A>::type(0));
-        out[q * (G + 1) + tid] = acc_add(base, ex);
-        if (tid == G - 1) {
-            A tot = acc_from<A>(typename R_of<A>::type(0));
-            for (int k = 0; k < nw; ++k) tot = acc_add(tot, scratch[k * 8 + q]);
-            out[q * (G + 1) + G] = tot;
+        ex[q] = acc_shfl_up(v[q], 1);
+        if (lane == 0) ex[q] = acc_from<A>(T(0));
+    }
+    if (nw == 1) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            out[q][tid] = ex[q];
+            if (lane == 31) out[q][G] = v[q];
+        }
+        return;
+    }
+    __syncthreads();   // the previous scan has finished reading scratch
+    if (lane == 31) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) scratch[warp * 8 + q] = v[q];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            A t = lane < nw ? scratch[lane * 8 + q] : acc_from<A>(T(0));
+            for (int k = 1; k < nw; k <<= 1) {
+                const A y = acc_shfl_up(t, k);
+                if (lane >= k) t = acc_add(t, y);
+            }
+            A b = acc_shfl_up(t, 1);
+            if (lane == 0) b = acc_from<A>(T(0));
+            if (lane < nw) scratch[lane * 8 + q] = b;
+            if (lane == nw - 1) out[q][G] = t;
         }
     }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) out[q][tid] = acc_add(scratch[warp * 8 + q], ex[q]);
 }
 
-// x-moment prefixes of the chunks (once per frequency)
+// x-moment prefixes of the chunks together with the prefixes of one channel
+// (sum w v, sum w x v), all about 0
 template <typename R, typename A>
-__device__ void build_x_prefix(const Frame<R> &fr, const Small<R, A> &sm, int c0, int c1, R o)
+__device__ void build_xy_prefix(const Frame<R> &fr, const Small<R, A> &sm, const R *vy, int c0,
+                                int c1, R o)
 {
-    R w_ = R(0), a_ = R(0), b_ = R(0);
+    const int L = blockDim.x + 1;
+    R w_ = R(0), a_ = R(0), b_ = R(0), sc = R(0), sd = R(0);
     for (int j = c0; j < c1; ++j) {
-        const R w = fr.WT[j], d = fr.X[j] - o;
+        const R w = fr.WT[j], d = fr.X[j] - o, wv = w * vy[j];
         w_ += w;
         a_ += w * d;
         b_ += w * d * d;
+        sc += wv;
+        sd += wv * d;
     }
-    // about 0: sum w x = a + o W, sum w x^2 = b + 2 o a + o^2 W
-    A v[3];
+    // about 0: sum w x = a + o W, sum w x^2 = b + 2 o a + o^2 W, sum w x v = d + o c
+    A v[5];
     v[0] = acc_from<A>(w_);
     v[1] = acc_add(acc_from<A>(a_), acc_mul(acc_from<A>(w_), o));
     v[2] = acc_add(acc_add(acc_from<A>(b_), acc_mul(acc_from<A>(a_), R(2) * o)),
                    acc_mul(acc_mul(acc_from<A>(w_), o), o));
-    block_scan_store<A, 3>(v, sm.px, sm.scan);
+    v[3] = acc_from<A>(sc);
+    v[4] = acc_add(acc_from<A>(sd), acc_mul(acc_from<A>(sc), o));
+    A *const out[5] = {sm.px, sm.px + L, sm.px + 2 * L, sm.pc, sm.pc + L};
+    block_scan_store<A, 5>(v, out, sm.scan);
 }
 
-// channel prefixes of the chunks (each pass)
+// channel prefixes of the chunks (each later pass)
 template <typename R, int NCH, bool DIFF = false, typename A>
 __device__ void build_channel_prefix(const Frame<R> &fr, const Small<R, A> &sm, const R *const *vv,
                                      int c0, int c1, R o)
 {
+    const int L = blockDim.x + 1;
     A v[2 * NCH];
 #pragma unroll
     for (int ch = 0; ch < NCH; ++ch) {
@@ -607,27 +633,49 @@ __device__ void build_channel_prefix(const Frame<R> &fr, const Small<R, A> &sm, 
         v[2 * ch] = acc_from<A>(sc);
         v[2 * ch + 1] = acc_add(acc_from<A>(sd), acc_mul(acc_from<A>(sc), o));  // sum w x v about 0
     }
-    block_scan_store<A, 2 * NCH>(v, sm.pc, sm.scan);
+    A *out[2 * NCH];
+#pragma unroll
+    for (int q = 0; q < 2 * NCH; ++q) out[q] = sm.pc + q * L;
+    block_scan_store<A, 2 * NCH>(v, out, sm.scan);
 }
 
-// first chunk starting at or after p / last boundary at or before p
-__device__ inline int chunk_lower(const int *cs, int G, int p)
+// Chunk u starts at cs[u] = floor(u n / G), moved forward past a run of ties
+// it would split, so cs[u] >= floor(u n / G): the arithmetic guess below is
+// never too low, and the correction walks down over tie-emptied chunks only.
+// First chunk starting at or after p (0 <= p <= n):
+__device__ inline int chunk_lower(const int *cs, int G, int n, int p)
 {
-    int lo = 0, hi = G;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (cs[mid] < p) lo = mid + 1; else hi = mid;
-    }
-    return lo;
+    int u = (int)(((long long)p * G + n - 1) / n);   // ceil(p G / n): cs[u] >= p
+    while (u > 0 && cs[u - 1] >= p) --u;
+    return u;
 }
-__device__ inline int chunk_upper(const int *cs, int G, int p)
+// Last chunk boundary at or before q (0 <= q <= n):
+__device__ inline int chunk_upper(const int *cs, int G, int n, int q)
 {
-    int lo = 0, hi = G;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (cs[mid] <= p) lo = mid; else hi = mid - 1;
+    int u = (int)(((long long)(q + 1) * G + n - 1) / n) - 1;   // floor(u n / G) <= q
+    if (u > G) u = G;
+    while (cs[u] > q) --u;
+    return u;
+}
+
+// one point at slot p (0 <= p < n) with abscissa shift sh (-1, 0, +1)
+template <typename R, int NCH, bool DIFF>
+__device__ inline void win_add_slot(Win<R, NCH> &s, const Frame<R> &fr, const R *const *v, int p,
+                                    R sh, R o)
+{
+    const R dx = (fr.X[p] - o) + sh;
+    const R w = fr.WT[p];
+    const R wdx = w * dx;
+    s.W += w;
+    s.A += wdx;
+    s.B += wdx * dx;
+    if (sizeof(R) == 4) s.hiB = fmax(s.hiB, s.B);
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        R vc = chan<R, NCH, DIFF>(v, c, p);
+        s.C[c] += w * vc;
+        s.D[c] += wdx * vc;
     }
-    return lo;
 }
 
 // Sums of the window [c - h, c + h] about origin o.  Whole chunks come from
@@ -644,15 +692,16 @@ __device__ void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R, A> &
     s.zero();
     // three segments of constant shift: slots before 0, inside, after n-1
     const int ea = c - h, eb = c + h;
-#pragma unroll
+#pragma unroll 1
     for (int seg = -1; seg <= 1; ++seg) {
         int pa, pb;
         if (seg < 0) { pa = ea + n; pb = n - 1; if (ea >= 0) continue; }
         else if (seg == 0) { pa = ea < 0 ? 0 : ea; pb = eb >= n ? n - 1 : eb; }
         else { pa = 0; pb = eb - n; if (eb < n) continue; }
-        const int ua = chunk_lower(sm.cs, G, pa);
-        const int ub = chunk_upper(sm.cs, G, pb + 1);
-        int q0 = pa, q1 = pb;   // points left to add one by one: [q0, ..) and (.., q1]
+        const int ua = chunk_lower(sm.cs, G, n, pa);
+        const int ub = chunk_upper(sm.cs, G, n, pb + 1);
+        // points added one by one: [pa, pa + nl) and [pr, pr + (nt - nl))
+        int nl = pb - pa + 1, nt = nl, pr = pa;
         if (ua < ub) {
             // chunks ua..ub-1 lie inside [pa, pb]
             const A w = acc_add(sm.px[0 * L + ub], acc_neg(sm.px[0 * L + ua]));
@@ -680,13 +729,14 @@ __device__ void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R, A> &
                 C[ch] = acc_add(C[ch], cc[ch]);
                 D[ch] = acc_add(D[ch], dd[ch]);
             }
-            // ragged ends
+            // ragged ends, both in one loop
             const int fa = sm.cs[ua], fb = sm.cs[ub];
-            for (int p = pa; p < fa; ++p) win_add<R, NCH, DIFF>(s, fr, v, seg < 0 ? p - n : (seg > 0 ? p + n : p), n, o, R(1));
-            for (int p = fb; p <= pb; ++p) win_add<R, NCH, DIFF>(s, fr, v, seg < 0 ? p - n : (seg > 0 ? p + n : p), n, o, R(1));
-        } else {
-            for (int p = q0; p <= q1; ++p) win_add<R, NCH, DIFF>(s, fr, v, seg < 0 ? p - n : (seg > 0 ? p + n : p), n, o, R(1));
+            nl = fa - pa;
+            nt = nl + (pb - fb + 1);
+            pr = fb - nl;
         }
+        for (int k = 0; k < nt; ++k)
+            win_add_slot<R, NCH, DIFF>(s, fr, v, k < nl ? pa + k : pr + k, (R)seg, o);
     }
     // about o: A = S1 - o W, B = S2 - 2 o S1 + o^2 W, D = D - o C
     const A oW = acc_mul(W, o);
@@ -749,10 +799,20 @@ __device__ inline void win_fit(Fit<R, NCH> &f, const Win<R, NCH> &s, R xj_minus_
 // largest moment they have held; where the centred spread is below a fixed
 // part of that (a tight cluster after wide windows, or a far origin), this
 // centre's window is refitted directly in FP64.
+// (out of line, arguments by value: the rare call must not force the
+// caller's fits, frame or channel table into local memory)
+template <typename R, int NCH>
+struct Chans {
+    const R *p[NCH];
+};
 template <typename R, int NCH, bool DIFF = false>
-__device__ void win_refit_fp64(Fit<R, NCH> &f, const Frame<R> &fr, const R *const *v, int j,
-                               int h, int n, double vsmlsq)
+__device__ __noinline__ Fit<R, NCH> win_refit_fp64(const Frame<R> fr, const Chans<R, NCH> cv, int j,
+                                                   int h, int n, double vsmlsq)
 {
+    const R *v[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) v[c] = cv.p[c];
+    Fit<R, NCH> f;
     double sw = 0.0, swx = 0.0, swv[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) swv[c] = 0.0;
@@ -788,6 +848,8 @@ __device__ void win_refit_fp64(Fit<R, NCH> &f, const Frame<R> &fr, const R *cons
         f.b[c] = (R)(slope ? sxv[c] / sxx : 0.0);
         f.s[c] = (R)(swv[c] / sw + (slope ? sxv[c] / sxx : 0.0) * dxj);
     }
+    f.sxx = (R)sxx;
+    return f;
 }
 
 template <typename R, int NCH, bool DIFF = false>
@@ -798,8 +860,13 @@ __device__ inline void win_fit_checked(Fit<R, NCH> &f, const Win<R, NCH> &s, con
     win_fit<R, NCH>(f, s, fr.X[j] - o, vsmlsq);
     if (sizeof(R) == 4) {
         const R sxx = f.sxx;
-        if (sxx < s.hiB * refit_frac && s.hiB > R(0))
-            win_refit_fp64<R, NCH, DIFF>(f, fr, v, j, h, n, (double)vsmlsq);
+        if (sxx < s.hiB * refit_frac && s.hiB > R(0)) {
+            Chans<R, NCH> cv;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) cv.p[c] = (DIFF && c == NCH - 1) ? nullptr : v[c];
+            f = win_refit_fp64<R, NCH, DIFF>(fr, cv, j, h, n, (double)vsmlsq);
+            f.sxx = sxx;
+        }
         if (fabs(sxx - vsmlsq) <= (R)kNearSlope * vsmlsq) near = true;
     }
 }
@@ -957,7 +1024,7 @@ __device__ inline void run_push(RunAvg<R, K> &ra, const Frame<R> &fr, int j, boo
 // original index) and binary64 magnitudes and weights read through perm.
 // Every lane returns the fit; all lanes of the warp must call it together.
 template <typename R>
-__device__ double warp_fit_fp64(const Frame<R> &fr, const double *y64, const double *w64, int j,
+__device__ __noinline__ double warp_fit_fp64(const Frame<R> fr, const double *y64, const double *w64, int j,
                                 int h, int n, double vsmlsq64, double xj)
 {
     const int lane = threadIdx.x & 31;
@@ -1096,7 +1163,6 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
     __syncthreads();
     const int c0 = sm.cs[tid], c1 = sm.cs[tid + 1];
     const R o = (c0 < c1) ? fr.X[c0] : R(0);
-    build_x_prefix(fr, sm, c0, c1, o);
 
     KSum<R> chi2;
     bool near = false;
@@ -1105,7 +1171,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
     if (VARIANT == VAR_SP) {
         // one sweep, three windows on y, generalized validation (Sec. 3)
         const R *vy[1] = {fr.Y};
-        build_channel_prefix<R, 1>(fr, sm, vy, c0, c1, o);
+        build_xy_prefix(fr, sm, fr.Y, c0, c1, o);
         __syncthreads();
         const int lane = tid & 31;
         const int len = c1 - c0;
@@ -1131,6 +1197,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
             const double xq = (double)(((uint64_t)fr.key[pj] << 32) | fr.klo[pj]) * 5.421010862427522e-20;
             vsm64 = 1.0e-6 * (xq - xi) * (xq - xi);
         }
+        // a point whose bound E on its chi2 change exceeds this is refitted
+        const R sens_lim = (R)(a.sens_tau * a.chi0[obj]);
         RunAvg<R, 1> ra;
         ra.reset(c0);
         auto emit = [&](int i, const R (&v)[1]) {
@@ -1181,9 +1249,9 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
                         const R sp_ = sp;
                         const R dvds = (sp_ - K.s1 < R(0)) ? fabs(s0 - s1) * (-K.inv01)
                                                            : fabs(s2 - s1) * K.inv21;
-                        const double E = 2.0 * (double)fr.WT[j] * fabs((double)(yj - val[0])) *
-                                         (double)((K.s2 - sk) * dvds * tmp * (ge / gm + we / g2));
-                        if (E > a.sens_tau * a.chi0[obj]) contested = true;
+                        const R E = R(2) * fr.WT[j] * fabs(yj - val[0]) *
+                                    ((K.s2 - sk) * dvds * tmp * (ge / gm + we / g2));
+                        if (E > sens_lim) contested = true;
                     }
                 }
             }
@@ -1229,7 +1297,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
     // whose leverage reached 1; resolved below).
     {
         const R *vy[1] = {fr.Y};
-        build_channel_prefix<R, 1>(fr, sm, vy, c0, c1, o);
+        build_xy_prefix(fr, sm, fr.Y, c0, c1, o);
         __syncthreads();
         if (c0 < c1) {
             Win<R, 1> w0, w1, w2;
