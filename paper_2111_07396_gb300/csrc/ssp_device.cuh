@@ -113,24 +113,39 @@ struct Frame {
     R *C[7];                // smoother columns
     uint32_t *tie;          // bit j: sorted points j and j+1 have the same
                             // folded phase (exact fold output, not rounded X)
-    uint32_t *key, *klo;    // phase as 64-bit fixed point, high / low word
-    uint16_t *slot, *tmp, *perm;  // sort scratch (n <= 65535)
+    uint32_t *key, *klo;    // phase as 64-bit fixed point, high / low word: by
+                            // original index after the fold, in sorted order
+                            // after the sort
+    uint32_t *skh, *skl;    // sort scratch: keys by bucket position
+    uint16_t *slot, *tmp, *perm;  // sort scratch; perm: original index of
+                                  // each sorted point (n <= 65535)
     uint32_t *cnt;          // bucket counts / starts
     double *ph;             // FP64 phase by original index
 };
 
 __host__ __device__ inline size_t tie_words(int n) { return ((size_t)n + 31) / 32; }
 
-// Frame layout: X, WT, Y and the seven columns, each align16(sizeof(R) n);
-// the sort scratch (key, klo, slot, tmp, perm, cnt and, for FP64, the phases
-// by original index) overlays the columns from C0 on; the tie bitmask
-// follows whichever of the two ends later, because the gather writes it
-// while it still reads the sort's output.
+// Frame layout.  X, WT and Y come first; while the phases are sorted that
+// region holds the scatter scratch instead (keys by bucket position, slots
+// and scattered indices).  The sort region follows: key and klo (the fold
+// output by original index, then the keys in sorted order), perm, the bucket
+// counts and, for FP64, the phases by original index.  SS columns C0..C6 also
+// follow X, WT, Y and overlay the sort region, which is dead once the gather
+// has run; SP keeps the sorted keys for its exact refits.  The tie bitmask
+// follows whichever region ends later, because the gather writes it while it
+// still reads the sort's output.
+template <typename R>
+__host__ __device__ inline size_t xwy_bytes(int n)
+{
+    const size_t col = align16(sizeof(R) * (size_t)n);
+    const size_t scat = align16(4 * (size_t)n) * 2 + align16(2 * (size_t)n) * 2;
+    return 3 * col > scat ? 3 * col : scat;
+}
+
 template <typename R>
 __host__ __device__ inline size_t sort_end(int n)
 {
-    const size_t col = align16(sizeof(R) * (size_t)n);
-    size_t s = col * 3 + align16(4 * (size_t)n) * 2 + align16(2 * (size_t)n) * 2 +
+    size_t s = xwy_bytes<R>(n) + align16(4 * (size_t)n) * 2 +
                align16(2 * (size_t)pow2_at_least(n)) + align16(4 * (size_t)bucket_count(n));
     if (sizeof(R) == 8) s += align16(8 * (size_t)n);
     return s;
@@ -139,7 +154,7 @@ __host__ __device__ inline size_t sort_end(int n)
 template <typename R>
 __host__ __device__ inline size_t tie_offset(int n, int ncols)
 {
-    const size_t cols = align16(sizeof(R) * (size_t)n) * ncols;
+    const size_t cols = xwy_bytes<R>(n) + align16(sizeof(R) * (size_t)n) * (size_t)(ncols - 3);
     const size_t s = sort_end<R>(n);
     return cols > s ? cols : s;
 }
@@ -157,22 +172,24 @@ template <typename R>
 __device__ inline Frame<R> carve_frame(unsigned char *base, int n, int variant)
 {
     Frame<R> f;
-    const size_t col = align16(sizeof(R) * (size_t)n);
+    const size_t col = align16(sizeof(R) * (size_t)n), xwy = xwy_bytes<R>(n);
+    const size_t a4 = align16(4 * (size_t)n), a2 = align16(2 * (size_t)n);
+    const size_t ap = align16(2 * (size_t)pow2_at_least(n));
     f.X = (R *)base;
     f.WT = (R *)(base + col);
     f.Y = (R *)(base + 2 * col);
-    for (int k = 0; k < 7; ++k) f.C[k] = (R *)(base + (3 + k) * col);
-    f.tie = (uint32_t *)(base + tie_offset<R>(n, frame_cols(variant)));
-    unsigned char *s = base + 3 * col;
-    const size_t a4 = align16(4 * (size_t)n), a2 = align16(2 * (size_t)n);
-    const size_t ap = align16(2 * (size_t)pow2_at_least(n));
+    f.skh = (uint32_t *)base;
+    f.skl = (uint32_t *)(base + a4);
+    f.slot = (uint16_t *)(base + 2 * a4);
+    f.tmp = (uint16_t *)(base + 2 * a4 + a2);
+    for (int k = 0; k < 7; ++k) f.C[k] = (R *)(base + xwy + k * col);
+    unsigned char *s = base + xwy;
     f.key = (uint32_t *)s;
     f.klo = (uint32_t *)(s + a4);
-    f.slot = (uint16_t *)(s + 2 * a4);
-    f.tmp = (uint16_t *)(s + 2 * a4 + a2);
-    f.perm = (uint16_t *)(s + 2 * a4 + 2 * a2);
-    f.cnt = (uint32_t *)(s + 2 * a4 + 2 * a2 + ap);
-    f.ph = (double *)(s + 2 * a4 + 2 * a2 + ap + align16(4 * (size_t)bucket_count(n)));
+    f.perm = (uint16_t *)(s + 2 * a4);
+    f.cnt = (uint32_t *)(s + 2 * a4 + ap);
+    f.ph = (double *)(s + 2 * a4 + ap + align16(4 * (size_t)bucket_count(n)));
+    f.tie = (uint32_t *)(base + tie_offset<R>(n, frame_cols(variant)));
     return f;
 }
 
@@ -417,33 +434,82 @@ __device__ __noinline__ void bitonic_argsort(const Frame<R> fr, int n)
     }
 }
 
+// Fold (Alg. 1 computePhasedTime) and stable argsort of the phases: a
+// counting sort on the top bits of the 64-bit fixed-point phase into about
+// n/2 buckets, each bucket ranked by full key, then original index (FP64:
+// binary64 phase between equal keys, then index); buckets more crowded than
+// kBucketRankMax fall back to a bitonic sort.  On return perm holds the
+// original index of each sorted point and key/klo the sorted keys.
 template <typename R, typename A>
-__device__ void argsort_phases(const Frame<R> &fr, int n, const Small<R, A> &sm)
+__device__ void fold_and_sort(const Frame<R> &fr, int n, const Small<R, A> &sm, const double *tt,
+                              double f)
 {
     const int tid = threadIdx.x, G = blockDim.x;
     const int nb = bucket_count(n);
     const int shift = 32 - (31 - __clz(nb));
     for (int b = tid; b < nb; b += G) fr.cnt[b] = 0u;
     __syncthreads();
-    for (int i = tid; i < n; i += G)
-        fr.slot[i] = (uint16_t)atomicAdd(&fr.cnt[fr.key[i] >> shift], 1u);
+    for (int i = tid; i < n; i += G) {
+        uint64_t fx;
+        if (sizeof(R) == 8) {
+            const double ph = fold_fp64(tt[i], f);
+            fr.ph[i] = ph;
+            fx = __double2ull_rz(ph * 18446744073709551616.0);
+        } else {
+            fx = fold_fixed64(tt[i], f);
+        }
+        const uint32_t kh = (uint32_t)(fx >> 32);
+        fr.key[i] = kh;
+        fr.klo[i] = (uint32_t)fx;
+        fr.slot[i] = (uint16_t)atomicAdd(&fr.cnt[kh >> shift], 1u);
+    }
     __syncthreads();
     const int crowd = block_exclusive_scan(fr.cnt, nb, sm.ired);
     if (crowd > kBucketRankMax) {
         bitonic_argsort(fr, n);
+        // sorted keys by way of the scatter scratch
+        for (int p = tid; p < n; p += G) {
+            const uint32_t i = fr.perm[p];
+            fr.skh[p] = fr.key[i];
+            fr.skl[p] = fr.klo[i];
+        }
+        __syncthreads();
+        for (int p = tid; p < n; p += G) {
+            fr.key[p] = fr.skh[p];
+            fr.klo[p] = fr.skl[p];
+        }
+        __syncthreads();
         return;
     }
-    for (int i = tid; i < n; i += G)
-        fr.tmp[fr.cnt[fr.key[i] >> shift] + fr.slot[i]] = (uint16_t)i;
+    // scatter index and key to the bucket's slots
+    for (int i = tid; i < n; i += G) {
+        const uint32_t kh = fr.key[i];
+        const int p = (int)fr.cnt[kh >> shift] + fr.slot[i];
+        fr.tmp[p] = (uint16_t)i;
+        fr.skh[p] = kh;
+        fr.skl[p] = fr.klo[i];
+    }
     __syncthreads();
+    // rank within the bucket (its members sit next to each other)
     for (int p = tid; p < n; p += G) {
-        const uint32_t i = fr.tmp[p];
-        const uint32_t b = fr.key[i] >> shift;
+        const uint32_t i = fr.tmp[p], kh = fr.skh[p], kl = fr.skl[p];
+        const uint32_t b = kh >> shift;
         const int lo = (int)fr.cnt[b];
         const int hi = (b + 1 < (uint32_t)nb) ? (int)fr.cnt[b + 1] : n;
         int rank = 0;
-        for (int q = lo; q < hi; ++q) rank += key_less(fr, fr.tmp[q], i) ? 1 : 0;
+        for (int q = lo; q < hi; ++q) {
+            const uint32_t qh = fr.skh[q], ql = fr.skl[q];
+            bool less = qh < kh || (qh == kh && ql < kl);
+            if (qh == kh && ql == kl) {
+                const uint32_t iq = fr.tmp[q];
+                less = iq < i;
+                if (sizeof(R) == 8 && fr.ph[iq] != fr.ph[i]) less = fr.ph[iq] < fr.ph[i];
+            }
+            rank += less ? 1 : 0;
+        }
         fr.perm[lo + rank] = (uint16_t)i;
+        fr.key[lo + rank] = kh;
+        fr.klo[lo + rank] = kl;
     }
     __syncthreads();
 }
@@ -615,23 +681,48 @@ __device__ void build_xy_prefix(const Frame<R> &fr, const Small<R, A> &sm, const
     block_scan_store<A, 5>(v, out, sm.scan);
 }
 
-// channel prefixes of the chunks (each later pass)
-template <typename R, int NCH, bool DIFF = false, typename A>
+// channel prefixes of the chunks (each later pass).  With FIX, a stored
+// channel value below 0 (a CV residual whose leverage reached 1) is first
+// replaced by the previous centre's (0 at the first centre), as Listing 1
+// does; a value read from a neighbouring chunk while its owner resolves it is
+// either still negative (the walk goes on) or already the value the walk
+// would find.
+template <typename R, int NCH, bool DIFF = false, bool FIX = false, typename A>
 __device__ void build_channel_prefix(const Frame<R> &fr, const Small<R, A> &sm, const R *const *vv,
                                      int c0, int c1, R o)
 {
+    constexpr int NS = DIFF ? NCH - 1 : NCH;   // stored channels
     const int L = blockDim.x + 1;
+    R sc[NCH], sd[NCH];
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) sc[ch] = sd[ch] = R(0);
+    for (int j = c0; j < c1; ++j) {
+        const R w = fr.WT[j], d = fr.X[j] - o;
+        R val[NCH];
+#pragma unroll
+        for (int ch = 0; ch < NS; ++ch) {
+            R x = vv[ch][j];
+            if (FIX && x < R(0)) {
+                int q = j - 1;
+                while (q >= 0 && vv[ch][q] < R(0)) --q;
+                x = (q >= 0) ? vv[ch][q] : R(0);
+                const_cast<R *>(vv[ch])[j] = x;
+            }
+            val[ch] = x;
+        }
+        if (DIFF) val[NCH - 1] = val[0] - val[1];
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+            const R wv = w * val[ch];
+            sc[ch] += wv;
+            sd[ch] += wv * d;
+        }
+    }
     A v[2 * NCH];
 #pragma unroll
     for (int ch = 0; ch < NCH; ++ch) {
-        R sc = R(0), sd = R(0);
-        for (int j = c0; j < c1; ++j) {
-            const R wv = fr.WT[j] * chan<R, NCH, DIFF>(vv, ch, j);
-            sc += wv;
-            sd += wv * (fr.X[j] - o);
-        }
-        v[2 * ch] = acc_from<A>(sc);
-        v[2 * ch + 1] = acc_add(acc_from<A>(sd), acc_mul(acc_from<A>(sc), o));  // sum w x v about 0
+        v[2 * ch] = acc_from<A>(sc[ch]);
+        v[2 * ch + 1] = acc_add(acc_from<A>(sd[ch]), acc_mul(acc_from<A>(sc[ch]), o));  // sum w x v about 0
     }
     A *out[2 * NCH];
 #pragma unroll
@@ -645,14 +736,14 @@ __device__ void build_channel_prefix(const Frame<R> &fr, const Small<R, A> &sm, 
 // First chunk starting at or after p (0 <= p <= n):
 __device__ inline int chunk_lower(const int *cs, int G, int n, int p)
 {
-    int u = (int)(((long long)p * G + n - 1) / n);   // ceil(p G / n): cs[u] >= p
+    int u = (int)(((unsigned)(p * G) + (unsigned)(n - 1)) / (unsigned)n);   // ceil(p G / n): cs[u] >= p
     while (u > 0 && cs[u - 1] >= p) --u;
     return u;
 }
 // Last chunk boundary at or before q (0 <= q <= n):
 __device__ inline int chunk_upper(const int *cs, int G, int n, int q)
 {
-    int u = (int)(((long long)(q + 1) * G + n - 1) / n) - 1;   // floor(u n / G) <= q
+    int u = (int)(((unsigned)((q + 1) * G) + (unsigned)(n - 1)) / (unsigned)n) - 1;   // floor(u n / G) <= q
     if (u > G) u = G;
     while (cs[u] > q) --u;
     return u;
@@ -1020,8 +1111,8 @@ __device__ inline void run_push(RunAvg<R, K> &ra, const Frame<R> &fr, int j, boo
 
 
 // Binary64 line fit of window [j - h, j + h] at centre j, summed by the 32
-// lanes of a warp: exact phases (the fold's 64-bit fixed-point output by
-// original index) and binary64 magnitudes and weights read through perm.
+// lanes of a warp: exact phases (the sorted 64-bit fixed-point keys) and
+// binary64 magnitudes and weights read through perm.
 // Every lane returns the fit; all lanes of the warp must call it together.
 template <typename R>
 __device__ __noinline__ double warp_fit_fp64(const Frame<R> fr, const double *y64, const double *w64, int j,
@@ -1033,7 +1124,7 @@ __device__ __noinline__ double warp_fit_fp64(const Frame<R> fr, const double *y6
         int sh;
         const int p = slot_point(e, n, sh);
         const uint32_t i = fr.perm[p];
-        const double x = (double)(((uint64_t)fr.key[i] << 32) | fr.klo[i]) * 5.421010862427522e-20 + sh;
+        const double x = (double)(((uint64_t)fr.key[p] << 32) | fr.klo[p]) * 5.421010862427522e-20 + sh;
         const double w = w64[i], y = y64[i], dx = x - xj;
         sw += w;
         sa += w * dx;
@@ -1073,23 +1164,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
     const R *wv = (const R *)a.wv + base;
     const double *tt = a.tt + base;
 
-    // ---- fold: phase bits as a 64-bit fixed-point fraction ----
-    for (int i = tid; i < n; i += G) {
-        uint64_t fx;
-        if (sizeof(R) == 8) {
-            const double ph = fold_fp64(tt[i], f);
-            fr.ph[i] = ph;
-            fx = __double2ull_rz(ph * 18446744073709551616.0);
-        } else {
-            fx = fold_fixed64(tt[i], f);
-        }
-        fr.key[i] = (uint32_t)(fx >> 32);
-        fr.klo[i] = (uint32_t)fx;
-    }
-    __syncthreads();
-
-    // ---- sort ----
-    argsort_phases<R>(fr, n, sm);
+    // ---- fold and sort ----
+    fold_and_sort(fr, n, sm, tt, f);
 
     // ---- gather ----
     // tie bits and the degenerate test use the exact fold output, so runs of
@@ -1100,20 +1176,20 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
         bool tj = false;
         if (j < n) {
             const uint32_t i = fr.perm[j];
+            const uint32_t kh = fr.key[j], kl = fr.klo[j];
             R x;
             if (sizeof(R) == 8) {
                 x = (R)fr.ph[i];
             } else {
-                const uint64_t fx = ((uint64_t)fr.key[i] << 32) | fr.klo[i];
+                const uint64_t fx = ((uint64_t)kh << 32) | kl;
                 x = (R)(__ull2float_rz(fx) * 5.421010862427522e-20f);   // * 2^-64
             }
             fr.X[j] = x;
             fr.WT[j] = wv[i];
             fr.Y[j] = yc[i];
             if (j + 1 < n) {
-                const uint32_t i2 = fr.perm[j + 1];
-                tj = (sizeof(R) == 8) ? (fr.ph[i] == fr.ph[i2])
-                                      : (fr.key[i] == fr.key[i2] && fr.klo[i] == fr.klo[i2]);
+                tj = (sizeof(R) == 8) ? (fr.ph[i] == fr.ph[fr.perm[j + 1]])
+                                      : (kh == fr.key[j + 1] && kl == fr.klo[j + 1]);
             }
         }
         const uint32_t word = __ballot_sync(0xffffffffu, tj);
@@ -1121,9 +1197,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
         tie |= tj;
     }
     const bool ties = __syncthreads_or(tie) != 0;
-    const uint32_t pf = fr.perm[0], pl = fr.perm[n - 1];
-    const bool flat = (sizeof(R) == 8) ? !(fr.ph[pl] > fr.ph[pf])
-                                       : (fr.key[pl] == fr.key[pf] && fr.klo[pl] == fr.klo[pf]);
+    const bool flat = (sizeof(R) == 8) ? !(fr.ph[fr.perm[n - 1]] > fr.ph[fr.perm[0]])
+                                       : (fr.key[n - 1] == fr.key[0] && fr.klo[n - 1] == fr.klo[0]);
 
     // ---- degenerate abscissae: weighted mean (Listing 1) ----
     if (flat) {
@@ -1154,7 +1229,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
 
     // ---- chunks: contiguous centre ranges that never split a run of ties ----
     {
-        int c = (int)(((long long)tid * n) / G);
+        int c = (int)((unsigned)(tid * n) / (unsigned)G);   // n G < 2^31
         if (ties)
             while (c > 0 && c < n && tie_next(fr, c - 1)) ++c;
         sm.cs[tid] = c;
@@ -1192,9 +1267,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
         const double *w64 = a.wv64 ? a.wv64 + base : nullptr;
         double vsm64 = 0.0;
         if (sizeof(R) == 4 && y64) {
-            const uint32_t pi = fr.perm[qi], pj = fr.perm[qj];
-            const double xi = (double)(((uint64_t)fr.key[pi] << 32) | fr.klo[pi]) * 5.421010862427522e-20;
-            const double xq = (double)(((uint64_t)fr.key[pj] << 32) | fr.klo[pj]) * 5.421010862427522e-20;
+            const double xi = (double)(((uint64_t)fr.key[qi] << 32) | fr.klo[qi]) * 5.421010862427522e-20;
+            const double xq = (double)(((uint64_t)fr.key[qj] << 32) | fr.klo[qj]) * 5.421010862427522e-20;
             vsm64 = 1.0e-6 * (xq - xi) * (xq - xi);
         }
         // a point whose bound E on its chi2 change exceeds this is refitted
@@ -1261,7 +1335,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
                 todo &= todo - 1;
                 const int je = __shfl_sync(0xffffffffu, j, src);
                 const uint32_t pe = fr.perm[je];
-                const double xe = (double)(((uint64_t)fr.key[pe] << 32) | fr.klo[pe]) * 5.421010862427522e-20;
+                const double xe = (double)(((uint64_t)fr.key[je] << 32) | fr.klo[je]) * 5.421010862427522e-20;
                 const double t0 = warp_fit_fp64<R>(fr, y64, w64, je, h0, n, vsm64, xe);
                 const double t1 = warp_fit_fp64<R>(fr, y64, w64, je, h1, n, vsm64, xe);
                 const double t2 = warp_fit_fp64<R>(fr, y64, w64, je, h2, n, vsm64, xe);
@@ -1336,20 +1410,6 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
         }
     }
     __syncthreads();
-    // a residual whose leverage reached 1 repeats the previous centre's (0 at
-    // the first centre); reading neighbours while they are being resolved is
-    // safe because a resolved value equals what the walk would find
-    for (int j = c0; j < c1; ++j) {
-#pragma unroll
-        for (int k = 1; k < 6; k += 2) {
-            if (fr.C[k][j] < R(0)) {
-                int q = j - 1;
-                while (q >= 0 && fr.C[k][q] < R(0)) --q;
-                fr.C[k][j] = (q >= 0) ? fr.C[k][q] : R(0);
-            }
-        }
-    }
-    __syncthreads();
 
     // pass B: midrange smooth of the three residual columns (and, FP32C, of the
     // tweeter-minus-midrange difference), span choice with bass enhancement
@@ -1359,7 +1419,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
         constexpr int NB = DIFF ? 4 : 3;
         const R *vr[3] = {fr.C[1], fr.C[3], fr.C[5]};
         const float margin = a.near_ss * fminf(1.f, 256.f / (float)n) * fminf(1.f, 512.f / (float)n);
-        build_channel_prefix<R, NB, DIFF>(fr, sm, vr, c0, c1, o);
+        // resolves the -1 residuals of pass A while it sums them
+        build_channel_prefix<R, NB, DIFF, true>(fr, sm, vr, c0, c1, o);
         __syncthreads();
         if (c0 < c1) {
             Win<R, NB> w1;
