@@ -16,6 +16,12 @@ sampled during the timed region.
 
 --impl reference times the plain FP64 C oracle (the only reference there is)
 on the host cores over a bounded sample of the same workload per step.
+
+--serve runs the serving workload instead: Poisson arrivals of single light
+curves (2,000 objects/s for 60 s by default, n ~ logU(30, 3000), 10^4
+frequencies, SS or SP per request) submitted through the C ABI's serving
+entry points (ssp_server_*), and prints sustained objects/s and the
+arrival-to-result latency percentiles as its own JSON line.
 """
 from __future__ import annotations
 
@@ -57,6 +63,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--n-freq", type=int, default=100_000)
+    ap.add_argument("--serve", action="store_true", help="serving workload (ssp_server_*)")
+    ap.add_argument("--rate", type=float, default=2000.0, help="--serve: arrivals per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="--serve: seconds of arrivals")
+    ap.add_argument("--serve-freq", type=int, default=10_000, help="--serve: trial frequencies")
     return ap.parse_args()
 
 
@@ -128,9 +138,10 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-def cpu_baseline(cat, budget_s=12.0, max_freq=4096):
+def cpu_baseline(cat, p32=None, budget_s=12.0, max_freq=4096):
     """The FP64 oracle, as it stands, on the host cores over a bounded sample
-    of the workload's frequencies (both variants)."""
+    of the workload's frequencies (both variants); with p32 (this run's FP32C
+    powers) also the oracle at a few sampled frequencies against them."""
     import oracle
     t, y, dy = cat.obj(0)
     n = t.size
@@ -147,9 +158,18 @@ def cpu_baseline(cat, budget_s=12.0, max_freq=4096):
         used += time.perf_counter() - t0
         done += fq.size
     ptf = 2 * n * done
-    return {"value": ptf / used, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{done} of {cat.freq.size} frequencies (random), SS+SP, n={n}, "
-                      f"{used:.1f} s wall"}
+    out = {"value": ptf / used, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{done} of {cat.freq.size} frequencies (random), SS+SP, n={n}, "
+                     f"{used:.1f} s wall"}
+    if p32 is not None:
+        from tests.parity import gate_error, oracle_powers, sample_freqs
+        chk = {}
+        for v, code in (("ss", oracle.SS), ("sp", oracle.SP)):
+            qs = sample_freqs(cat.freq.size, 12, seed=5, include=[int(np.argmax(p32[v]))])
+            ref = oracle_powers(t, y, dy, cat.freq[qs], code)
+            chk[v] = {"frequencies": int(qs.size), "max_gate_err": gate_error(p32[v][qs], ref)}
+        out["oracle_check_fp32c"] = chk
+    return out
 
 
 def run_reference(args):
@@ -352,27 +372,100 @@ def run_ours(args):
             "fp64": fp64, "accuracy_fp32c": acc,
             "best_period": b32}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cat)
-        # oracle at a few sampled frequencies against this run's FP32C output
-        import oracle
-        from tests.parity import oracle_powers, sample_freqs
-        tt_, yy, dyy = cat.obj(0)
-        chk = {}
-        for v, code in (("ss", oracle.SS), ("sp", oracle.SP)):
-            qs = sample_freqs(nf, 12, seed=5, include=[int(np.argmax(p32[v]))])
-            ref = oracle_powers(tt_, yy, dyy, cat.freq[qs], code)
-            chk[v] = {"frequencies": int(qs.size), "max_gate_err": gate_error(p32[v][qs], ref)}
-        line["oracle_check_fp32c"] = chk
+        line["cpu_baseline"] = cpu_baseline(cat, p32)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+def run_serve(args):
+    """Serving workload through ssp_server_*: a submitter thread replays the
+    Poisson arrival times, a collector thread takes each finished ticket and
+    its results.  Latency = result in hand minus scheduled arrival."""
+    import threading
+
+    from paper_2111_07396_gb300 import build as ssp_build
+    from paper_2111_07396_gb300 import ssp, synth
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    ssp_build.build()
+    ssp.lib()
+    arrivals, cat, variants = synth.config5_arrivals(args.rate, args.duration, args.serve_freq)
+    N, nf = int(arrivals.size), int(cat.freq.size)
+    objs = [cat.obj(k) for k in range(N)]
+    names = ("ss", "sp")
+    srv = ssp.Server(cat.freq, precision="fp32c")
+    for k in range(8):                              # warm-up: plans, pools, pinned buffers
+        t, y, dy = objs[k]
+        srv.poll(srv.submit(t, y, dy, names[k % 2]), wait_ms=60000)
+    first = srv.submit(*objs[0], "ss")              # tickets are sequential from here on
+    srv.poll(first, wait_ms=60000)
+    lat = np.full(N, np.nan)
+    lat_srv = np.full(N, np.nan)
+    best = np.zeros(N)
+    t0 = time.perf_counter() + 0.1
+    errors = []
+
+    def submitter():
+        for k in range(N):
+            d = t0 + arrivals[k] - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            t, y, dy = objs[k]
+            try:
+                srv.submit(t, y, dy, names[variants[k]])
+            except Exception as e:  # noqa: BLE001
+                errors.append(repr(e))
+                return
+
+    def collector():
+        got = 0
+        while got < N and not errors:
+            tk = srv.next(wait_ms=1000)
+            if tk is None:
+                continue
+            k = tk - first - 1
+            r = srv.poll(tk)
+            lat[k] = (time.perf_counter() - (t0 + arrivals[k])) * 1e3
+            lat_srv[k] = r[2]
+            best[k] = r[1]
+            got += 1
+
+    ts = threading.Thread(target=submitter)
+    tc = threading.Thread(target=collector)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        ts.start()
+        tc.start()
+        ts.join()
+        tc.join()
+    end = float(np.nanmax(arrivals + lat / 1e3))    # first arrival to last result, s
+    srv.close()
+    ptf = float(np.sum(cat.n_per_object)) * nf
+    q = lambda a, p: float(np.nanpercentile(a, p))
+    line = {"metric": "served objects/s (Poisson arrivals, single-object requests)",
+            "value": N / end, "unit": "objects/s", "higher_is_better": True,
+            "offered_rate": args.rate, "objects": N, "duration_s": args.duration,
+            "ptf_per_s": ptf / end, "busy_s": end, "errors": errors[:3],
+            "latency_ms": {"p50": q(lat, 50), "p90": q(lat, 90), "p99": q(lat, 99),
+                           "max": float(np.nanmax(lat))},
+            "server_latency_ms": {"p50": q(lat_srv, 50), "p99": q(lat_srv, 99)},
+            "dtype": "f32", "data": "synthetic", "clocks": clk.summary(),
+            "config": {"workload": f"Poisson arrivals {args.rate:g}/s for {args.duration:g} s, "
+                                   f"n ~ logU(30, 3000), {nf} freqs in [0.05, 15), "
+                                   "variant per request Bernoulli(0.5), FP32C",
+                       "api": "ssp_server_submit / next / poll (host arrays)"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_ours(args)
 

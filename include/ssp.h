@@ -55,7 +55,9 @@ typedef enum {
     SSP_ERR_NOMEM = -2,       /* device memory budget exceeded */
     SSP_ERR_CUDA = -3,        /* a CUDA call failed */
     SSP_ERR_TIMEOUT = -4,     /* a bounded wait expired */
-    SSP_ERR_UNSUPPORTED = -5  /* valid request this build cannot run */
+    SSP_ERR_UNSUPPORTED = -5, /* valid request this build cannot run */
+    SSP_ERR_BUSY = -6,        /* serving: too many requests in flight */
+    SSP_PENDING = 1           /* serving: the request has not finished yet */
 } ssp_status;
 
 typedef struct {
@@ -150,6 +152,71 @@ int ssp_periodogram_device_noalloc(const double *t, const double *y, const doubl
                                    const double *freq_grid, int64_t n_freq, ssp_variant variant,
                                    const ssp_params *params, void *out_power,
                                    double *out_best_period, void *stream);
+
+/*
+ * Serving: one light curve per request, results collected asynchronously.
+ * (The paper's batches are whole catalogs, Sec. 4.3; a survey alert stream
+ * instead delivers objects one at a time.)  A server owns one frequency grid,
+ * one parameter set and a worker on the current device.  It gathers queued
+ * requests of one variant into a batch, at most max_batch_ptf points x
+ * frequencies.  Two batches are in flight at once: while one computes, the
+ * next is copied in.  Each batch runs the pipeline of ssp_periodogram_device.
+ * A request's results are identical to ssp_periodogram on that object alone,
+ * whatever else is in flight.
+ */
+typedef struct ssp_server ssp_server;
+typedef struct {
+    double max_batch_ptf;   /* cap on points x frequencies per batch; <= 0: 4e9 */
+    double max_wait_ms;     /* how long the oldest queued request may wait for
+                               more to arrive when a batch slot is free; <= 0:
+                               launch at once */
+    int64_t max_in_flight;  /* requests submitted and not yet collected by
+                               ssp_server_poll; <= 0: 1 << 20 */
+} ssp_server_config;
+
+/*
+ * Creates a server for freq_grid (host, n_freq values, copied) and params
+ * (NULL = defaults; copied); config NULL = defaults.  *out receives the
+ * handle.  Errors: SSP_ERR_ARG (grid or params), SSP_ERR_UNSUPPORTED,
+ * SSP_ERR_CUDA (no device).
+ */
+int ssp_server_create(const double *freq_grid, int64_t n_freq, const ssp_params *params,
+                      const ssp_server_config *config, ssp_server **out);
+
+/*
+ * Queues one object: t, y, dy are host arrays of n points, copied before the
+ * call returns.  *out_ticket receives the request's ticket (increasing from
+ * 1).  Errors: SSP_ERR_ARG (the value rules of ssp_periodogram, n outside
+ * 4..65535), SSP_ERR_UNSUPPORTED, SSP_ERR_BUSY (max_in_flight requests are
+ * submitted and not yet collected; nothing is queued).
+ */
+int ssp_server_submit(ssp_server *s, const double *t, const double *y, const double *dy,
+                      int64_t n, ssp_variant variant, int64_t *out_ticket);
+
+/*
+ * Waits up to wait_ms (0 = do not wait) for a request that has finished and
+ * was not reported by this call before; SSP_OK with its ticket in
+ * *out_ticket, or SSP_PENDING if none finished in time.
+ */
+int ssp_server_next(ssp_server *s, int wait_ms, int64_t *out_ticket);
+
+/*
+ * Waits up to wait_ms for request `ticket`.  SSP_OK: out_power (n_freq
+ * values, double for SSP_FP64 and float for SSP_FP32C) and
+ * *out_best_period hold the results, *out_latency_ms (if not NULL) the time
+ * from submission to completion, and the ticket is retired.  SSP_PENDING: not
+ * finished yet.  The request's own error status (e.g. SSP_ERR_NOMEM) if its
+ * batch failed; the ticket is retired.  SSP_ERR_ARG: unknown or retired
+ * ticket.
+ */
+int ssp_server_poll(ssp_server *s, int64_t ticket, int wait_ms, void *out_power,
+                    double *out_best_period, double *out_latency_ms);
+
+/*
+ * Stops the worker after the batches already on the GPU complete; queued and
+ * uncollected requests are dropped.  Frees everything the server holds.
+ */
+int ssp_server_destroy(ssp_server *s);
 
 /* Static text for a status code. */
 const char *ssp_status_string(int status);

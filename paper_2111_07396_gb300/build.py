@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "libssp.so")
-SOURCES = ["ssp_api.cu", "ssp_fp32.cu", "ssp_fp64.cu", "ssp_redo.cu"]
+SOURCES = ["ssp_api.cu", "ssp_server.cu", "ssp_fp32.cu", "ssp_fp64.cu", "ssp_redo.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -2,6 +2,7 @@
 // launch planner (length buckets, work items, device-memory batches) and the
 // host/device entry points.  All arithmetic of the method runs in the kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -13,6 +14,7 @@
 
 #include "../../include/ssp.h"
 #include "ssp_fold.h"
+#include "ssp_internal.h"
 #include "ssp_launch.h"
 
 namespace ssp {
@@ -298,7 +300,7 @@ size_t workspace_bytes(const Plan &plan, int64_t n_obj, int64_t n_points, int64_
 
 // ---- per-phase event timers ----
 std::mutex g_prof_mu;
-bool g_prof_on = false;
+std::atomic<bool> g_prof_on{false};
 struct Mark {
     int phase;
     cudaEvent_t a, b;
@@ -339,6 +341,26 @@ void keep_pool_memory()
 
 
 // The whole device path of one batch, enqueued on stream s.
+// value rules for host inputs: finite t and y, finite dy > 0 whose weight is
+// finite (and within float range for SSP_FP32C)
+int check_values(const double *t, const double *y, const double *dy, int64_t N, int precision)
+{
+    for (int64_t i = 0; i < N; ++i) {
+        if (!std::isfinite(t[i]) || !std::isfinite(y[i]))
+            return fail(SSP_ERR_ARG, "t or y at point %lld is not finite", (long long)i);
+        if (!std::isfinite(dy[i]) || !(dy[i] > 0.0))
+            return fail(SSP_ERR_ARG, "dy at point %lld must be finite and > 0", (long long)i);
+        const double w = 1.0 / (dy[i] * dy[i]);
+        if (!(w > 0.0) || !std::isfinite(w))
+            return fail(SSP_ERR_ARG, "dy at point %lld gives a weight outside binary64", (long long)i);
+        if (precision == SSP_FP32C && !(w >= 1.1754943508222875e-38 && w <= 3.4028234663852886e38))
+            return fail(SSP_ERR_UNSUPPORTED,
+                        "dy at point %lld gives a weight outside float range; use SSP_FP64",
+                        (long long)i);
+    }
+    return SSP_OK;
+}
+
 int run_device(const double *t, const double *y, const double *dy, const int64_t *npo,
                int64_t n_obj, const double *freq, int64_t n_freq, ssp_variant variant,
                const ssp_params &P, void *out_power, double *out_best, cudaStream_t s)
@@ -635,6 +657,39 @@ std::once_flag g_pool_once;
 
 }  // namespace
 
+// entry points for the other translation units of the library (ssp_internal.h)
+namespace ssp_internal {
+int fail(int code, const char *msg) { return ::fail(code, "%s", msg); }
+std::string last_error() { return g_err; }
+void clear_error() { g_err.clear(); }
+int check_params(const ssp_params &p) { return ::check_params(&p); }
+int check_one_object(const ssp_params &p, const double *t, const double *y, const double *dy,
+                     int64_t n)
+{
+    int rc = ::check_shape(&n, 1, 1, SSP_SS);
+    if (rc) return rc;
+    if (!t || !y || !dy) return ::fail(SSP_ERR_ARG, "NULL array argument");
+    return ::check_values(t, y, dy, n, (int)p.precision);
+}
+int check_freq(const double *freq_grid, int64_t n_freq)
+{
+    if (!freq_grid) return ::fail(SSP_ERR_ARG, "NULL frequency grid");
+    if (n_freq < 1 || n_freq > (int64_t)1 << 31) return ::fail(SSP_ERR_ARG, "n_freq out of range");
+    for (int64_t q = 0; q < n_freq; ++q)
+        if (!std::isfinite(freq_grid[q]) || !(freq_grid[q] > 0.0))
+            return ::fail(SSP_ERR_ARG, "freq_grid[%lld] must be finite and > 0", (long long)q);
+    return SSP_OK;
+}
+int run(const double *t, const double *y, const double *dy, const int64_t *n_per_object,
+        int64_t n_objects, const double *freq, int64_t n_freq, ssp_variant variant,
+        const ssp_params &p, void *out_power, double *out_best, cudaStream_t s)
+{
+    std::call_once(g_pool_once, keep_pool_memory);
+    return ::run_device(t, y, dy, n_per_object, n_objects, freq, n_freq, variant, p, out_power,
+                        out_best, s);
+}
+}  // namespace ssp_internal
+
 extern "C" {
 
 void ssp_default_params(ssp_params *p)
@@ -658,6 +713,8 @@ const char *ssp_status_string(int status)
     case SSP_ERR_CUDA: return "CUDA error";
     case SSP_ERR_TIMEOUT: return "bounded wait expired";
     case SSP_ERR_UNSUPPORTED: return "unsupported request";
+    case SSP_ERR_BUSY: return "too many requests in flight";
+    case SSP_PENDING: return "pending";
     default: return "unknown status";
     }
 }
@@ -771,19 +828,8 @@ int ssp_periodogram(const double *t, const double *y, const double *dy,
         return fail(SSP_ERR_ARG, "NULL array argument");
     int64_t N = 0;
     for (int64_t o = 0; o < n_objects; ++o) N += n_per_object[o];
-    for (int64_t i = 0; i < N; ++i) {
-        if (!std::isfinite(t[i]) || !std::isfinite(y[i]))
-            return fail(SSP_ERR_ARG, "t or y at point %lld is not finite", (long long)i);
-        if (!std::isfinite(dy[i]) || !(dy[i] > 0.0))
-            return fail(SSP_ERR_ARG, "dy at point %lld must be finite and > 0", (long long)i);
-        const double w = 1.0 / (dy[i] * dy[i]);
-        if (!(w > 0.0) || !std::isfinite(w))
-            return fail(SSP_ERR_ARG, "dy at point %lld gives a weight outside binary64", (long long)i);
-        if (P.precision == SSP_FP32C && !(w >= 1.1754943508222875e-38 && w <= 3.4028234663852886e38))
-            return fail(SSP_ERR_UNSUPPORTED,
-                        "dy at point %lld gives a weight outside float range; use SSP_FP64",
-                        (long long)i);
-    }
+    rc = check_values(t, y, dy, N, (int)P.precision);
+    if (rc) return rc;
     for (int64_t q = 0; q < n_freq; ++q)
         if (!std::isfinite(freq_grid[q]) || !(freq_grid[q] > 0.0))
             return fail(SSP_ERR_ARG, "freq_grid[%lld] must be finite and > 0", (long long)q);

@@ -19,6 +19,7 @@ SSP_SS, SSP_SP = 0, 1
 SSP_FP64, SSP_FP32C = 0, 1
 SSP_OK, SSP_ERR_ARG, SSP_ERR_NOMEM, SSP_ERR_CUDA, SSP_ERR_TIMEOUT, SSP_ERR_UNSUPPORTED = (
     0, -1, -2, -3, -4, -5)
+SSP_ERR_BUSY, SSP_PENDING = -6, 1
 VARIANTS = {"ss": SSP_SS, "sp": SSP_SP, SSP_SS: SSP_SS, SSP_SP: SSP_SP}
 PRECISIONS = {"fp64": SSP_FP64, "fp32c": SSP_FP32C, SSP_FP64: SSP_FP64, SSP_FP32C: SSP_FP32C}
 
@@ -31,6 +32,11 @@ class ssp_params(ctypes.Structure):
 
 class ssp_phase_time(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
+class ssp_server_config(ctypes.Structure):
+    _fields_ = [("max_batch_ptf", ctypes.c_double), ("max_wait_ms", ctypes.c_double),
+                ("max_in_flight", ctypes.c_int64)]
 
 
 PHASES = ("prep", "pgram_ss", "pgram_sp", "redo", "argmax")
@@ -77,6 +83,17 @@ def lib():
         L.ssp_profile_enable.restype = None
         L.ssp_profile_read.argtypes = [ctypes.POINTER(ssp_phase_time), ctypes.c_int]
         L.ssp_profile_read.restype = ctypes.c_int
+        L.ssp_server_create.argtypes = [P, i64, ctypes.POINTER(ssp_params),
+                                        ctypes.POINTER(ssp_server_config), ctypes.POINTER(P)]
+        L.ssp_server_create.restype = ctypes.c_int
+        L.ssp_server_submit.argtypes = [P, P, P, P, i64, ctypes.c_int, ctypes.POINTER(i64)]
+        L.ssp_server_submit.restype = ctypes.c_int
+        L.ssp_server_next.argtypes = [P, ctypes.c_int, ctypes.POINTER(i64)]
+        L.ssp_server_next.restype = ctypes.c_int
+        L.ssp_server_poll.argtypes = [P, i64, ctypes.c_int, P, P, P]
+        L.ssp_server_poll.restype = ctypes.c_int
+        L.ssp_server_destroy.argtypes = [P]
+        L.ssp_server_destroy.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -200,6 +217,74 @@ def ssp_periodogram_device_noalloc(t, y, dy, n_per_object, freq_grid, out_power,
         _dev_ptr(out_best_period), ctypes.c_void_p(s))
     _check(rc)
     return out_power, out_best_period
+
+
+class Server:
+    """The serving API (ssp_server_create / submit / next / poll / destroy):
+    one light curve per request, results collected asynchronously.  Host
+    numpy arrays in and out; the batching, copies and kernels are the
+    library's."""
+
+    def __init__(self, freq_grid, precision="fp32c", alpha=9.0, spans=None, params=None,
+                 max_batch_ptf=0.0, max_wait_ms=0.0, max_in_flight=0):
+        self._p = params if params is not None else ssp_default_params(precision, alpha, spans)
+        self.freq = _f64(freq_grid)
+        self.n_freq = int(self.freq.size)
+        self.dtype = np.float64 if self._p.precision == SSP_FP64 else np.float32
+        cfg = ssp_server_config(float(max_batch_ptf), float(max_wait_ms), int(max_in_flight))
+        h = ctypes.c_void_p()
+        _check(lib().ssp_server_create(_ptr(self.freq), self.n_freq, ctypes.byref(self._p),
+                                       ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def ssp_server_submit(self, t, y, dy, variant="ss") -> int:
+        t_, y_, dy_ = _f64(t), _f64(y), _f64(dy)
+        if not (t_.size == y_.size == dy_.size):
+            raise ValueError("t, y and dy must have the same length")
+        ticket = ctypes.c_int64()
+        _check(lib().ssp_server_submit(self._h, _ptr(t_), _ptr(y_), _ptr(dy_), t_.size,
+                                       VARIANTS[variant], ctypes.byref(ticket)))
+        return int(ticket.value)
+
+    def ssp_server_next(self, wait_ms=0):
+        """Ticket of a finished request not reported before, or None."""
+        ticket = ctypes.c_int64()
+        rc = lib().ssp_server_next(self._h, int(wait_ms), ctypes.byref(ticket))
+        if rc == SSP_PENDING:
+            return None
+        _check(rc)
+        return int(ticket.value)
+
+    def ssp_server_poll(self, ticket, wait_ms=0):
+        """(power [n_freq], best_period, latency_ms) once finished, else None."""
+        power = np.empty(self.n_freq, dtype=self.dtype)
+        best, lat = ctypes.c_double(), ctypes.c_double()
+        rc = lib().ssp_server_poll(self._h, int(ticket), int(wait_ms), _ptr(power),
+                                   ctypes.byref(best), ctypes.byref(lat))
+        if rc == SSP_PENDING:
+            return None
+        _check(rc)
+        return power, float(best.value), float(lat.value)
+
+    def ssp_server_destroy(self) -> None:
+        if self._h:
+            h, self._h = self._h, None
+            _check(lib().ssp_server_destroy(h))
+
+    submit, next, poll, close = ssp_server_submit, ssp_server_next, ssp_server_poll, \
+        ssp_server_destroy
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _numel(a):

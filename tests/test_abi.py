@@ -93,3 +93,20 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(ssp, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         ssp.lib()
+
+
+def test_server_rejects_bad_grid_and_params_before_cuda():
+    with pytest.raises(ssp.SSPError) as ei:
+        ssp.Server([0.3, 0.0])
+    assert ei.value.status == ssp.SSP_ERR_ARG
+    with pytest.raises(ssp.SSPError) as ei:
+        ssp.Server([0.3, 0.4], alpha=-1.0)
+    assert ei.value.status == ssp.SSP_ERR_ARG
+    assert ssp.ssp_status_string(ssp.SSP_ERR_BUSY) == "too many requests in flight"
+    assert ssp.ssp_status_string(ssp.SSP_PENDING) == "pending"
+    assert ctypes.sizeof(ssp.ssp_server_config) == 24
+    # calls on a NULL handle are argument errors, not crashes
+    t = ctypes.c_int64()
+    assert ssp.lib().ssp_server_next(None, 0, ctypes.byref(t)) == ssp.SSP_ERR_ARG
+    assert ssp.lib().ssp_server_poll(None, 1, 0, None, None, None) == ssp.SSP_ERR_ARG
+    assert ssp.lib().ssp_server_destroy(None) == ssp.SSP_ERR_ARG
