@@ -22,6 +22,13 @@ curves (2,000 objects/s for 60 s by default, n ~ logU(30, 3000), 10^4
 frequencies, SS or SP per request) submitted through the C ABI's serving
 entry points (ssp_server_*), and prints sustained objects/s and the
 arrival-to-result latency percentiles as its own JSON line.
+
+--matrix c1,c2,c3,c4 measures each configuration for SS and SP in FP32C and
+FP64 through the device entry point (one JSON line per configuration and
+variant): throughput, roofline fraction, FP32C agreement with FP64, and the
+oracle on the host cores over a bounded sample.  C3 is autotuned first
+(ssp_autotune; its time is reported, not counted).  C4's FP64 leg runs on a
+subset of its objects.
 """
 from __future__ import annotations
 
@@ -67,6 +74,7 @@ def parse():
     ap.add_argument("--rate", type=float, default=2000.0, help="--serve: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="--serve: seconds of arrivals")
     ap.add_argument("--serve-freq", type=int, default=10_000, help="--serve: trial frequencies")
+    ap.add_argument("--matrix", default="", help="comma list of configurations (c1..c4)")
     return ap.parse_args()
 
 
@@ -138,13 +146,15 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-def cpu_baseline(cat, p32=None, budget_s=12.0, max_freq=4096):
+def cpu_baseline(cat, p32=None, budget_s=12.0, max_freq=4096, obj=0, variants=("ss", "sp")):
     """The FP64 oracle, as it stands, on the host cores over a bounded sample
-    of the workload's frequencies (both variants); with p32 (this run's FP32C
-    powers) also the oracle at a few sampled frequencies against them."""
+    of the workload's frequencies (both variants, or `variants`) for object
+    `obj`; with p32 (this run's FP32C powers of that object) also the oracle
+    at a few sampled frequencies against them."""
     import oracle
-    t, y, dy = cat.obj(0)
+    t, y, dy = cat.obj(obj)
     n = t.size
+    codes = [{"ss": oracle.SS, "sp": oracle.SP}[v] for v in variants]
     rng = np.random.default_rng(7)
     order = rng.permutation(cat.freq.size)
     cores = os.cpu_count() or 1
@@ -153,18 +163,21 @@ def cpu_baseline(cat, p32=None, budget_s=12.0, max_freq=4096):
     while done < max_freq and used < budget_s:
         fq = cat.freq[order[done:done + batch]]
         t0 = time.perf_counter()
-        for code in (oracle.SS, oracle.SP):
+        for code in codes:
             oracle.periodogram(t, y, dy, [n], fq, code, n_threads=cores)
         used += time.perf_counter() - t0
         done += fq.size
-    ptf = 2 * n * done
+    ptf = len(codes) * n * done
     out = {"value": ptf / used, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"{done} of {cat.freq.size} frequencies (random), SS+SP, n={n}, "
+           "sample": f"{done} of {cat.freq.size} frequencies (random), "
+                     f"{'+'.join(v.upper() for v in variants)}, object {obj} (n={n}), "
                      f"{used:.1f} s wall"}
     if p32 is not None:
         from tests.parity import gate_error, oracle_powers, sample_freqs
         chk = {}
         for v, code in (("ss", oracle.SS), ("sp", oracle.SP)):
+            if v not in p32:
+                continue
             qs = sample_freqs(cat.freq.size, 12, seed=5, include=[int(np.argmax(p32[v]))])
             ref = oracle_powers(t, y, dy, cat.freq[qs], code)
             chk[v] = {"frequencies": int(qs.size), "max_gate_err": gate_error(p32[v][qs], ref)}
@@ -460,12 +473,104 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+def run_matrix(args):
+    """Per configuration and variant: FP32C and FP64 through the device entry
+    point, agreement, roofline fraction and a bounded oracle sample."""
+    import torch
+
+    from paper_2111_07396_gb300 import build as ssp_build
+    from paper_2111_07396_gb300 import ssp, synth
+    from tests.parity import gate_error
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    ssp_build.build()
+    ssp.lib()
+    dev = torch.device("cuda", 0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    gens = {"c1": synth.config1, "c2": synth.config2, "c3": synth.config3, "c4": synth.config4}
+    stream = torch.cuda.Stream(device=dev)
+    for name in [c for c in args.matrix.split(",") if c]:
+        cat = gens[name]()
+        N, nf = int(cat.n_per_object.size), int(cat.freq.size)
+        put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        fq = put(cat.freq)
+        sub = cat if name != "c4" else cat.subset(list(range(min(N, 40))))
+        for v in ("ss", "sp"):
+            tune = None
+            if name == "c3":
+                t0 = time.perf_counter()
+                g = ssp.ssp_autotune(cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq, variant=v,
+                                     budget_ptf=1e9)
+                tune = {"seconds": time.perf_counter() - t0, "threads_per_range": g.tolist()}
+
+            def timed(c, precision):
+                tdev, ydev, dydev = put(c.t), put(c.y), put(c.dy)
+                dt = torch.float64 if precision == "fp64" else torch.float32
+                pw = torch.empty((c.n_per_object.size, nf), dtype=dt, device=dev)
+                bp = torch.empty(c.n_per_object.size, dtype=torch.float64, device=dev)
+                with torch.cuda.stream(stream):
+                    ssp.ssp_periodogram_device(tdev, ydev, dydev, c.n_per_object, fq, pw, bp,
+                                               variant=v, precision=precision, stream=stream)
+                    stream.synchronize()
+                    ssp.ssp_profile_read(True)
+                    ssp.ssp_profile_enable(True)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ssp.ssp_periodogram_device(tdev, ydev, dydev, c.n_per_object, fq, pw, bp,
+                                               variant=v, precision=precision, stream=stream)
+                    e1.record(stream)
+                    stream.synchronize()
+                    ssp.ssp_profile_enable(False)
+                    prof = ssp.ssp_profile_read(True)
+                ms = e0.elapsed_time(e1)
+                return pw.cpu().numpy(), bp.cpu().numpy(), ms, prof
+
+            with ClockSampler(0) as clk:
+                p32, b32, ms32, prof32 = timed(cat, "fp32c")
+            p64s, b64s, ms64, _ = timed(sub, "fp64")
+            ptf = float(np.sum(cat.n_per_object)) * nf
+            ptf_sub = float(np.sum(sub.n_per_object)) * nf
+            ns = int(sub.n_per_object.size)
+            p32s = p32[:ns]
+            clocks = clk.summary()
+            mhz = clocks["sm_mhz"] if clocks else 1432.0
+            peak = FP32_LANES_PER_SM * sms * mhz * 1e6 / 1e12
+            kname = "pgram_" + v
+            k_ms = prof32[kname][1]
+            same = float(np.mean(np.argmax(p32s, axis=1) == np.argmax(p64s, axis=1)))
+            big = int(np.argmax(cat.n_per_object))
+            cpu = cpu_baseline(cat, budget_s=8.0, max_freq=512, obj=big, variants=(v,))
+            line = {"metric": "point*frequency evals/s", "config": name, "variant": v,
+                    "objects": N, "points": int(np.sum(cat.n_per_object)), "n_freq": nf,
+                    "fp32c": {"value": ptf / (ms32 / 1e3), "ms": ms32,
+                              "kernel_ms": k_ms, "redo_ms": prof32["redo"][1]},
+                    "fp64": {"value": ptf_sub / (ms64 / 1e3), "ms": ms64,
+                             "objects": ns},
+                    "fp32c_vs_fp64": {"max_gate_err": gate_error(p32s, p64s),
+                                      "max_abs_err": float(np.max(np.abs(p32s - p64s))),
+                                      "best_index_same": same,
+                                      "best_period_same": float(np.mean(b32[:ns] == b64s))},
+                    "roofline": {"bound": "alu", "ops_per_ptf": OPS_PER_PTF[v],
+                                 "achieved": OPS_PER_PTF[v] * ptf / (k_ms / 1e3) / 1e12,
+                                 "peak": peak, "unit": "TFLOP/s",
+                                 "frac": OPS_PER_PTF[v] * ptf / (k_ms / 1e3) / 1e12 / peak},
+                    "autotune": tune, "clocks": clocks,
+                    "cpu_baseline": cpu}
+            print(json.dumps(line), flush=True)
+            if name == "c3":
+                ssp.ssp_autotune_clear()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.serve:
         run_serve(args)
+    elif args.matrix:
+        run_matrix(args)
     else:
         run_ours(args)
 

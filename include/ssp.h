@@ -218,6 +218,29 @@ int ssp_server_poll(ssp_server *s, int64_t ticket, int wait_ms, void *out_power,
  */
 int ssp_server_destroy(ssp_server *s);
 
+/*
+ * Autotuning of the launch plan.  Objects are planned in five length ranges
+ * (n <= 384, <= 768, <= 1536, <= 2048, larger); each range runs one launch
+ * whose threads per CTA follow a fixed rule by default.  ssp_autotune times
+ * the rule's choice, half of it and double it (within 32..512, at least two
+ * centres per thread) for every range that the given objects (host arrays,
+ * as ssp_periodogram) occupy.  The timing runs the full device pipeline on
+ * those objects and an evenly spaced sample of freq_grid, about budget_ptf
+ * points x frequencies per range (<= 0: 2e9); each candidate is run three
+ * times and the last two are timed.  The fastest choice is kept for later
+ * calls with this precision and variant in this process.
+ * out_group_sizes (may be NULL) receives the five ranges' threads per CTA
+ * after tuning.  Results of later calls stay within the precision's
+ * tolerance but are not bitwise those of the rule, because the chunking
+ * changes rounding.  Call it before other work, not concurrently with it.
+ * Errors: as ssp_periodogram.
+ */
+int ssp_autotune(const double *t, const double *y, const double *dy, const int64_t *n_per_object,
+                 int64_t n_objects, const double *freq_grid, int64_t n_freq, ssp_variant variant,
+                 const ssp_params *params, double budget_ptf, int32_t *out_group_sizes);
+/* Forgets every tuned choice: the fixed rule applies again. */
+void ssp_autotune_clear(void);
+
 /* Static text for a status code. */
 const char *ssp_status_string(int status);
 /* Detail of the last error returned on the calling thread ("" if none). */

@@ -136,31 +136,46 @@ int check_shape(const int64_t *n_per_object, int64_t n_objects, int64_t n_freq, 
     return SSP_OK;
 }
 
-// threads per CTA for an object of n points: about a dozen centres per thread
-// (SSP_GROUP_SCALE, a power of two, scales the choice for calibration).  SS
-// objects above 2048 points take 512 threads: the SS frame of such an object
-// leaves room for one CTA per SM, and 16 warps hide more latency than 8.
-int group_size_base(int n, int variant);
+// Objects are planned in length ranges; the objects of one range share a
+// launch.  Threads per CTA by default: about a dozen centres per thread
+// (SSP_GROUP_SCALE, a power of two, scales the rule for calibration).  FP32C
+// SS objects above 2048 points take 512 threads: their frame leaves room for
+// one CTA per SM, and 16 warps hide more latency than 8 (the FP64 kernel,
+// bound by its FP64 pipe, runs slower that way).  ssp_autotune
+// replaces the rule per (precision, variant, range) with measured choices.
+constexpr int kRanges = 5;
+constexpr int kRangeMax[kRanges] = {384, 768, 1536, 2048, 65535};
+std::atomic<int> g_tuned[2][2][kRanges];   // [precision][variant][range]; 0 = rule
 
-int group_size(int n, int variant)
+int range_of(int n)
+{
+    for (int r = 0; r < kRanges; ++r)
+        if (n <= kRangeMax[r]) return r;
+    return kRanges - 1;
+}
+
+int group_size_rule(int n, int variant, int precision)
 {
     static const int scale = [] {
         const char *e = std::getenv("SSP_GROUP_SCALE");
         const int v = e ? std::atoi(e) : 0;
         return (v == 2 || v == 4 || v == -2 || v == -4) ? v : 1;
     }();
-    int g = group_size_base(n, variant);
+    int g;
+    if (n <= 384) g = 32;
+    else if (n <= 768) g = 64;
+    else if (n <= 1536) g = 128;
+    else if (variant == SSP_SS && precision == SSP_FP32C && n > 2048) g = 512;
+    else g = 256;
     if (scale > 1) g = std::min(512, g * scale);
     if (scale < 0) g = std::max(32, g / -scale);
     return g;
 }
-int group_size_base(int n, int variant)
+
+int group_size(int n, int variant, int precision)
 {
-    if (n <= 384) return 32;
-    if (n <= 768) return 64;
-    if (n <= 1536) return 128;
-    if (variant == SSP_SS && n > 2048) return 512;
-    return 256;
+    const int t = g_tuned[precision == SSP_FP64 ? 0 : 1][variant][range_of(n)].load();
+    return t ? t : group_size_rule(n, variant, precision);
 }
 
 struct LaunchCfg {
@@ -221,15 +236,16 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
     if (rc) return rc;
     plan.buckets.clear();
     plan.redo = precision == SSP_FP32C;
-    for (int G : {32, 64, 128, 256, 512}) {
+    for (int r = 0; r < kRanges; ++r) {
         Bucket b;
-        b.G = G;
         for (int64_t o = 0; o < n_obj; ++o)
-            if (group_size((int)npo[o], variant) == G) {
+            if (range_of((int)npo[o]) == r) {
                 b.objects.push_back((int)o);
                 b.n_max = std::max(b.n_max, (int)npo[o]);
             }
-        if (!b.objects.empty()) plan.buckets.push_back(std::move(b));
+        if (b.objects.empty()) continue;
+        b.G = group_size(b.n_max, variant, precision);
+        plan.buckets.push_back(std::move(b));
     }
     plan.items_total = 0;
     plan.slab_total = 0;
@@ -291,6 +307,7 @@ size_t workspace_bytes(const Plan &plan, int64_t n_obj, int64_t n_points, int64_
     b += align16(rsize(precision) * (size_t)n_points) * 2;  // yc, wv
     if (plan.redo) b += align16(8 * (size_t)n_points) * 2;  // FP64 copies
     b += align16(8 * (size_t)n_obj);                        // chi0
+    b += align16(8 * (size_t)n_obj);                        // ymax
     b += align16(sizeof(int4) * plan.items_total);
     b += align16(8 * plan.buckets.size() + 8);              // two counters per bucket
     if (plan.redo) b += align16((size_t)n_obj * (size_t)n_freq);  // near flags
@@ -393,6 +410,7 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
     double *d_yc64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
     double *d_wv64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
     double *d_chi0 = (double *)take(8 * (size_t)n_obj);
+    double *d_ymax = (double *)take(8 * (size_t)n_obj);
     int4 *d_items = (int4 *)take(sizeof(int4) * plan.items_total);
     const size_t n_counters = 2 * plan.buckets.size() + 2;
     int *d_counters = (int *)take(4 * n_counters);
@@ -422,6 +440,7 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
         pa.yc64 = d_yc64;
         pa.wv64 = d_wv64;
         pa.chi0 = d_chi0;
+        pa.ymax = d_ymax;
         pa.bad = d_bad;
         Mark mk;
         bool on = prof_begin(SSP_PHASE_PREP, s, mk);
@@ -436,6 +455,7 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
             ga.yc = d_yc;
             ga.wv = d_wv;
             ga.chi0 = d_chi0;
+            ga.ymax = d_ymax;
             ga.yc64 = d_yc64;
             ga.wv64 = d_wv64;
             ga.bad = d_bad;
@@ -568,6 +588,7 @@ int run_device_noalloc(const double *t, const double *y, const double *dy, const
     double *d_yc64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
     double *d_wv64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
     double *d_chi0 = (double *)take(8 * (size_t)n_obj);
+    double *d_ymax = (double *)take(8 * (size_t)n_obj);
     int4 *d_items = (int4 *)take(sizeof(int4) * plan.items_total);
     const size_t n_counters = 2 * plan.buckets.size() + 2;
     int *d_counters = (int *)take(4 * n_counters);
@@ -597,6 +618,7 @@ int run_device_noalloc(const double *t, const double *y, const double *dy, const
         pa.yc64 = d_yc64;
         pa.wv64 = d_wv64;
         pa.chi0 = d_chi0;
+        pa.ymax = d_ymax;
         pa.bad = d_bad;
         if ((e = prep_launch(prec, pa, (int)n_obj, s))) break;
         size_t item_base = 0;
@@ -608,6 +630,7 @@ int run_device_noalloc(const double *t, const double *y, const double *dy, const
             ga.yc = d_yc;
             ga.wv = d_wv;
             ga.chi0 = d_chi0;
+            ga.ymax = d_ymax;
             ga.yc64 = d_yc64;
             ga.wv64 = d_wv64;
             ga.bad = d_bad;
@@ -905,6 +928,138 @@ int ssp_periodogram(const double *t, const double *y, const double *dy,
     if (status == SSP_OK && e != cudaSuccess) status = cuda_fail(e, "synchronize");
     cudaStreamDestroy(s);
     return status;
+}
+
+// ---------------------------------------------------------------------------
+// autotuning of the threads per CTA, per length range
+// ---------------------------------------------------------------------------
+int ssp_autotune(const double *t, const double *y, const double *dy, const int64_t *n_per_object,
+                 int64_t n_objects, const double *freq_grid, int64_t n_freq, ssp_variant variant,
+                 const ssp_params *params, double budget_ptf, int32_t *out_group_sizes)
+{
+    g_err.clear();
+    ssp_params P;
+    ssp_default_params(&P);
+    if (params) P = *params;
+    int rc = check_params(&P);
+    if (rc) return rc;
+    rc = check_shape(n_per_object, n_objects, n_freq, variant);
+    if (rc) return rc;
+    if (!t || !y || !dy || !freq_grid) return fail(SSP_ERR_ARG, "NULL array argument");
+    if (!(budget_ptf > 0.0)) budget_ptf = 2.0e9;
+    std::vector<int64_t> off((size_t)n_objects + 1, 0);
+    for (int64_t o = 0; o < n_objects; ++o) off[o + 1] = off[o] + n_per_object[o];
+    rc = check_values(t, y, dy, off[n_objects], (int)P.precision);
+    if (rc) return rc;
+    for (int64_t q = 0; q < n_freq; ++q)
+        if (!std::isfinite(freq_grid[q]) || !(freq_grid[q] > 0.0))
+            return fail(SSP_ERR_ARG, "freq_grid[%lld] must be finite and > 0", (long long)q);
+    std::call_once(g_pool_once, keep_pool_memory);
+    const int pi = P.precision == SSP_FP64 ? 0 : 1, vi = (int)variant;
+    const size_t rs = rsize((int)P.precision);
+    cudaStream_t s;
+    SSP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int status = SSP_OK;
+    for (int r = 0; r < kRanges && status == SSP_OK; ++r) {
+        std::vector<int64_t> objs;
+        for (int64_t o = 0; o < n_objects; ++o)
+            if (range_of((int)n_per_object[o]) == r) objs.push_back(o);
+        if (objs.empty()) continue;
+        // the range's objects (in order, up to the budget at 64 frequencies
+        // each) on an evenly spaced sample of the grid: enough (object,
+        // frequency) pairs to fill the GPU, about budget_ptf of work
+        std::vector<int64_t> npo;
+        int64_t pts = 0;
+        int n_max = 0;
+        for (int64_t o : objs) {
+            if (!npo.empty() && (double)(pts + n_per_object[o]) * 64.0 > budget_ptf) break;
+            npo.push_back(n_per_object[o]);
+            pts += n_per_object[o];
+            n_max = std::max(n_max, (int)n_per_object[o]);
+        }
+        const int64_t nob = (int64_t)npo.size();
+        int64_t F = (int64_t)(budget_ptf / (double)pts);
+        F = std::max<int64_t>(F, (4096 + nob - 1) / nob);
+        F = std::max<int64_t>(64, std::min<int64_t>(F, n_freq));
+        std::vector<double> ht((size_t)pts), hy((size_t)pts), hdy((size_t)pts), hf((size_t)F);
+        int64_t at = 0;
+        for (size_t k = 0; k < npo.size(); ++k) {
+            const int64_t o = objs[k], n = n_per_object[o];
+            std::memcpy(&ht[(size_t)at], t + off[o], 8 * (size_t)n);
+            std::memcpy(&hy[(size_t)at], y + off[o], 8 * (size_t)n);
+            std::memcpy(&hdy[(size_t)at], dy + off[o], 8 * (size_t)n);
+            at += n;
+        }
+        for (int64_t q = 0; q < F; ++q) hf[(size_t)q] = freq_grid[(q * n_freq) / F];
+        unsigned char *blk = nullptr;
+        const size_t a = align16(8 * (size_t)pts), bf = align16(8 * (size_t)F),
+                     bp = align16(rs * (size_t)nob * (size_t)F), bb = align16(8 * (size_t)nob);
+        cudaError_t e = cudaMallocAsync((void **)&blk, 3 * a + bf + bp + bb, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            status = fail(SSP_ERR_NOMEM, "autotune sample does not fit");
+            break;
+        }
+        double *dt = (double *)blk, *dyv = (double *)(blk + a), *ddy = (double *)(blk + 2 * a);
+        double *df = (double *)(blk + 3 * a);
+        void *dpw = blk + 3 * a + bf;
+        double *dbest = (double *)(blk + 3 * a + bf + bp);
+        cudaMemcpyAsync(dt, ht.data(), 8 * (size_t)pts, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(dyv, hy.data(), 8 * (size_t)pts, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(ddy, hdy.data(), 8 * (size_t)pts, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(df, hf.data(), 8 * (size_t)F, cudaMemcpyHostToDevice, s);
+        // candidates around the rule: half, same, double, within 32..512 and
+        // with at least two centres per thread
+        const int g0 = group_size_rule(n_max, vi, (int)P.precision);
+        std::vector<int> cand;
+        for (int g : {g0 / 2, g0, g0 * 2})
+            if (g >= 32 && g <= 512 && (g == g0 || 2 * g <= std::max(64, n_max))) cand.push_back(g);
+        const int prev = g_tuned[pi][vi][r].load();
+        int best_g = g0;
+        float best_ms = 0.f;
+        for (int g : cand) {
+            g_tuned[pi][vi][r].store(g);
+            float ms = 0.f;
+            for (int rep = 0; rep < 3 && status == SSP_OK; ++rep) {
+                if (rep == 1) cudaEventRecord(e0, s);
+                rc = run_device(dt, dyv, ddy, npo.data(), nob, df, F, variant, P, dpw, dbest, s);
+                if (rc) status = rc;
+            }
+            if (status != SSP_OK) break;
+            cudaEventRecord(e1, s);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+                status = cuda_fail(e, "autotune timing");
+                break;
+            }
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best_ms == 0.f || ms < best_ms) {
+                best_ms = ms;
+                best_g = g;
+            }
+        }
+        g_tuned[pi][vi][r].store(status == SSP_OK ? best_g : prev);
+        cudaFreeAsync(blk, s);
+    }
+    cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    if (out_group_sizes)
+        for (int r = 0; r < kRanges; ++r) {
+            const int tg = g_tuned[pi][vi][r].load();
+            out_group_sizes[r] = tg ? tg : group_size_rule(kRangeMax[r], vi, (int)P.precision);
+        }
+    return status;
+}
+
+void ssp_autotune_clear(void)
+{
+    for (auto &a : g_tuned)
+        for (auto &b : a)
+            for (auto &c : b) c.store(0);
 }
 
 }  // extern "C"

@@ -67,6 +67,7 @@ struct PgramArgs {
     const void *yc;         // [N] centred magnitudes, R
     const void *wv;         // [N] weights dy^-2, R
     const double *chi0;     // [n_obj]
+    const double *ymax;     // [n_obj] largest centred magnitude
     const double *yc64, *wv64;  // [N] binary64 inputs (FP32C: exact SP refits)
     const int *bad;         // [n_obj] nonzero: invalid input, NaN output
     const double *freq;     // [n_freq]
@@ -1273,6 +1274,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
         }
         // a point whose bound E on its chi2 change exceeds this is refitted
         const R sens_lim = (R)(a.sens_tau * a.chi0[obj]);
+        const R ymax = (R)a.ymax[obj];
         RunAvg<R, 1> ra;
         ra.reset(c0);
         auto emit = [&](int i, const R (&v)[1]) {
@@ -1305,7 +1307,19 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
                 val[0] = interpolate_span<R>(K, sp, s0, s1, s2);
                 if (sizeof(R) == 4 && y64) {
                     const R scale = fmax(fmax(fabs(yj), fabs(s0)), fabs(s1));
-                    contested = fabs(g0 - g1) <= (R)a.near_sp * (R)1.1920929e-7 * scale;
+                    // a tweeter/midrange near-tie: the window sums round at the
+                    // magnitudes they slide over, which the object's largest
+                    // centred magnitude bounds.  Settling the choice in binary64
+                    // only matters if the other choice could move chi2 by more
+                    // than the per-point budget: the smooth lies between the
+                    // three fits, so it moves by at most their spread R, and
+                    // w (y - v)^2 by at most w R (2 |y - v| + R).  A tie run
+                    // spreads the change over its members: always settled.
+                    if (fabs(g0 - g1) <= (R)a.near_sp * (R)1.1920929e-7 * fmax(scale, ymax)) {
+                        const R rs = fmax(fmax(s0, s1), s2) - fmin(fmin(s0, s1), s2);
+                        const bool in_run = ties && (tie_next(fr, j) || (j > 0 && tie_next(fr, j - 1)));
+                        contested = in_run || fr.WT[j] * rs * (R(2) * fabs(yj - val[0]) + rs) > sens_lim;
+                    }
                     // bound on the power change from the FP32 error of the
                     // residuals through bass enhancement and interpolation:
                     // each residual's error is its slope times the rounding

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a)
     }
     __syncthreads();
     const double ybar = swy / sw;
-    double c0 = 0.0;
+    double c0 = 0.0, ym = 0.0;
     R *yc = (R *)a.yc + base;
     R *wv = (R *)a.wv + base;
     for (int i = tid; i < n; i += blockDim.x) {
@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a)
         const double tt = __dsub_rn(t, tmin);
         const double d = y - ybar;
         c0 += w * d * d;
+        ym = fmax(ym, fabs(d));
         a.tt[base + i] = tt;
         yc[i] = (R)d;
         wv[i] = (R)w;
@@ -82,12 +83,20 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a)
         }
     }
     c0 = warp_sum(c0);
-    if (lane == 0) s_red[0][warp] = c0;
+    for (int off = 16; off > 0; off >>= 1) ym = fmax(ym, __shfl_xor_sync(0xffffffffu, ym, off));
+    if (lane == 0) {
+        s_red[0][warp] = c0;
+        s_red[1][warp] = ym;
+    }
     __syncthreads();
     if (tid == 0) {
-        double c = 0.0;
-        for (int k = 0; k < nw; ++k) c += s_red[0][k];
+        double c = 0.0, m = 0.0;
+        for (int k = 0; k < nw; ++k) {
+            c += s_red[0][k];
+            m = fmax(m, s_red[1][k]);
+        }
         a.chi0[o] = c;
+        a.ymax[o] = m;
         a.bad[o] = bad;
     }
 }

@@ -16,6 +16,7 @@ struct PrepArgs {
     void *yc, *wv;             // [N] R: centred magnitudes, weights
     double *yc64, *wv64;       // [N] FP64 copies for the FP32C recompute (or null)
     double *chi0;              // [n_obj]
+    double *ymax;              // [n_obj] largest |y - ybar_w|
     int *bad;                  // [n_obj]
 };
 

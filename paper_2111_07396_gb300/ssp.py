@@ -94,6 +94,11 @@ def lib():
         L.ssp_server_poll.restype = ctypes.c_int
         L.ssp_server_destroy.argtypes = [P]
         L.ssp_server_destroy.restype = ctypes.c_int
+        L.ssp_autotune.argtypes = [P, P, P, P, i64, P, i64, ctypes.c_int,
+                                   ctypes.POINTER(ssp_params), ctypes.c_double, P]
+        L.ssp_autotune.restype = ctypes.c_int
+        L.ssp_autotune_clear.argtypes = []
+        L.ssp_autotune_clear.restype = None
         _lib = L
     return _lib
 
@@ -217,6 +222,24 @@ def ssp_periodogram_device_noalloc(t, y, dy, n_per_object, freq_grid, out_power,
         _dev_ptr(out_best_period), ctypes.c_void_p(s))
     _check(rc)
     return out_power, out_best_period
+
+
+def ssp_autotune(t, y, dy, n_per_object, freq_grid, variant="ss", precision="fp32c", alpha=9.0,
+                 spans=None, params=None, budget_ptf=0.0):
+    """Times the threads-per-CTA candidates of every length range these
+    objects occupy and keeps the fastest; returns the five ranges' choices."""
+    p = params if params is not None else ssp_default_params(precision, alpha, spans)
+    t_, y_, dy_, fq = _f64(t), _f64(y), _f64(dy), _f64(freq_grid)
+    npo = np.ascontiguousarray(n_per_object, dtype=np.int64)
+    out = np.zeros(5, dtype=np.int32)
+    _check(lib().ssp_autotune(_ptr(t_), _ptr(y_), _ptr(dy_), _ptr(npo), int(npo.size), _ptr(fq),
+                              int(fq.size), VARIANTS[variant], ctypes.byref(p), float(budget_ptf),
+                              _ptr(out)))
+    return out
+
+
+def ssp_autotune_clear() -> None:
+    lib().ssp_autotune_clear()
 
 
 class Server:

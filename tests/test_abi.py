@@ -110,3 +110,16 @@ def test_server_rejects_bad_grid_and_params_before_cuda():
     assert ssp.lib().ssp_server_next(None, 0, ctypes.byref(t)) == ssp.SSP_ERR_ARG
     assert ssp.lib().ssp_server_poll(None, 1, 0, None, None, None) == ssp.SSP_ERR_ARG
     assert ssp.lib().ssp_server_destroy(None) == ssp.SSP_ERR_ARG
+
+
+def test_autotune_rejects_bad_arguments_before_cuda():
+    t, y, dy = np.arange(8.0), np.ones(8), np.ones(8)
+    for kw, status in ((dict(n_per_object=[3], t=t[:3], y=y[:3], dy=dy[:3]), ssp.SSP_ERR_ARG),
+                       (dict(freq_grid=[0.3, 0.0]), ssp.SSP_ERR_ARG),
+                       (dict(dy=np.r_[np.ones(7), -1.0]), ssp.SSP_ERR_ARG)):
+        args = dict(t=t, y=y, dy=dy, n_per_object=[8], freq_grid=[0.3, 0.4])
+        args.update(kw)
+        with pytest.raises(ssp.SSPError) as ei:
+            ssp.ssp_autotune(**args)
+        assert ei.value.status == status
+    ssp.ssp_autotune_clear()   # needs no device
