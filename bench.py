@@ -58,6 +58,22 @@ UNIT = "pt*f/s"
 OPS_PER_PTF = {"ss": 3 * 49 + 3 * 40 + 40 + 40 + 8 + 8 + 3,
                "sp": 3 * 40 + 3 * 3 + 8 + 8 + 3}
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) per full-size launch of the FP32C periodogram
+# kernels, from one ncu capture (profiles/pgram_kernel_c2_n3000.md).  They
+# apply only to the kernel sources they were taken on: bench.py reports them
+# while the hash of those sources still matches, else null.
+TRAFFIC_SOURCES = ("ssp_device.cuh", "ssp_kernels.cuh", "ssp_fold.h", "ssp_launch.h", "ssp_fp32.cu")
+TRAFFIC = {"sha256": "02f5563d70a38f767e56af45aac37e261588ce89a8b5cb44d4fe8464b6213c69",
+           "ss": 1561600, "sp": 1174528 + 15614208}
+
+
+def traffic_per_launch(variant):
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2111_07396_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return TRAFFIC[variant] if h.hexdigest() == TRAFFIC["sha256"] else None
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -366,13 +382,22 @@ def run_ours(args):
     ach_ss = OPS_PER_PTF["ss"] * n * nf / (ss_ms / ss_launches / 1e3) / 1e12
     ach_sp = OPS_PER_PTF["sp"] * n * nf / (sp_ms / sp_launches / 1e3) / 1e12
     roof = {"bound": "alu", "kernel": "pgram_kernel<float,SS>", "achieved": ach_ss,
-            "peak": peak, "unit": "TFLOP/s", "frac": ach_ss / peak, "traffic": None,
+            "peak": peak, "unit": "TFLOP/s", "frac": ach_ss / peak,
+            "traffic": traffic_per_launch("ss"),
             "ops_per_ptf": OPS_PER_PTF["ss"], "avg_launch_ms": ss_ms / ss_launches,
             "peak_basis": f"{FP32_LANES_PER_SM} FP32 ops/clk/SM x {sms} SMs x "
                           f"{clk_mhz:.0f} MHz (median SM clock sampled during the timed region)",
             "sp": {"kernel": "pgram_kernel<float,SP>", "achieved": ach_sp,
                    "frac": ach_sp / peak, "ops_per_ptf": OPS_PER_PTF["sp"],
+                   "traffic": traffic_per_launch("sp"),
                    "avg_launch_ms": sp_ms / sp_launches}}
+
+    try:
+        f32, f64 = ssp.ssp_measure_alu_peaks()
+        roof["measured_fma_tflops"] = {"fp32": f32, "fp64": f64,
+                                       "how": "FMA-chain microbenchmark (2 flops per FMA)"}
+    except ssp.SSPError:
+        pass
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "libssp.so")
-SOURCES = ["ssp_api.cu", "ssp_server.cu", "ssp_fp32.cu", "ssp_fp64.cu", "ssp_redo.cu"]
+SOURCES = ["ssp_api.cu", "ssp_server.cu", "ssp_fp32.cu", "ssp_fp64.cu", "ssp_redo.cu",
+           "ssp_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -44,7 +45,7 @@ def _stale(target, deps):
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(ROOT, "include", "ssp.h"))
+    headers += [os.path.join(ROOT, "include", f) for f in ("ssp.h", "ssp_peaks.h")]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

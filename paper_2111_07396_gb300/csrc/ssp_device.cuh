@@ -1022,7 +1022,7 @@ __device__ inline R choose_span(const SpanK<R> &K, R r0, R r1, R r2, R res_woof,
     if (K.bass && below && resmin > R(0)) {
         R tmp = fdiv(resmin, res_woof);
         if (tmp < R(1.0e-7)) tmp = R(1.0e-7);
-        const R pw = (K.ex == R(1)) ? tmp : pow(tmp, K.ex);
+        const R pw = (K.ex == R(1)) ? tmp : (sizeof(R) == 4 ? (R)powf((float)tmp, (float)K.ex) : (R)pow((double)tmp, (double)K.ex));
         s += (K.s2 - s) * pw;
     }
     return s;
@@ -1182,8 +1182,15 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
             if (sizeof(R) == 8) {
                 x = (R)fr.ph[i];
             } else {
-                const uint64_t fx = ((uint64_t)kh << 32) | kl;
-                x = (R)(__ull2float_rz(fx) * 5.421010862427522e-20f);   // * 2^-64
+                // X = the phase truncated to float.  From 2^-8 up, the top
+                // word alone holds the float's 24 bits (its own truncation is
+                // the same); only tiny phases need the 64-bit conversion.
+                if (kh >= (1u << 24)) {
+                    x = (R)(__uint2float_rz(kh) * 2.3283064365386963e-10f);   // * 2^-32
+                } else {
+                    const uint64_t fx = ((uint64_t)kh << 32) | kl;
+                    x = (R)(__ull2float_rz(fx) * 5.421010862427522e-20f);    // * 2^-64
+                }
             }
             fr.X[j] = x;
             fr.WT[j] = wv[i];

@@ -99,6 +99,8 @@ def lib():
         L.ssp_autotune.restype = ctypes.c_int
         L.ssp_autotune_clear.argtypes = []
         L.ssp_autotune_clear.restype = None
+        L.ssp_measure_alu_peaks.argtypes = [P, P]
+        L.ssp_measure_alu_peaks.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -236,6 +238,15 @@ def ssp_autotune(t, y, dy, n_per_object, freq_grid, variant="ss", precision="fp3
                               int(fq.size), VARIANTS[variant], ctypes.byref(p), float(budget_ptf),
                               _ptr(out)))
     return out
+
+
+def ssp_measure_alu_peaks():
+    """(FP32, FP64) FMA-chain peaks of the current GPU in TFLOP/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    rc = lib().ssp_measure_alu_peaks(ctypes.byref(a), ctypes.byref(b))
+    if rc:
+        raise SSPError(rc, "ALU peak microbenchmark failed")
+    return a.value, b.value
 
 
 def ssp_autotune_clear() -> None:

@@ -180,3 +180,16 @@ def test_device_entry_marks_invalid_object_nan():
     p = pw.cpu().numpy()
     assert np.all(np.isnan(p[1])) and np.isnan(bp[1].item())
     assert np.all(np.isfinite(p[0])) and np.all(np.isfinite(p[2]))
+
+
+@pytest.mark.parametrize("obj,q", [(239, 1135), (2867, 752)])
+def test_sp_tweeter_midrange_near_tie(obj, q):
+    # Full-size C3 points whose tweeter and midrange GCV residuals agree to a
+    # few 1e-8: the FP32 choice must be settled as binary64 settles it.
+    cat = synth.config3(n_objects=obj + 1)
+    t, y, dy = cat.obj(obj)
+    qs = np.arange(max(0, q - 2), min(cat.freq.size, q + 3))
+    fq = cat.freq[qs]
+    got, _ = ssp.ssp_periodogram(t, y, dy, [t.size], fq, variant="sp", precision="fp32c")
+    ref, _ = oracle.periodogram(t, y, dy, [t.size], fq, oracle.SP)
+    assert gate_error(got, ref) <= TOL["fp32c"]
