@@ -68,9 +68,9 @@ def lib():
             L.ssp_oracle_supsmu_sp.argtypes = [i, P, P, P, i, d, P, P]
             L.ssp_oracle_chi2.argtypes = [i, P, P, P]
             L.ssp_oracle_chi2.restype = d
-            L.ssp_oracle_power_one.argtypes = [i, P, P, P, d, i, d, P]
+            L.ssp_oracle_power_one.argtypes = [i, P, P, P, d, i, d, P, i, d]
             L.ssp_oracle_power_one.restype = d
-            L.ssp_oracle_periodogram.argtypes = [P, P, P, P, i64, P, i64, i, d, P, i, P, P]
+            L.ssp_oracle_periodogram.argtypes = [P, P, P, P, i64, P, i64, i, d, P, i, d, i, P, P]
             L.ssp_oracle_periodogram.restype = i
             _lib = L
         return _lib
@@ -164,15 +164,17 @@ def chi2(y, w, smo):
     return lib().ssp_oracle_chi2(y.size, _p(y), _p(w), _p(smo))
 
 
-def power_one(t, y, dy, f, variant=SS, alpha=9.0, spans=None):
+def power_one(t, y, dy, f, variant=SS, alpha=9.0, spans=None, iper=2, span=0.0):
+    """Power at one frequency.  iper 2 = periodic windows, 1 = clamped;
+    span > 0 = Listing 1's fixed-span smooth (either variant)."""
     t, y, dy = _f64(t), _f64(y), _f64(dy)
     sp = _spans(spans)
     return lib().ssp_oracle_power_one(t.size, _p(t), _p(y), _p(dy), float(f), int(variant),
-                                      float(alpha), _p(sp))
+                                      float(alpha), _p(sp), int(iper), float(span))
 
 
 def periodogram(t, y, dy, n_per_object, freq, variant=SS, alpha=9.0, spans=None,
-                n_threads=None):
+                n_threads=None, iper=2, span=0.0):
     """Whole periodogram: returns (power[n_objects, n_freq], best_period[n_objects])."""
     t, y, dy, freq = _f64(t), _f64(y), _f64(dy), _f64(freq)
     npo = np.ascontiguousarray(n_per_object, dtype=np.int64)
@@ -183,8 +185,8 @@ def periodogram(t, y, dy, n_per_object, freq, variant=SS, alpha=9.0, spans=None,
         n_threads = os.cpu_count() or 1
     sp = _spans(spans)
     rc = lib().ssp_oracle_periodogram(_p(t), _p(y), _p(dy), _p(npo), nobj, _p(freq), nf,
-                                      int(variant), float(alpha), _p(sp), int(n_threads),
-                                      _p(power), _p(best))
+                                      int(variant), float(alpha), _p(sp), int(iper), float(span),
+                                      int(n_threads), _p(power), _p(best))
     if rc != 0:
         raise ValueError("oracle rejected the input (every object needs n >= 4)")
     return power, best

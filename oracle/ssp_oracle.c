@@ -378,7 +378,7 @@ double ssp_oracle_chi2(int n, const double *y, const double *w, const double *sm
 
 double ssp_oracle_power_prepped(int n, const double *tt, const double *y,
                                 const double *w, double chi0, double f, int variant,
-                                double alpha, const double spans[3])
+                                double alpha, const double spans[3], int iper, double span)
 {
     double *x = (double *)malloc(sizeof(double) * 4 * (size_t)n);
     int *perm = (int *)malloc(sizeof(int) * (size_t)n);
@@ -388,10 +388,12 @@ double ssp_oracle_power_prepped(int n, const double *tt, const double *y,
         ys[j] = y[perm[j]];
         ws[j] = w[perm[j]];
     }
-    if (variant == SSP_ORACLE_SP)
-        ssp_oracle_supsmu_sp(n, x, ys, ws, 2, alpha, spans, smo);
+    /* a fixed span (span > 0) is Listing 1's single smooth, whatever the
+     * variant: SP differs from SS only in how it chooses the span */
+    if (variant == SSP_ORACLE_SP && !(span > 0.0))
+        ssp_oracle_supsmu_sp(n, x, ys, ws, iper, alpha, spans, smo);
     else
-        ssp_oracle_supsmu(n, x, ys, ws, 2, 0.0, alpha, spans, smo);
+        ssp_oracle_supsmu(n, x, ys, ws, iper, span, alpha, spans, smo);
     double chi2 = ssp_oracle_chi2(n, ys, ws, smo);
     free(perm);
     free(x);
@@ -400,12 +402,14 @@ double ssp_oracle_power_prepped(int n, const double *tt, const double *y,
 }
 
 double ssp_oracle_power_one(int n, const double *t, const double *y, const double *dy,
-                            double f, int variant, double alpha, const double spans[3])
+                            double f, int variant, double alpha, const double spans[3],
+                            int iper, double span)
 {
     double *tt = (double *)malloc(sizeof(double) * 2 * (size_t)n);
     double chi0;
     ssp_oracle_prep(n, t, y, dy, tt, tt + n, &chi0);
-    double p = ssp_oracle_power_prepped(n, tt, y, tt + n, chi0, f, variant, alpha, spans);
+    double p = ssp_oracle_power_prepped(n, tt, y, tt + n, chi0, f, variant, alpha, spans, iper,
+                                        span);
     free(tt);
     return p;
 }
@@ -419,6 +423,8 @@ typedef struct {
     int variant;
     double alpha;
     const double *spans;
+    int iper;
+    double span;
     double *power;
     int64_t first, stride;
 } pgram_job;
@@ -433,7 +439,7 @@ static void *pgram_worker(void *arg)
         int n = (int)(J->off[o + 1] - a);
         J->power[k] = ssp_oracle_power_prepped(n, J->tt + a, J->y + a, J->w + a,
                                                J->chi0[o], J->freq[q], J->variant,
-                                               J->alpha, J->spans);
+                                               J->alpha, J->spans, J->iper, J->span);
     }
     return NULL;
 }
@@ -441,8 +447,8 @@ static void *pgram_worker(void *arg)
 int ssp_oracle_periodogram(const double *t, const double *y, const double *dy,
                            const int64_t *n_per_object, int64_t n_objects,
                            const double *freq, int64_t n_freq, int variant, double alpha,
-                           const double spans[3], int n_threads, double *out_power,
-                           double *out_best_period)
+                           const double spans[3], int iper, double span, int n_threads,
+                           double *out_power, double *out_best_period)
 {
     if (n_objects < 1 || n_freq < 1) return -1;
     int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_objects + 1));
@@ -463,7 +469,7 @@ int ssp_oracle_periodogram(const double *t, const double *y, const double *dy,
     pgram_job *jobs = (pgram_job *)malloc(sizeof(pgram_job) * (size_t)n_threads);
     for (int i = 0; i < n_threads; i++) {
         pgram_job J = {(int)n_objects, off, tt, y, w, chi0, freq, n_freq, variant, alpha,
-                       spans, out_power, i, n_threads};
+                       spans, iper, span, out_power, i, n_threads};
         jobs[i] = J;
         pthread_create(&th[i], NULL, pgram_worker, &jobs[i]);
     }

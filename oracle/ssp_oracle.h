@@ -44,17 +44,20 @@ void ssp_oracle_supsmu_sp(int n, const double *x, const double *y, const double 
                           int iper, double alpha, const double spans[3], double *smo);
 
 double ssp_oracle_chi2(int n, const double *y, const double *w, const double *smo);
+/* iper: 2 periodic windows, 1 windows clamped inside the data (Listing 1);
+ * span > 0: Listing 1's fixed-span single smooth, for either variant */
 double ssp_oracle_power_prepped(int n, const double *tt, const double *y,
                                 const double *w, double chi0, double f, int variant,
-                                double alpha, const double spans[3]);
+                                double alpha, const double spans[3], int iper, double span);
 double ssp_oracle_power_one(int n, const double *t, const double *y, const double *dy,
-                            double f, int variant, double alpha, const double spans[3]);
+                            double f, int variant, double alpha, const double spans[3],
+                            int iper, double span);
 /* whole periodogram, n_threads worker threads over (object, frequency) pairs */
 int ssp_oracle_periodogram(const double *t, const double *y, const double *dy,
                            const int64_t *n_per_object, int64_t n_objects,
                            const double *freq, int64_t n_freq, int variant, double alpha,
-                           const double spans[3], int n_threads, double *out_power,
-                           double *out_best_period);
+                           const double spans[3], int iper, double span, int n_threads,
+                           double *out_power, double *out_best_period);
 
 #ifdef __cplusplus
 }

@@ -120,3 +120,43 @@ def test_periodogram_row_equals_single_power():
 def test_rejects_short_objects():
     with pytest.raises(ValueError):
         oracle.periodogram([0, 1, 2], [1, 2, 3], [1, 1, 1], [3], [0.5])
+
+
+def _brute_power(t, y, dy, f, variant, iper, span):
+    from tests import brute
+    tt = t - t.min()
+    w = dy ** -2.0
+    p = tt * f
+    x = p - np.floor(p)
+    order = np.lexsort((np.arange(t.size), x))
+    xs, ys, ws = x[order], y[order], w[order]
+    if span > 0.0:
+        if xs[-1] <= xs[0]:
+            smo = np.full(t.size, np.sum(ws * ys) / np.sum(ws))
+        else:
+            smo, _ = brute.runline(xs, ys, ws, span, -iper, brute.vsmlsq_of(xs))
+    elif variant == oracle.SP:
+        smo = brute.supsmu_sp(xs, ys, ws, iper=iper)
+    else:
+        smo = brute.supsmu(xs, ys, ws, iper=iper)
+    ybar = np.sum(w * y) / np.sum(w)
+    chi0 = np.sum(w * (y - ybar) ** 2)
+    return 1.0 - np.sum(ws * (ys - smo) ** 2) / chi0
+
+
+@pytest.mark.parametrize("variant", [oracle.SS, oracle.SP])
+@pytest.mark.parametrize("iper,span", [(1, 0.0), (2, 0.3), (1, 0.3), (1, 0.05)])
+def test_periodogram_modes_match_brute_force(variant, iper, span):
+    # non-periodic windows (clamped inside the data) and the fixed-span
+    # single smooth of Listing 1, end to end through the periodogram driver
+    g = np.random.default_rng(11)
+    n = 23
+    t = np.sort(g.uniform(0, 40, n))
+    y = np.sin(2 * np.pi * t / 2.3) + g.normal(0, 0.2, n)
+    dy = g.uniform(0.1, 0.3, n)
+    freqs = np.array([0.11, 0.4347, 1.7])
+    got, _ = oracle.periodogram(t, y, dy, [n], freqs, variant, iper=iper, span=span)
+    for q, f in enumerate(freqs):
+        ref = _brute_power(t, y, dy, f, variant, iper, span)
+        assert abs(got[0, q] - ref) <= 1e-10 * max(1.0, abs(ref))
+        assert abs(oracle.power_one(t, y, dy, f, variant, iper=iper, span=span) - got[0, q]) <= 1e-15
