@@ -67,10 +67,16 @@ typedef struct {
     double alpha;        /* bass enhancement in [0, 10]; default 9 (Sec. 5.1);
                             0 disables it (Sec. 5.4, transits). */
     int periodic;        /* 1 (default): windows wrap around the phase circle
-                            (Listing 1 iper = 2).  0 is SSP_ERR_UNSUPPORTED. */
+                            (Listing 1 iper = 2).  0: each window is the
+                            2 ibw + 1 consecutive points slid to lie inside
+                            [0, n-1] (Listing 1 iper = 1). */
     ssp_precision precision; /* default SSP_FP32C */
     double hbm_fraction; /* beta of Eq. 1: fraction of free device memory the
                             host entry point may use; default 0.75 (Sec. 4.1) */
+    double span;         /* 0 (default): variable span (SS or SP).  In (0, 1]:
+                            Listing 1's fixed-span mode, one running-line smooth
+                            of that span, no cross-validation; the same for
+                            both variants. */
 } ssp_params;
 
 /* Fill *p with the defaults listed above. */

@@ -189,9 +189,12 @@ void ssp_oracle_runline_raw(int n, const double *x, const double *v, const doubl
         if (iper > 0) {
             /* cross-validated residual: exact leave-one-out residual of a
              * linear smoother; when the leverage reaches 1 the previous
-             * point's value is kept (0 for the first point) */
+             * point's value is kept (0 for the first point).  Leverage 1
+             * is exact for some windows (a point alone at one end of a
+             * clamped window, the rest tied), where 1 - w h is rounding
+             * noise of either sign: within 1e-10 of 1 counts as reached. */
             double den = 1.0 - w[j] * h;
-            if (den > 0.0) acvr[j] = fabs(v[j] - smo[j]) / den;
+            if (den > 1.0e-10) acvr[j] = fabs(v[j] - smo[j]) / den;
             else acvr[j] = (j > 0) ? acvr[j - 1] : 0.0;
         }
     }

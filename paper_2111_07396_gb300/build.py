@@ -17,8 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "libssp.so")
-SOURCES = ["ssp_api.cu", "ssp_server.cu", "ssp_fp32.cu", "ssp_fp64.cu", "ssp_redo.cu",
-           "ssp_peaks.cu"]
+SOURCES = ["ssp_api.cu", "ssp_server.cu", "ssp_fp32.cu", "ssp_fp32_clamp.cu", "ssp_fp64.cu",
+           "ssp_fp64_clamp.cu", "ssp_redo.cu", "ssp_redo_clamp.cu", "ssp_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -22,17 +22,23 @@ cudaError_t prep_launch_fp32(const PrepArgs &, int, cudaStream_t);
 cudaError_t prep_launch_fp64(const PrepArgs &, int, cudaStream_t);
 cudaError_t argmax_launch_fp32(const ArgmaxArgs &, int, cudaStream_t);
 cudaError_t argmax_launch_fp64(const ArgmaxArgs &, int, cudaStream_t);
-cudaError_t pgram_occupancy_fp32(int, bool, int, size_t, int *);
-cudaError_t pgram_occupancy_fp64(int, bool, int, size_t, int *);
-cudaError_t pgram_occupancy_redo(int, bool, int, size_t, int *);
-cudaError_t pgram_launch_fp32(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
-cudaError_t pgram_launch_fp64(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
-cudaError_t pgram_launch_redo(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_fp32_per(int, bool, int, size_t, int *);
+cudaError_t pgram_launch_fp32_per(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_fp32_clamp(int, bool, int, size_t, int *);
+cudaError_t pgram_launch_fp32_clamp(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_fp64_per(int, bool, int, size_t, int *);
+cudaError_t pgram_launch_fp64_per(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_fp64_clamp(int, bool, int, size_t, int *);
+cudaError_t pgram_launch_fp64_clamp(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_redo_per(int, bool, int, size_t, int *);
+cudaError_t pgram_launch_redo_per(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_redo_clamp(int, bool, int, size_t, int *);
+cudaError_t pgram_launch_redo_clamp(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
 size_t pgram_small_bytes_fp32(int, int);
-size_t pgram_small_bytes_fp64(int, int);
-size_t pgram_small_bytes_redo(int, int);
 size_t pgram_frame_bytes_fp32(int, int);
+size_t pgram_small_bytes_fp64(int, int);
 size_t pgram_frame_bytes_fp64(int, int);
+size_t pgram_small_bytes_redo(int, int);
 size_t pgram_frame_bytes_redo(int, int);
 
 cudaError_t prep_launch(int p, const PrepArgs &a, int n, cudaStream_t s)
@@ -43,18 +49,26 @@ cudaError_t argmax_launch(int p, const ArgmaxArgs &a, int n, cudaStream_t s)
 {
     return p == SSP_FP64 ? argmax_launch_fp64(a, n, s) : argmax_launch_fp32(a, n, s);
 }
-cudaError_t pgram_occupancy(int p, int v, bool g, int G, size_t smem, int *bps)
+cudaError_t pgram_occupancy(int p, int v, bool g, bool per, int G, size_t smem, int *bps)
 {
-    return p == SSP_FP64 ? pgram_occupancy_fp64(v, g, G, smem, bps)
-         : p == kPrecRedo ? pgram_occupancy_redo(v, g, G, smem, bps)
-                          : pgram_occupancy_fp32(v, g, G, smem, bps);
+    if (per)
+        return p == SSP_FP64 ? pgram_occupancy_fp64_per(v, g, G, smem, bps)
+             : p == kPrecRedo ? pgram_occupancy_redo_per(v, g, G, smem, bps)
+                              : pgram_occupancy_fp32_per(v, g, G, smem, bps);
+    return p == SSP_FP64 ? pgram_occupancy_fp64_clamp(v, g, G, smem, bps)
+         : p == kPrecRedo ? pgram_occupancy_redo_clamp(v, g, G, smem, bps)
+                          : pgram_occupancy_fp32_clamp(v, g, G, smem, bps);
 }
-cudaError_t pgram_launch(int p, int v, bool g, int grid, int G, size_t smem, const PgramArgs &a,
-                         cudaStream_t s)
+cudaError_t pgram_launch(int p, int v, bool g, bool per, int grid, int G, size_t smem,
+                         const PgramArgs &a, cudaStream_t s)
 {
-    return p == SSP_FP64 ? pgram_launch_fp64(v, g, grid, G, smem, a, s)
-         : p == kPrecRedo ? pgram_launch_redo(v, g, grid, G, smem, a, s)
-                          : pgram_launch_fp32(v, g, grid, G, smem, a, s);
+    if (per)
+        return p == SSP_FP64 ? pgram_launch_fp64_per(v, g, grid, G, smem, a, s)
+             : p == kPrecRedo ? pgram_launch_redo_per(v, g, grid, G, smem, a, s)
+                              : pgram_launch_fp32_per(v, g, grid, G, smem, a, s);
+    return p == SSP_FP64 ? pgram_launch_fp64_clamp(v, g, grid, G, smem, a, s)
+         : p == kPrecRedo ? pgram_launch_redo_clamp(v, g, grid, G, smem, a, s)
+                          : pgram_launch_fp32_clamp(v, g, grid, G, smem, a, s);
 }
 size_t pgram_small_bytes(int p, int G, int variant)
 {
@@ -112,8 +126,8 @@ int check_params(const ssp_params *p)
         return fail(SSP_ERR_ARG, "unknown precision %d", (int)p->precision);
     if (!(p->hbm_fraction > 0.0 && p->hbm_fraction <= 1.0))
         return fail(SSP_ERR_ARG, "hbm_fraction must be in (0, 1]");
-    if (p->periodic != 1)
-        return fail(SSP_ERR_UNSUPPORTED, "only periodic windows are implemented (periodic = 1)");
+    if (p->periodic != 0 && p->periodic != 1) return fail(SSP_ERR_ARG, "periodic must be 0 or 1");
+    if (!(p->span >= 0.0 && p->span <= 1.0)) return fail(SSP_ERR_ARG, "span must be in [0, 1]");
     return SSP_OK;
 }
 
@@ -145,7 +159,7 @@ int check_shape(const int64_t *n_per_object, int64_t n_objects, int64_t n_freq, 
 // replaces the rule per (precision, variant, range) with measured choices.
 constexpr int kRanges = 5;
 constexpr int kRangeMax[kRanges] = {384, 768, 1536, 2048, 65535};
-std::atomic<int> g_tuned[2][2][kRanges];   // [precision][variant][range]; 0 = rule
+std::atomic<int> g_tuned[2][3][kRanges];   // [precision][kernel variant][range]; 0 = rule
 
 int range_of(int n)
 {
@@ -170,6 +184,13 @@ int group_size_rule(int n, int variant, int precision)
     if (scale > 1) g = std::min(512, g * scale);
     if (scale < 0) g = std::max(32, g / -scale);
     return g;
+}
+
+// the kernel a request runs: SS, SP, or (a fixed span, either variant) the
+// single smooth
+int kernel_variant(ssp_variant v, const ssp_params &P)
+{
+    return P.span > 0.0 ? VAR_FIXED : (int)v;
 }
 
 int group_size(int n, int variant, int precision)
@@ -209,7 +230,7 @@ int device_limits(int *num_sms, size_t *max_smem)
 }
 
 // frame placement and persistent grid of one kernel for one bucket
-int configure(int precision, int variant, int G, int n_max, int sms, size_t max_smem,
+int configure(int precision, int variant, bool per, int G, int n_max, int sms, size_t max_smem,
               LaunchCfg &c)
 {
     const size_t small = align16(pgram_small_bytes(precision, G, variant));
@@ -218,7 +239,7 @@ int configure(int precision, int variant, int G, int n_max, int sms, size_t max_
     c.smem = c.gmem ? small : small + frame;
     c.slab_bytes = c.gmem ? frame : 0;
     int bps = 0;
-    cudaError_t e = pgram_occupancy(precision, variant, c.gmem, G, c.smem, &bps);
+    cudaError_t e = pgram_occupancy(precision, variant, c.gmem, per, G, c.smem, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy");
     if (bps < 1) return fail(SSP_ERR_NOMEM, "a CTA frame for n = %d does not fit", n_max);
     c.grid = bps * sms;
@@ -228,7 +249,7 @@ int configure(int precision, int variant, int G, int n_max, int sms, size_t max_
 // Length buckets (one launch each, sized for the bucket's largest object),
 // work items (object, frequency range) ordered longest first.
 int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision, int variant,
-               Plan &plan)
+               bool per, Plan &plan)
 {
     int sms = 0;
     size_t max_smem = 0;
@@ -250,10 +271,10 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
     plan.items_total = 0;
     plan.slab_total = 0;
     for (Bucket &b : plan.buckets) {
-        rc = configure(precision, variant, b.G, b.n_max, sms, max_smem, b.main);
+        rc = configure(precision, variant, per, b.G, b.n_max, sms, max_smem, b.main);
         if (rc) return rc;
         if (plan.redo) {
-            rc = configure(kPrecRedo, variant, b.G, b.n_max, sms, max_smem, b.redo);
+            rc = configure(kPrecRedo, variant, per, b.G, b.n_max, sms, max_smem, b.redo);
             if (rc) return rc;
         }
         const int resident = b.main.grid;
@@ -384,7 +405,9 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
 {
     const int prec = (int)P.precision;
     Plan plan;
-    int rc = build_plan(npo, n_obj, n_freq, prec, (int)variant, plan);
+    const int kv = kernel_variant(variant, P);
+    const bool per = P.periodic != 0;
+    int rc = build_plan(npo, n_obj, n_freq, prec, kv, per, plan);
     if (rc) return rc;
     std::vector<int64_t> off((size_t)n_obj + 1, 0);
     for (int64_t o = 0; o < n_obj; ++o) off[o + 1] = off[o] + npo[o];
@@ -477,10 +500,12 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
             ga.sens_ulps = near_margin("SSP_SENS_ULPS", ssp::kSensUlps);
             ga.sens_tau = near_margin("SSP_SENS_TAU", (float)ssp::kSensTau);
             ga.recompute = 0;
+            ga.periodic = P.periodic;
+            ga.span = P.span;
             slab_cur += b.main.gmem ? b.main.slab_bytes * (size_t)b.main.grid : 0;
             const int ph = variant == SSP_SP ? SSP_PHASE_PGRAM_SP : SSP_PHASE_PGRAM_SS;
             on = prof_begin(ph, s, mk);
-            if ((e = pgram_launch(prec, (int)variant, b.main.gmem, b.main.grid, b.G, b.main.smem,
+            if ((e = pgram_launch(prec, kv, b.main.gmem, per, b.main.grid, b.G, b.main.smem,
                                   ga, s)))
                 break;
             prof_end(on, mk, s);
@@ -494,7 +519,7 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
                 ga.recompute = 1;
                 slab_cur += b.redo.gmem ? b.redo.slab_bytes * (size_t)b.redo.grid : 0;
                 on = prof_begin(SSP_PHASE_REDO, s, mk);
-                if ((e = pgram_launch(kPrecRedo, (int)variant, b.redo.gmem, b.redo.grid, b.G,
+                if ((e = pgram_launch(kPrecRedo, kv, b.redo.gmem, per, b.redo.grid, b.G,
                                       b.redo.smem, ga, s)))
                     break;
                 prof_end(on, mk, s);
@@ -554,7 +579,9 @@ int run_device_noalloc(const double *t, const double *y, const double *dy, const
 {
     const int prec = (int)P.precision;
     Plan plan;
-    int rc = build_plan(npo, n_obj, n_freq, prec, (int)variant, plan);
+    const int kv = kernel_variant(variant, P);
+    const bool per = P.periodic != 0;
+    int rc = build_plan(npo, n_obj, n_freq, prec, kv, per, plan);
     if (rc) return rc;
     for (const Bucket &b : plan.buckets)
         if (b.main.gmem || (plan.redo && b.redo.gmem))
@@ -650,14 +677,16 @@ int run_device_noalloc(const double *t, const double *y, const double *dy, const
             ga.sens_ulps = near_margin("SSP_SENS_ULPS", ssp::kSensUlps);
             ga.sens_tau = near_margin("SSP_SENS_TAU", (float)ssp::kSensTau);
             ga.recompute = 0;
-            if ((e = pgram_launch(prec, (int)variant, false, b.main.grid, b.G, b.main.smem, ga, s)))
+            ga.periodic = P.periodic;
+            ga.span = P.span;
+            if ((e = pgram_launch(prec, kv, false, per, b.main.grid, b.G, b.main.smem, ga, s)))
                 break;
             if (plan.redo) {
                 ga.yc = d_yc64;
                 ga.wv = d_wv64;
                 ga.item_counter = d_counters + 2 * k + 1;
                 ga.recompute = 1;
-                if ((e = pgram_launch(kPrecRedo, (int)variant, false, b.redo.grid, b.G, b.redo.smem,
+                if ((e = pgram_launch(kPrecRedo, kv, false, per, b.redo.grid, b.G, b.redo.smem,
                                       ga, s)))
                     break;
             }
@@ -725,6 +754,7 @@ void ssp_default_params(ssp_params *p)
     p->periodic = 1;
     p->precision = SSP_FP32C;
     p->hbm_fraction = 0.75;
+    p->span = 0.0;
 }
 
 const char *ssp_status_string(int status)
@@ -955,7 +985,7 @@ int ssp_autotune(const double *t, const double *y, const double *dy, const int64
         if (!std::isfinite(freq_grid[q]) || !(freq_grid[q] > 0.0))
             return fail(SSP_ERR_ARG, "freq_grid[%lld] must be finite and > 0", (long long)q);
     std::call_once(g_pool_once, keep_pool_memory);
-    const int pi = P.precision == SSP_FP64 ? 0 : 1, vi = (int)variant;
+    const int pi = P.precision == SSP_FP64 ? 0 : 1, vi = kernel_variant(variant, P);
     const size_t rs = rsize((int)P.precision);
     cudaStream_t s;
     SSP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));

@@ -32,7 +32,9 @@
 
 namespace ssp {
 
-enum { VAR_SS = 0, VAR_SP = 1 };
+// kernel variants: SS (Listing 1), SP (Sec. 3), and Listing 1's fixed-span
+// single smooth, which is the same computation for both
+enum { VAR_SS = 0, VAR_SP = 1, VAR_FIXED = 2 };
 constexpr int kMaxThreads = 512;
 constexpr int kBucketRankMax = 64;   // larger buckets switch to the bitonic sort
 
@@ -82,6 +84,8 @@ struct PgramArgs {
     size_t slab_bytes;
     unsigned char *near;    // [n_obj][n_freq] FP32C: decision near a threshold
     int recompute;          // FP64 kernel: only flagged (o, q), float power out
+    int periodic;           // 1: periodic windows; 0: windows clamped inside the data
+    double span;            // > 0: Listing 1's fixed-span single smooth
     int power_f32;          // power array holds float
     float near_ss;          // SS margin for n <= 256 (scaled down above)
     float near_sp;          // SP margin in units of eps_fp32 * magnitude scale
@@ -122,7 +126,18 @@ struct Frame {
                                   // each sorted point (n <= 65535)
     uint32_t *cnt;          // bucket counts / starts
     double *ph;             // FP64 phase by original index
+    int per;                // windows wrap (periodic) or are clamped inside [0, n-1]
 };
+
+// first slot of the 2h+1-point window of centre j: j - h with periodic
+// wrap, else the window slid to lie inside the data (Listing 1 iper = 1)
+template <typename R>
+__device__ inline int win_lo(const Frame<R> &fr, int j, int h, int n)
+{
+    if (fr.per) return j - h;
+    const int lo = j - h;
+    return lo < 0 ? 0 : (lo > n - 1 - 2 * h ? n - 1 - 2 * h : lo);
+}
 
 __host__ __device__ inline size_t tie_words(int n) { return ((size_t)n + 31) / 32; }
 
@@ -161,7 +176,7 @@ __host__ __device__ inline size_t tie_offset(int n, int ncols)
 }
 
 // columns a variant keeps: SS uses X, WT, Y and C0..C6; SP only X, WT, Y
-__host__ __device__ inline int frame_cols(int variant) { return variant == VAR_SP ? 3 : 10; }
+__host__ __device__ inline int frame_cols(int variant) { return variant == VAR_SS ? 10 : 3; }
 
 template <typename R>
 __host__ __device__ inline size_t frame_bytes(int n, int variant)
@@ -191,6 +206,7 @@ __device__ inline Frame<R> carve_frame(unsigned char *base, int n, int variant)
     f.cnt = (uint32_t *)(s + 2 * a4 + ap);
     f.ph = (double *)(s + 2 * a4 + ap + align16(4 * (size_t)bucket_count(n)));
     f.tie = (uint32_t *)(base + tie_offset<R>(n, frame_cols(variant)));
+    f.per = 1;
     return f;
 }
 
@@ -292,7 +308,7 @@ struct Small {
 
 // channels a variant smooths at once: SS pass B smooths three residual
 // columns and their difference; SP only y
-__host__ __device__ inline int max_channels(int variant) { return variant == VAR_SP ? 1 : 4; }
+__host__ __device__ inline int max_channels(int variant) { return variant == VAR_SS ? 4 : 1; }
 
 template <typename A>
 __host__ __device__ inline size_t small_bytes(int G, int variant)
@@ -783,7 +799,7 @@ __device__ void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R, A> &
     for (int ch = 0; ch < NCH; ++ch) C[ch] = D[ch] = W;
     s.zero();
     // three segments of constant shift: slots before 0, inside, after n-1
-    const int ea = c - h, eb = c + h;
+    const int ea = win_lo(fr, c, h, n), eb = ea + 2 * h;
 #pragma unroll 1
     for (int seg = -1; seg <= 1; ++seg) {
         int pa, pb;
@@ -905,10 +921,11 @@ __device__ __noinline__ Fit<R, NCH> win_refit_fp64(const Frame<R> fr, const Chan
 #pragma unroll
     for (int c = 0; c < NCH; ++c) v[c] = cv.p[c];
     Fit<R, NCH> f;
+    const int lo = win_lo(fr, j, h, n);
     double sw = 0.0, swx = 0.0, swv[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) swv[c] = 0.0;
-    for (int e = j - h; e <= j + h; ++e) {
+    for (int e = lo; e <= lo + 2 * h; ++e) {
         int sh;
         int p = slot_point(e, n, sh);
         double w = (double)fr.WT[p], x = (double)fr.X[p] + sh;
@@ -921,7 +938,7 @@ __device__ __noinline__ Fit<R, NCH> win_refit_fp64(const Frame<R> fr, const Chan
     double sxx = 0.0, sxv[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) sxv[c] = 0.0;
-    for (int e = j - h; e <= j + h; ++e) {
+    for (int e = lo; e <= lo + 2 * h; ++e) {
         int sh;
         int p = slot_point(e, n, sh);
         double w = (double)fr.WT[p], dx = (double)fr.X[p] + sh - xm;
@@ -968,6 +985,9 @@ template <typename R, int NCH, bool DIFF = false>
 __device__ inline void win_slide(Win<R, NCH> &s, const Frame<R> &fr, const R *const *v, int j,
                                  int h, int n, R o)
 {
+    // a window clamped inside the data moves only while h <= j <= n - 2 - h,
+    // and then exactly as a periodic one does
+    if (!fr.per && (j < h || j > n - 2 - h)) return;
     win_add<R, NCH, DIFF>(s, fr, v, j - h, n, o, R(-1));
     win_add<R, NCH, DIFF>(s, fr, v, j + h + 1, n, o, R(1));
 }
@@ -1121,7 +1141,8 @@ __device__ __noinline__ double warp_fit_fp64(const Frame<R> fr, const double *y6
 {
     const int lane = threadIdx.x & 31;
     double sw = 0.0, sa = 0.0, sb = 0.0, sc = 0.0, sd = 0.0;
-    for (int e = j - h + lane; e <= j + h; e += 32) {
+    const int lo = win_lo(fr, j, h, n);
+    for (int e = lo + lane; e <= lo + 2 * h; e += 32) {
         int sh;
         const int p = slot_point(e, n, sh);
         const uint32_t i = fr.perm[p];
@@ -1151,6 +1172,40 @@ struct FreqResult {
     double chi2;
     bool near;   // FP32C: some decision fell within its margin
 };
+
+// Listing 1's fixed-span mode: one running-line smooth of y with span
+// a.span, no cross-validation, then chi2 (its own kernel variant).
+template <typename R, typename A>
+__device__ inline FreqResult fixed_span_pass(const PgramArgs &a, const Frame<R> &fr,
+                                             const Small<R, A> &sm, int n, int c0, int c1, R o,
+                                             R vsmlsq, bool ties, R rf)
+{
+    const int hs = half_width(n, a.span);
+    const R *vy[1] = {fr.Y};
+    KSum<R> chi2;
+    bool near = false;
+    build_xy_prefix(fr, sm, fr.Y, c0, c1, o);
+    __syncthreads();
+    if (c0 < c1) {
+        Win<R, 1> w;
+        win_init<R, 1>(w, fr, sm, vy, c0, hs, n, o);
+        RunAvg<R, 1> ra;
+        ra.reset(c0);
+        auto emit = [&](int i, const R (&v)[1]) {
+            const R d = fr.Y[i] - v[0];
+            chi2.add(fr.WT[i] * d * d);
+        };
+        for (int j = c0; j < c1; ++j) {
+            Fit<R, 1> f1;
+            win_fit_checked<R, 1>(f1, w, fr, vy, j, hs, n, o, vsmlsq, near, rf);
+            const R val[1] = {f1.s[0]};
+            run_push<R, 1>(ra, fr, j, ties, val, emit);
+            if (j + 1 < c1) win_slide<R, 1>(w, fr, vy, j, hs, n, o);
+        }
+    }
+    near = __syncthreads_or(near) != 0;
+    return FreqResult{block_sum(chi2.value(), sm.red), near};
+}
 
 // ---------------------------------------------------------------------------
 // one (object, frequency)
@@ -1250,6 +1305,9 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
     KSum<R> chi2;
     bool near = false;
     const R rf = (R)a.refit_frac;
+
+    if (VARIANT == VAR_FIXED)   // Listing 1's single smooth of y
+        return fixed_span_pass<R, A>(a, fr, sm, n, c0, c1, o, vsmlsq, ties, rf);
 
     if (VARIANT == VAR_SP) {
         // one sweep, three windows on y, generalized validation (Sec. 3)
@@ -1417,9 +1475,12 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
                 const R d2 = R(1) - wj * (f2.rW + f2.dxj * f2.dxj * f2.rS);
                 if (sizeof(R) == 4 && fmin(fmin(fabs(d0), fabs(d1)), fabs(d2)) < (R)kNearLev)
                     near = true;
-                fr.C[1][j] = d0 > R(0) ? fdiv(fabs(yj - f0.s[0]), d0) : R(-1);
-                fr.C[3][j] = d1 > R(0) ? fdiv(fabs(yj - f1.s[0]), d1) : R(-1);
-                fr.C[5][j] = d2 > R(0) ? fdiv(fabs(yj - f2.s[0]), d2) : R(-1);
+                // leverage within 1e-10 of 1 counts as 1 (it is exactly 1 for
+                // some clamped windows, and 1 - w h is then rounding noise);
+                // FP32C flags any 1 - w h below kNearLev for the FP64 redo
+                fr.C[1][j] = d0 > R(1e-10) ? fdiv(fabs(yj - f0.s[0]), d0) : R(-1);
+                fr.C[3][j] = d1 > R(1e-10) ? fdiv(fabs(yj - f1.s[0]), d1) : R(-1);
+                fr.C[5][j] = d2 > R(1e-10) ? fdiv(fabs(yj - f2.s[0]), d2) : R(-1);
                 const R val[3] = {f0.s[0], f1.s[0], f2.s[0]};
                 run_push<R, 3>(ra, fr, j, ties, val, emit);
                 if (j + 1 < c1) {
@@ -1527,7 +1588,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
 // FP32C launches flag frequencies whose decisions came within their margins;
 // the FP64 kernel's recompute launch then redoes exactly those frequencies
 // and overwrites their (float) power.
-template <typename R, int VARIANT, bool GMEM, bool PLAIN>
+template <typename R, int VARIANT, bool GMEM, bool PLAIN, bool PER>
 __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
 {
     typedef typename AccSel<R, PLAIN>::T A;
@@ -1546,7 +1607,8 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
         const int4 item = a.items[it];
         const int o = item.x;
         const int n = (int)(a.off[o + 1] - a.off[o]);
-        const Frame<R> fr = carve_frame<R>(big, n, VARIANT);
+        Frame<R> fr = carve_frame<R>(big, n, VARIANT);
+        fr.per = PER;
         const bool bad = a.bad[o] != 0;
         for (int q = item.y; q < item.z; ++q) {
             const int64_t at = (int64_t)o * a.n_freq + q;

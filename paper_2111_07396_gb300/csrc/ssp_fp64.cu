@@ -1,5 +1,7 @@
-// ssp_fp64.cu -- FP64 instantiation: binary64 throughout (double-double
-// window prefixes), phase fold bit-identical to Alg. 1's rounded product.
+// ssp_fp64.cu -- FP64 instantiation, periodic windows: binary64 throughout
+// (double-double window prefixes), phase fold bit-identical to Alg. 1's
+// rounded product.
 #include "ssp_kernels.cuh"
 SSP_INSTANTIATE_PREP(double, fp64)
-SSP_INSTANTIATE_PGRAM(double, fp64, false)
+SSP_INSTANTIATE_SIZES(double, false, fp64)
+SSP_INSTANTIATE_PGRAM(double, false, true, fp64_per)

@@ -150,38 +150,54 @@ __global__ void __launch_bounds__(256) argmax_kernel(ArgmaxArgs a)
     }                                                                                         \
     }
 
-// periodogram kernels of one precision and accumulator
-#define SSP_INSTANTIATE_PGRAM(R, PREC, PLAIN)                                                 \
+// periodogram kernels of one precision, accumulator and window mode (PER:
+// periodic windows, else clamped inside the data); SUF names the functions
+#define SSP_INSTANTIATE_PGRAM(R, PLAIN, PER, SUF)                                             \
     namespace ssp {                                                                           \
     template <int V, bool GM>                                                                 \
-    static cudaError_t occ_##PREC(int G, size_t smem, int *bps)                               \
+    static cudaError_t occ_##SUF(int G, size_t smem, int *bps)                                \
     {                                                                                         \
-        cudaError_t e = cudaFuncSetAttribute(pgram_kernel<R, V, GM, PLAIN>,                   \
+        cudaError_t e = cudaFuncSetAttribute(pgram_kernel<R, V, GM, PLAIN, PER>,              \
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                              (int)smem);                                      \
         if (e != cudaSuccess) return e;                                                       \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                 \
-            bps, pgram_kernel<R, V, GM, PLAIN>, G, smem);                                     \
+            bps, pgram_kernel<R, V, GM, PLAIN, PER>, G, smem);                                \
     }                                                                                         \
-    cudaError_t pgram_occupancy_##PREC(int variant, bool gmem, int G, size_t smem, int *bps)  \
+    cudaError_t pgram_occupancy_##SUF(int variant, bool gmem, int G, size_t smem, int *bps)   \
     {                                                                                         \
-        if (variant == VAR_SS) return gmem ? occ_##PREC<VAR_SS, true>(G, smem, bps)           \
-                                           : occ_##PREC<VAR_SS, false>(G, smem, bps);         \
-        return gmem ? occ_##PREC<VAR_SP, true>(G, smem, bps)                                  \
-                    : occ_##PREC<VAR_SP, false>(G, smem, bps);                                \
+        switch (variant) {                                                                    \
+        case VAR_SS: return gmem ? occ_##SUF<VAR_SS, true>(G, smem, bps)                      \
+                                 : occ_##SUF<VAR_SS, false>(G, smem, bps);                    \
+        case VAR_SP: return gmem ? occ_##SUF<VAR_SP, true>(G, smem, bps)                      \
+                                 : occ_##SUF<VAR_SP, false>(G, smem, bps);                    \
+        default: return gmem ? occ_##SUF<VAR_FIXED, true>(G, smem, bps)                       \
+                             : occ_##SUF<VAR_FIXED, false>(G, smem, bps);                     \
+        }                                                                                     \
     }                                                                                         \
-    cudaError_t pgram_launch_##PREC(int variant, bool gmem, int grid, int G, size_t smem,     \
-                                    const PgramArgs &a, cudaStream_t s)                       \
+    cudaError_t pgram_launch_##SUF(int variant, bool gmem, int grid, int G, size_t smem,      \
+                                   const PgramArgs &a, cudaStream_t s)                        \
     {                                                                                         \
-        if (variant == VAR_SS) {                                                              \
-            if (gmem) pgram_kernel<R, VAR_SS, true, PLAIN><<<grid, G, smem, s>>>(a);          \
-            else pgram_kernel<R, VAR_SS, false, PLAIN><<<grid, G, smem, s>>>(a);              \
-        } else {                                                                              \
-            if (gmem) pgram_kernel<R, VAR_SP, true, PLAIN><<<grid, G, smem, s>>>(a);          \
-            else pgram_kernel<R, VAR_SP, false, PLAIN><<<grid, G, smem, s>>>(a);              \
+        switch (variant) {                                                                    \
+        case VAR_SS:                                                                          \
+            if (gmem) pgram_kernel<R, VAR_SS, true, PLAIN, PER><<<grid, G, smem, s>>>(a);     \
+            else pgram_kernel<R, VAR_SS, false, PLAIN, PER><<<grid, G, smem, s>>>(a);         \
+            break;                                                                            \
+        case VAR_SP:                                                                          \
+            if (gmem) pgram_kernel<R, VAR_SP, true, PLAIN, PER><<<grid, G, smem, s>>>(a);     \
+            else pgram_kernel<R, VAR_SP, false, PLAIN, PER><<<grid, G, smem, s>>>(a);         \
+            break;                                                                            \
+        default:                                                                              \
+            if (gmem) pgram_kernel<R, VAR_FIXED, true, PLAIN, PER><<<grid, G, smem, s>>>(a);  \
+            else pgram_kernel<R, VAR_FIXED, false, PLAIN, PER><<<grid, G, smem, s>>>(a);      \
         }                                                                                     \
         return cudaGetLastError();                                                            \
     }                                                                                         \
+    }
+
+// shared-memory sizes of one precision and accumulator
+#define SSP_INSTANTIATE_SIZES(R, PLAIN, PREC)                                                 \
+    namespace ssp {                                                                           \
     size_t pgram_small_bytes_##PREC(int G, int variant)                                       \
     {                                                                                         \
         return small_bytes<typename AccSel<R, PLAIN>::T>(G, variant);                         \

@@ -27,7 +27,7 @@ PRECISIONS = {"fp64": SSP_FP64, "fp32c": SSP_FP32C, SSP_FP64: SSP_FP64, SSP_FP32
 class ssp_params(ctypes.Structure):
     _fields_ = [("spans", ctypes.c_double * 3), ("alpha", ctypes.c_double),
                 ("periodic", ctypes.c_int), ("precision", ctypes.c_int),
-                ("hbm_fraction", ctypes.c_double)]
+                ("hbm_fraction", ctypes.c_double), ("span", ctypes.c_double)]
 
 
 class ssp_phase_time(ctypes.Structure):
@@ -105,10 +105,13 @@ def lib():
     return _lib
 
 
-def ssp_default_params(precision="fp32c", alpha=None, spans=None, hbm_fraction=None) -> ssp_params:
+def ssp_default_params(precision="fp32c", alpha=None, spans=None, hbm_fraction=None,
+                       periodic=True, span=0.0) -> ssp_params:
     p = ssp_params()
     lib().ssp_default_params(ctypes.byref(p))
     p.precision = PRECISIONS[precision]
+    p.periodic = 1 if periodic else 0
+    p.span = float(span)
     if alpha is not None:
         p.alpha = float(alpha)
     if spans is not None:
@@ -163,10 +166,12 @@ def _ptr(a):
 
 
 def ssp_periodogram(t, y, dy, n_per_object, freq_grid, variant="ss", precision="fp32c",
-                    alpha=9.0, spans=None, params=None, out_power=None, out_best_period=None):
+                    alpha=9.0, spans=None, params=None, out_power=None, out_best_period=None,
+                    periodic=True, span=0.0):
     """Host-memory entry point.  Arrays may be numpy arrays or CPU torch
     tensors (pinned or not); returns (power [n_objects, n_freq], best_period)."""
-    p = params if params is not None else ssp_default_params(precision, alpha, spans)
+    p = params if params is not None else ssp_default_params(precision, alpha, spans,
+                                                             periodic=periodic, span=span)
     t_, y_, dy_ = (_host_array(a) for a in (t, y, dy))
     npo = np.ascontiguousarray(n_per_object, dtype=np.int64)
     fq = _host_array(freq_grid)

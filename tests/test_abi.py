@@ -46,7 +46,7 @@ def test_defaults_and_strings():
     assert p.hbm_fraction == 0.75
     assert ssp.ssp_status_string(ssp.SSP_ERR_ARG) == "invalid argument"
     assert ssp.ssp_version().startswith("ssp ")
-    assert ctypes.sizeof(ssp.ssp_params) == 48
+    assert ctypes.sizeof(ssp.ssp_params) == 56
 
 
 def _call(**kw):
@@ -80,12 +80,15 @@ def test_invalid_arguments_rejected_before_cuda(kw, status):
     assert ei.value.status == status
 
 
-def test_periodic_zero_unsupported():
+@pytest.mark.parametrize("field,value", [("periodic", 2), ("periodic", -1), ("span", -0.1),
+                                         ("span", 1.5), ("span", float("nan"))])
+def test_mode_fields_checked(field, value):
     p = ssp.ssp_default_params()
-    p.periodic = 0
+    assert p.periodic == 1 and p.span == 0.0
+    setattr(p, field, value)
     with pytest.raises(ssp.SSPError) as ei:
         _call(params=p)
-    assert ei.value.status == ssp.SSP_ERR_UNSUPPORTED
+    assert ei.value.status == ssp.SSP_ERR_ARG
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -193,3 +193,21 @@ def test_sp_tweeter_midrange_near_tie(obj, q):
     got, _ = ssp.ssp_periodogram(t, y, dy, [t.size], fq, variant="sp", precision="fp32c")
     ref, _ = oracle.periodogram(t, y, dy, [t.size], fq, oracle.SP)
     assert gate_error(got, ref) <= TOL["fp32c"]
+
+
+@pytest.mark.parametrize("periodic,span", [(False, 0.0), (True, 0.3), (False, 0.12)])
+@pytest.mark.parametrize("variant,code", VARIANTS)
+def test_window_modes(variant, code, periodic, span):
+    # non-periodic windows (clamped inside the data) and Listing 1's fixed span
+    cat = synth.concat([synth.config1(n_freq=300), _edge_catalog().subset([0, 1, 3, 6, 9])])
+    cat.freq = synth.config1(n_freq=300).freq
+    iper = 2 if periodic else 1
+    ref, ref_best = oracle.periodogram(cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq, code,
+                                       iper=iper, span=span)
+    for precision in ("fp64", "fp32c"):
+        got, best = ssp.ssp_periodogram(cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq,
+                                        variant=variant, precision=precision,
+                                        periodic=periodic, span=span)
+        assert gate_error(got, ref) <= TOL[precision], precision
+        if precision == "fp64":
+            np.testing.assert_array_equal(best, ref_best)

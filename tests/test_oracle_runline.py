@@ -110,3 +110,26 @@ def test_tie_average_equals_weighted_mean_of_fits():
     np.testing.assert_allclose(smo, ref, rtol=1e-12, atol=1e-12)
     run = np.flatnonzero(x == 0.25)
     assert run.size >= 3 and np.ptp(smo[run]) == 0.0
+
+
+def test_cv_fallback_for_exact_leverage_one_at_a_clamped_end():
+    # Non-periodic windows at the last point: its 5-point window holds four
+    # tied abscissae and the point itself, whose leverage is exactly 1 in
+    # exact arithmetic (w_j h_j = 1).  Rounding leaves 1 - w h at +-1e-16;
+    # the residual must fall back to the previous one, not divide by noise.
+    n = 12
+    g = np.random.default_rng(5)
+    x = np.sort(g.uniform(0.0, 0.8, n))
+    x[n - 5:n - 1] = 0.85
+    x[n - 1] = 0.97
+    v = g.normal(0, 1, n)
+    w = g.uniform(0.5, 2.0, n)
+    assert brute.half_width(n, 0.05) == 2
+    _, acvr = oracle.runline_raw(x, v, w, 0.05, 1, 0.0)
+    assert acvr[n - 1] == acvr[n - 2]
+    assert np.all(np.isfinite(acvr)) and np.max(acvr) < 1e3
+    # the same window by brute force: the fit through the other four points
+    # (all at one abscissa) cannot reach x_{n-1}, so no leave-one-out value
+    # exists there, while every other residual is the leave-one-out one
+    _, ref = brute.runline(x, v, w, 0.05, 1, 0.0, tie_average=False)
+    np.testing.assert_allclose(acvr[:n - 1], ref[:n - 1], rtol=1e-9, atol=1e-11)
