@@ -15,16 +15,16 @@ import threading
 import numpy as np
 
 __all__ = [
-    "build", "lib", "SS", "SP", "DEFAULT_SPANS", "prep", "phase", "fold_sort",
+    "build", "lib", "SS", "SP", "SPG", "DEFAULT_SPANS", "prep", "phase", "fold_sort",
     "half_width", "vsmlsq", "runline_raw", "runline", "tie_average", "supsmu",
-    "supsmu_sp", "chi2", "power_one", "periodogram",
+    "supsmu_sp", "supsmu_spg", "chi2", "power_one", "periodogram",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "ssp_oracle.c")
 SO = os.path.join(HERE, "libssp_oracle.so")
 
-SS, SP = 0, 1
+SS, SP, SPG = 0, 1, 2
 DEFAULT_SPANS = (0.05, 0.2, 0.5)  # Listing 1: tweeter, midrange, woofer
 
 _lock = threading.Lock()
@@ -66,6 +66,8 @@ def lib():
             L.ssp_oracle_tie_average.argtypes = [i, P, P, P]
             L.ssp_oracle_supsmu.argtypes = [i, P, P, P, i, d, d, P, P]
             L.ssp_oracle_supsmu_sp.argtypes = [i, P, P, P, i, d, P, P]
+            L.ssp_oracle_supsmu_spg.argtypes = [i, P, P, P, i, P, P, P]
+            L.ssp_oracle_supsmu_spg.restype = None
             L.ssp_oracle_chi2.argtypes = [i, P, P, P]
             L.ssp_oracle_chi2.restype = d
             L.ssp_oracle_power_one.argtypes = [i, P, P, P, d, i, d, P, i, d]
@@ -148,6 +150,16 @@ def supsmu(x, y, w, iper=2, span=0.0, alpha=9.0, spans=None):
     lib().ssp_oracle_supsmu(x.size, _p(x), _p(y), _p(w), int(iper), float(span),
                             float(alpha), _p(sp), _p(smo))
     return smo
+
+
+def supsmu_spg(x, y, w, iper=2, spans=None):
+    """Global generalized-validation reading of Sec. 3: (smooth, chosen span index)."""
+    x, y, w = _f64(x), _f64(y), _f64(w)
+    smo = np.empty(x.size)
+    k = ctypes.c_int(-1)
+    lib().ssp_oracle_supsmu_spg(x.size, _p(x), _p(y), _p(w), int(iper), _p(_spans(spans)), _p(smo),
+                                ctypes.byref(k))
+    return smo, k.value
 
 
 def supsmu_sp(x, y, w, iper=2, alpha=9.0, spans=None):

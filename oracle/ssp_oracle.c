@@ -366,6 +366,45 @@ void ssp_oracle_supsmu_sp(int n, const double *x, const double *y, const double 
     ssp_oracle_tie_average(n, x, w, smo);
 }
 
+/* Sec. 3, alternative reading (global generalized validation): the three
+ * spans' running lines are evaluated in the same sweep; each span scores
+ * the weighted sum of its squared generalized-validation residuals,
+ * G_s = sum_j w_j (|y_j - s_s(j)| / (1 - nu_s(j)/m_s))^2, and the whole
+ * frequency takes the span of least score (first strict minimum).  The
+ * smooth is that span's running line, averaged over runs of equal x.  No
+ * per-point choice, no bass enhancement. */
+void ssp_oracle_supsmu_spg(int n, const double *x, const double *y, const double *w,
+                           int iper, const double spans[3], double *smo, int *chosen)
+{
+    if (degenerate_mean(n, x, y, w, smo)) {
+        if (chosen) *chosen = -1;
+        return;
+    }
+    double vsmlsq = ssp_oracle_vsmlsq(n, x);
+    int jper = effective_jper(n, x, iper);
+    int periodic = (jper == 2);
+    double *fit = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double score[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < 3; i++) {
+        int ibw = ssp_oracle_half_width(n, spans[i]);
+        double m = (double)(2 * ibw + 1);
+        for (int j = 0; j < n; j++) {
+            double sxx;
+            fit[i * n + j] = window_fit(n, x, y, w, ibw, periodic, j, vsmlsq, NULL, &sxx);
+            double nu = (sxx > vsmlsq) ? 2.0 : 1.0;
+            double g = fabs(y[j] - fit[i * n + j]) / (1.0 - nu / m);
+            score[i] += w[j] * g * g;
+        }
+    }
+    int k = 0;
+    for (int i = 1; i < 3; i++)
+        if (score[i] < score[k]) k = i;
+    for (int j = 0; j < n; j++) smo[j] = fit[k * n + j];
+    ssp_oracle_tie_average(n, x, w, smo);
+    if (chosen) *chosen = k;
+    free(fit);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Alg. 1 per (object, frequency) and end to end                             */
 /* ------------------------------------------------------------------------ */
@@ -395,6 +434,8 @@ double ssp_oracle_power_prepped(int n, const double *tt, const double *y,
      * variant: SP differs from SS only in how it chooses the span */
     if (variant == SSP_ORACLE_SP && !(span > 0.0))
         ssp_oracle_supsmu_sp(n, x, ys, ws, iper, alpha, spans, smo);
+    else if (variant == SSP_ORACLE_SPG && !(span > 0.0))
+        ssp_oracle_supsmu_spg(n, x, ys, ws, iper, spans, smo, NULL);
     else
         ssp_oracle_supsmu(n, x, ys, ws, iper, span, alpha, spans, smo);
     double chi2 = ssp_oracle_chi2(n, ys, ws, smo);

@@ -15,7 +15,7 @@
 extern "C" {
 #endif
 
-enum { SSP_ORACLE_SS = 0, SSP_ORACLE_SP = 1 };
+enum { SSP_ORACLE_SS = 0, SSP_ORACLE_SP = 1, SSP_ORACLE_SPG = 2 };
 
 /* Alg. 1 compute_chi0_tt_weights */
 void ssp_oracle_prep(int n, const double *t, const double *y, const double *dy,
@@ -42,6 +42,11 @@ void ssp_oracle_supsmu(int n, const double *x, const double *y, const double *w,
 /* Sec. 3 single-pass generalized-validation variant (reading) */
 void ssp_oracle_supsmu_sp(int n, const double *x, const double *y, const double *w,
                           int iper, double alpha, const double spans[3], double *smo);
+/* Sec. 3, the alternative reading: one span per frequency, the one whose
+ * summed squared generalized-validation residuals are smallest; writes the
+ * chosen span index to *chosen (if not NULL) */
+void ssp_oracle_supsmu_spg(int n, const double *x, const double *y, const double *w,
+                           int iper, const double spans[3], double *smo, int *chosen);
 
 double ssp_oracle_chi2(int n, const double *y, const double *w, const double *smo);
 /* iper: 2 periodic windows, 1 windows clamped inside the data (Listing 1);

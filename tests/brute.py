@@ -148,3 +148,32 @@ def supsmu_sp(x, y, w, alpha=9.0, iper=2, spans=SPANS):
         s = _select(g, g[2], alpha, spans[2], spans)
         out[j] = _interp(s, fits[0], fits[1], fits[2], spans)
     return tie_avg(x, w, out)
+
+
+def supsmu_spg(x, y, w, iper=2, spans=SPANS):
+    """Global generalized-validation reading: per span, the weighted sum of
+    squared GCV residuals over all points; the least-score span's running
+    line, tie-averaged.  Returns (smooth, chosen span index)."""
+    n = x.size
+    if x[-1] <= x[0]:
+        return np.full(n, np.sum(w * y) / np.sum(w)), -1
+    vs = vsmlsq_of(x)
+    periodic = abs(iper) == 2
+    fits, scores = [], []
+    for s in spans:
+        ibw = half_width(n, s)
+        m = 2 * ibw + 1
+        f = np.empty(n)
+        score = 0.0
+        for j in range(n):
+            idx, xs = window(n, ibw, periodic, j, x)
+            f[j], sloped = wls_line(xs, y[idx], w[idx], x[j], vs)
+            nu = 2.0 if sloped else 1.0
+            score += w[j] * (abs(y[j] - f[j]) / (1.0 - nu / m)) ** 2
+        fits.append(f)
+        scores.append(score)
+    k = 0
+    for i in (1, 2):
+        if scores[i] < scores[k]:
+            k = i
+    return tie_avg(x, w, fits[k]), k

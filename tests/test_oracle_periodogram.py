@@ -137,6 +137,8 @@ def _brute_power(t, y, dy, f, variant, iper, span):
             smo, _ = brute.runline(xs, ys, ws, span, -iper, brute.vsmlsq_of(xs))
     elif variant == oracle.SP:
         smo = brute.supsmu_sp(xs, ys, ws, iper=iper)
+    elif variant == oracle.SPG:
+        smo = brute.supsmu_spg(xs, ys, ws, iper=iper)[0]
     else:
         smo = brute.supsmu(xs, ys, ws, iper=iper)
     ybar = np.sum(w * y) / np.sum(w)
@@ -144,8 +146,8 @@ def _brute_power(t, y, dy, f, variant, iper, span):
     return 1.0 - np.sum(ws * (ys - smo) ** 2) / chi0
 
 
-@pytest.mark.parametrize("variant", [oracle.SS, oracle.SP])
-@pytest.mark.parametrize("iper,span", [(1, 0.0), (2, 0.3), (1, 0.3), (1, 0.05)])
+@pytest.mark.parametrize("variant", [oracle.SS, oracle.SP, oracle.SPG])
+@pytest.mark.parametrize("iper,span", [(2, 0.0), (1, 0.0), (2, 0.3), (1, 0.3), (1, 0.05)])
 def test_periodogram_modes_match_brute_force(variant, iper, span):
     # non-periodic windows (clamped inside the data) and the fixed-span
     # single smooth of Listing 1, end to end through the periodogram driver

@@ -133,3 +133,36 @@ def test_clamp_of_smoothed_span_matters():
     w = g.uniform(0.5, 3, 24)
     np.testing.assert_allclose(oracle.supsmu(x, y, w), brute.supsmu(x, y, w),
                                rtol=1e-9, atol=1e-10)
+
+
+@pytest.mark.parametrize("iper", [1, 2])
+@pytest.mark.parametrize("n", [8, 17, 40])
+def test_spg_matches_brute_force(n, iper):
+    g = np.random.default_rng(1000 + n + iper)
+    x = np.sort(g.uniform(0, 1, n))
+    if n >= 17:
+        x[5:8] = x[5]            # a tie run
+    y = np.sin(2 * np.pi * 3 * x) + g.normal(0, 0.3, n)
+    w = g.uniform(0.5, 2.0, n)
+    smo, k = oracle.supsmu_spg(x, y, w, iper=iper)
+    ref, kref = brute.supsmu_spg(x, y, w, iper=iper)
+    assert k == kref
+    np.testing.assert_allclose(smo, ref, rtol=1e-10, atol=1e-12)
+
+
+def test_spg_chooses_the_span_the_data_want():
+    # a fast oscillation is followed best by the tweeter, a flat noisy line
+    # by the woofer: the global score picks each, and equal spans reduce
+    # SPG to that span's running line
+    g = np.random.default_rng(7)
+    n = 300
+    x = np.sort(g.uniform(0, 1, n))
+    w = np.ones(n)
+    fast = np.sin(2 * np.pi * 12 * x) + g.normal(0, 0.05, n)
+    flat = g.normal(0, 1.0, n)
+    assert oracle.supsmu_spg(x, fast, w)[1] == 0
+    assert oracle.supsmu_spg(x, flat, w)[1] == 2
+    smo, k = oracle.supsmu_spg(x, fast, w, spans=(0.2, 0.2, 0.2))
+    ref, _ = oracle.runline(x, fast, w, 0.2, -2, oracle.vsmlsq(x))
+    assert k == 0
+    np.testing.assert_allclose(smo, ref, rtol=1e-12, atol=1e-12)
