@@ -40,7 +40,11 @@ extern "C" {
 
 typedef enum {
     SSP_SS = 0, /* Super Smoother, cross-validated spans (Listing 1) */
-    SSP_SP = 1  /* SuperSmootherSP, generalized validation, one pass (Sec. 3) */
+    SSP_SP = 1, /* SuperSmootherSP, generalized validation, one pass (Sec. 3):
+                   a span chosen per point */
+    SSP_SPG = 2 /* the other reading of Sec. 3: one span per frequency, the one
+                   whose summed squared generalized-validation residuals
+                   sum w (|y - s|/(1 - nu/m))^2 are least; no bass */
 } ssp_variant;
 
 typedef enum {
@@ -261,7 +265,7 @@ const char *ssp_version(void);
  * recorded on the launching stream.  ssp_profile_read waits for the recorded
  * events, fills out[k] for k = SSP_PHASE_PREP (Alg. 1 compute_chi0_tt_weights),
  * SSP_PHASE_PGRAM_SS / SSP_PHASE_PGRAM_SP (fold + sort + smoother + chi2 of
- * that variant, one launch per length bucket), SSP_PHASE_REDO (SSP_FP32C
+ * SS, or of SP and SPG, one launch per length range), SSP_PHASE_REDO (SSP_FP32C
  * only: the FP64 launch that recomputes the frequencies whose FP32 decisions
  * came within their margins) and SSP_PHASE_ARGMAX (findPeriod), and clears
  * them if reset != 0.  Off by default; enabling adds two event records per

@@ -137,7 +137,8 @@ int check_shape(const int64_t *n_per_object, int64_t n_objects, int64_t n_freq, 
     if (n_objects > (int64_t)1 << 30) return fail(SSP_ERR_ARG, "n_objects too large");
     if (n_freq < 1) return fail(SSP_ERR_ARG, "n_freq must be >= 1");
     if (n_freq > (int64_t)1 << 31) return fail(SSP_ERR_ARG, "n_freq too large");
-    if (v != SSP_SS && v != SSP_SP) return fail(SSP_ERR_ARG, "unknown variant %d", (int)v);
+    if (v != SSP_SS && v != SSP_SP && v != SSP_SPG)
+        return fail(SSP_ERR_ARG, "unknown variant %d", (int)v);
     if (!n_per_object) return fail(SSP_ERR_ARG, "n_per_object is NULL");
     for (int64_t o = 0; o < n_objects; ++o) {
         if (n_per_object[o] < 4)
@@ -159,7 +160,7 @@ int check_shape(const int64_t *n_per_object, int64_t n_objects, int64_t n_freq, 
 // replaces the rule per (precision, variant, range) with measured choices.
 constexpr int kRanges = 5;
 constexpr int kRangeMax[kRanges] = {384, 768, 1536, 2048, 65535};
-std::atomic<int> g_tuned[2][3][kRanges];   // [precision][kernel variant][range]; 0 = rule
+std::atomic<int> g_tuned[2][4][kRanges];   // [precision][kernel variant][range]; 0 = rule
 
 int range_of(int n)
 {
@@ -190,7 +191,8 @@ int group_size_rule(int n, int variant, int precision)
 // single smooth
 int kernel_variant(ssp_variant v, const ssp_params &P)
 {
-    return P.span > 0.0 ? VAR_FIXED : (int)v;
+    if (P.span > 0.0) return VAR_FIXED;
+    return v == SSP_SS ? VAR_SS : v == SSP_SP ? VAR_SP : VAR_SPG;
 }
 
 int group_size(int n, int variant, int precision)
@@ -503,7 +505,7 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
             ga.periodic = P.periodic;
             ga.span = P.span;
             slab_cur += b.main.gmem ? b.main.slab_bytes * (size_t)b.main.grid : 0;
-            const int ph = variant == SSP_SP ? SSP_PHASE_PGRAM_SP : SSP_PHASE_PGRAM_SS;
+            const int ph = variant == SSP_SS ? SSP_PHASE_PGRAM_SS : SSP_PHASE_PGRAM_SP;
             on = prof_begin(ph, s, mk);
             if ((e = pgram_launch(prec, kv, b.main.gmem, per, b.main.grid, b.G, b.main.smem,
                                   ga, s)))

@@ -34,7 +34,10 @@ namespace ssp {
 
 // kernel variants: SS (Listing 1), SP (Sec. 3), and Listing 1's fixed-span
 // single smooth, which is the same computation for both
-enum { VAR_SS = 0, VAR_SP = 1, VAR_FIXED = 2 };
+enum { VAR_SS = 0, VAR_SP = 1, VAR_FIXED = 2, VAR_SPG = 3 };
+// SPG: relative gap between two spans' scores below which FP32C sends the
+// frequency to the FP64 recompute (the scores' FP32 error is ~1e-6)
+constexpr double kNearSPG = 1e-5;
 constexpr int kMaxThreads = 512;
 constexpr int kBucketRankMax = 64;   // larger buckets switch to the bitonic sort
 
@@ -1308,6 +1311,69 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
 
     if (VARIANT == VAR_FIXED)   // Listing 1's single smooth of y
         return fixed_span_pass<R, A>(a, fr, sm, n, c0, c1, o, vsmlsq, ties, rf);
+
+    if (VARIANT == VAR_SPG) {
+        // Sec. 3, global generalized validation: three windows in one
+        // sweep; each span scores sum w g^2 over the frequency and the least
+        // score's smooth gives chi2
+        const R *vy[1] = {fr.Y};
+        build_xy_prefix(fr, sm, fr.Y, c0, c1, o);
+        __syncthreads();
+        KSum<R> gs[3], xs[3];
+        if (c0 < c1) {
+            Win<R, 1> w0, w1, w2;
+            win_init<R, 1>(w0, fr, sm, vy, c0, h0, n, o);
+            win_init<R, 1>(w1, fr, sm, vy, c0, h1, n, o);
+            win_init<R, 1>(w2, fr, sm, vy, c0, h2, n, o);
+            const R m0 = (R)(2 * h0 + 1), m1 = (R)(2 * h1 + 1), m2 = (R)(2 * h2 + 1);
+            const R gl0 = R(1) / (R(1) - R(2) / m0), gc0 = R(1) / (R(1) - R(1) / m0);
+            const R gl1 = R(1) / (R(1) - R(2) / m1), gc1 = R(1) / (R(1) - R(1) / m1);
+            const R gl2 = R(1) / (R(1) - R(2) / m2), gc2 = R(1) / (R(1) - R(1) / m2);
+            RunAvg<R, 3> ra;
+            ra.reset(c0);
+            auto emit = [&](int i, const R (&v)[3]) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const R d = fr.Y[i] - v[k];
+                    xs[k].add(fr.WT[i] * d * d);
+                }
+            };
+            for (int j = c0; j < c1; ++j) {
+                Fit<R, 1> f0, f1, f2;
+                win_fit_checked<R, 1>(f0, w0, fr, vy, j, h0, n, o, vsmlsq, near, rf);
+                win_fit_checked<R, 1>(f1, w1, fr, vy, j, h1, n, o, vsmlsq, near, rf);
+                win_fit_checked<R, 1>(f2, w2, fr, vy, j, h2, n, o, vsmlsq, near, rf);
+                const R yj = fr.Y[j], wj = fr.WT[j];
+                const R g0 = fabs(yj - f0.s[0]) * (f0.slope ? gl0 : gc0);
+                const R g1 = fabs(yj - f1.s[0]) * (f1.slope ? gl1 : gc1);
+                const R g2 = fabs(yj - f2.s[0]) * (f2.slope ? gl2 : gc2);
+                gs[0].add(wj * g0 * g0);
+                gs[1].add(wj * g1 * g1);
+                gs[2].add(wj * g2 * g2);
+                const R val[3] = {f0.s[0], f1.s[0], f2.s[0]};
+                run_push<R, 3>(ra, fr, j, ties, val, emit);
+                if (j + 1 < c1) {
+                    win_slide<R, 1>(w0, fr, vy, j, h0, n, o);
+                    win_slide<R, 1>(w1, fr, vy, j, h1, n, o);
+                    win_slide<R, 1>(w2, fr, vy, j, h2, n, o);
+                }
+            }
+        }
+        double G[3], X[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            G[k] = block_sum(gs[k].value(), sm.red);
+            X[k] = block_sum(xs[k].value(), sm.red);
+        }
+        int kbest = 0;
+        for (int k = 1; k < 3; ++k)
+            if (G[k] < G[kbest]) kbest = k;
+        if (sizeof(R) == 4)
+            for (int k = 0; k < 3; ++k)
+                if (k != kbest && fabs(G[k] - G[kbest]) <= kNearSPG * fabs(G[kbest])) near = true;
+        near = __syncthreads_or(near) != 0;
+        return FreqResult{X[kbest], near};
+    }
 
     if (VARIANT == VAR_SP) {
         // one sweep, three windows on y, generalized validation (Sec. 3)

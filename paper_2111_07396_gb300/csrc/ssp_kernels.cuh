@@ -171,6 +171,8 @@ __global__ void __launch_bounds__(256) argmax_kernel(ArgmaxArgs a)
                                  : occ_##SUF<VAR_SS, false>(G, smem, bps);                    \
         case VAR_SP: return gmem ? occ_##SUF<VAR_SP, true>(G, smem, bps)                      \
                                  : occ_##SUF<VAR_SP, false>(G, smem, bps);                    \
+        case VAR_SPG: return gmem ? occ_##SUF<VAR_SPG, true>(G, smem, bps)                    \
+                                  : occ_##SUF<VAR_SPG, false>(G, smem, bps);                  \
         default: return gmem ? occ_##SUF<VAR_FIXED, true>(G, smem, bps)                       \
                              : occ_##SUF<VAR_FIXED, false>(G, smem, bps);                     \
         }                                                                                     \
@@ -186,6 +188,10 @@ __global__ void __launch_bounds__(256) argmax_kernel(ArgmaxArgs a)
         case VAR_SP:                                                                          \
             if (gmem) pgram_kernel<R, VAR_SP, true, PLAIN, PER><<<grid, G, smem, s>>>(a);     \
             else pgram_kernel<R, VAR_SP, false, PLAIN, PER><<<grid, G, smem, s>>>(a);         \
+            break;                                                                            \
+        case VAR_SPG:                                                                         \
+            if (gmem) pgram_kernel<R, VAR_SPG, true, PLAIN, PER><<<grid, G, smem, s>>>(a);    \
+            else pgram_kernel<R, VAR_SPG, false, PLAIN, PER><<<grid, G, smem, s>>>(a);        \
             break;                                                                            \
         default:                                                                              \
             if (gmem) pgram_kernel<R, VAR_FIXED, true, PLAIN, PER><<<grid, G, smem, s>>>(a);  \

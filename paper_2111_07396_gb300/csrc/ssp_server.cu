@@ -34,6 +34,7 @@ using ssp_internal::fail;
 constexpr double kDefaultBatchPtf = 4.0e9;
 constexpr int64_t kDefaultInFlight = (int64_t)1 << 20;
 constexpr int kSlots = 2;
+constexpr int kVariants = 3;   // SSP_SS, SSP_SP, SSP_SPG
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -109,8 +110,8 @@ struct ssp_server {
 
     std::mutex mu;
     std::condition_variable cv_launch, cv_complete, cv_done;
-    std::deque<std::shared_ptr<Request>> queue[2];
-    double pending_ptf[2] = {0.0, 0.0};
+    std::deque<std::shared_ptr<Request>> queue[kVariants];
+    double pending_ptf[kVariants] = {0.0, 0.0, 0.0};
     std::unordered_map<int64_t, std::shared_ptr<Request>> live;   // submitted, not collected
     std::deque<int64_t> finished;                                // not yet reported by next
     std::deque<int> launched;                                    // slots, in launch order
@@ -196,11 +197,13 @@ void launcher_loop(ssp_server *S, std::unique_lock<std::mutex> &lk)
         for (;;) {
             if (S->stop) return;
             slot = free_slot(S);
-            const bool q0 = !S->queue[0].empty(), q1 = !S->queue[1].empty();
-            if (slot >= 0 && (q0 || q1)) {
-                // the variant whose oldest request has waited longest
-                v = (q0 && (!q1 || S->queue[0].front()->t_submit <= S->queue[1].front()->t_submit))
-                        ? 0 : 1;
+            // the variant whose oldest request has waited longest
+            v = -1;
+            for (int k = 0; k < kVariants; ++k)
+                if (!S->queue[k].empty() &&
+                    (v < 0 || S->queue[k].front()->t_submit < S->queue[v].front()->t_submit))
+                    v = k;
+            if (slot >= 0 && v >= 0) {
                 const auto deadline = S->queue[v].front()->t_submit +
                                       std::chrono::duration_cast<Clock::duration>(
                                           std::chrono::duration<double, std::milli>(
@@ -367,7 +370,8 @@ int ssp_server_submit(ssp_server *s, const double *t, const double *y, const dou
 {
     ssp_internal::clear_error();
     if (!s || !out_ticket) return fail(SSP_ERR_ARG, "NULL server or ticket pointer");
-    if (variant != SSP_SS && variant != SSP_SP) return fail(SSP_ERR_ARG, "unknown variant");
+    if (variant != SSP_SS && variant != SSP_SP && variant != SSP_SPG)
+        return fail(SSP_ERR_ARG, "unknown variant");
     int rc = ssp_internal::check_one_object(s->P, t, y, dy, n);
     if (rc) return rc;
     auto r = std::make_shared<Request>();
@@ -437,8 +441,7 @@ int ssp_server_destroy(ssp_server *s)
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
-        s->queue[0].clear();
-        s->queue[1].clear();
+        for (auto &q : s->queue) q.clear();
         s->cv_launch.notify_all();
         s->cv_complete.notify_all();
         s->cv_done.notify_all();

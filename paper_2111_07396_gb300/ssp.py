@@ -15,12 +15,13 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SO = os.path.join(HERE, "libssp.so")
 
-SSP_SS, SSP_SP = 0, 1
+SSP_SS, SSP_SP, SSP_SPG = 0, 1, 2
 SSP_FP64, SSP_FP32C = 0, 1
 SSP_OK, SSP_ERR_ARG, SSP_ERR_NOMEM, SSP_ERR_CUDA, SSP_ERR_TIMEOUT, SSP_ERR_UNSUPPORTED = (
     0, -1, -2, -3, -4, -5)
 SSP_ERR_BUSY, SSP_PENDING = -6, 1
-VARIANTS = {"ss": SSP_SS, "sp": SSP_SP, SSP_SS: SSP_SS, SSP_SP: SSP_SP}
+VARIANTS = {"ss": SSP_SS, "sp": SSP_SP, "spg": SSP_SPG, SSP_SS: SSP_SS, SSP_SP: SSP_SP,
+            SSP_SPG: SSP_SPG}
 PRECISIONS = {"fp64": SSP_FP64, "fp32c": SSP_FP32C, SSP_FP64: SSP_FP64, SSP_FP32C: SSP_FP32C}
 
 

@@ -10,7 +10,7 @@ from paper_2111_07396_gb300 import ssp, synth
 from tests.parity import TOL, gate_error, oracle_powers, sample_freqs
 
 pytestmark = pytest.mark.gpu
-VARIANTS = [("ss", oracle.SS), ("sp", oracle.SP)]
+VARIANTS = [("ss", oracle.SS), ("sp", oracle.SP), ("spg", oracle.SPG)]
 
 
 @pytest.fixture(scope="module", autouse=True)
