@@ -17,7 +17,8 @@ import numpy as np
 __all__ = [
     "build", "lib", "SS", "SP", "SPG", "DEFAULT_SPANS", "prep", "phase", "fold_sort",
     "half_width", "vsmlsq", "runline_raw", "runline", "tie_average", "supsmu",
-    "supsmu_sp", "supsmu_spg", "chi2", "power_one", "periodogram",
+    "supsmu_sp", "supsmu_spg", "chi2", "power_one", "periodogram", "peaks", "fine_grid",
+    "search_refine",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -74,6 +75,13 @@ def lib():
             L.ssp_oracle_power_one.restype = d
             L.ssp_oracle_periodogram.argtypes = [P, P, P, P, i64, P, i64, i, d, P, i, d, i, P, P]
             L.ssp_oracle_periodogram.restype = i
+            L.ssp_oracle_peaks.argtypes = [P, i64, i, P]
+            L.ssp_oracle_peaks.restype = None
+            L.ssp_oracle_fine_grid.argtypes = [P, i64, i64, i, P]
+            L.ssp_oracle_fine_grid.restype = None
+            L.ssp_oracle_search_refine.argtypes = [P, P, P, P, i64, P, i64, i, i, d, P, i, i, i, i,
+                                                   P, P]
+            L.ssp_oracle_search_refine.restype = i
             _lib = L
         return _lib
 
@@ -202,3 +210,35 @@ def periodogram(t, y, dy, n_per_object, freq, variant=SS, alpha=9.0, spans=None,
     if rc != 0:
         raise ValueError("oracle rejected the input (every object needs n >= 4)")
     return power, best
+
+
+def peaks(p, k):
+    """Indices of the top k local maxima of p (ties by lower index)."""
+    p = _f64(p)
+    out = np.empty(int(k), dtype=np.int64)
+    lib().ssp_oracle_peaks(_p(p), p.size, int(k), _p(out))
+    return out
+
+
+def fine_grid(f, q, n_fine):
+    f = _f64(f)
+    out = np.empty(int(n_fine))
+    lib().ssp_oracle_fine_grid(_p(f), f.size, int(q), int(n_fine), _p(out))
+    return out
+
+
+def search_refine(t, y, dy, n_per_object, coarse, coarse_variant=SP, fine_variant=SS,
+                  n_peaks=3, n_fine=64, alpha=9.0, spans=None, iper=2, n_threads=None):
+    """(best_period[n_objects], best_power[n_objects]) of search-and-refine."""
+    t, y, dy, coarse = _f64(t), _f64(y), _f64(dy), _f64(coarse)
+    npo = np.ascontiguousarray(n_per_object, dtype=np.int64)
+    bp, bw = np.empty(npo.size), np.empty(npo.size)
+    if n_threads is None:
+        n_threads = os.cpu_count() or 1
+    rc = lib().ssp_oracle_search_refine(_p(t), _p(y), _p(dy), _p(npo), npo.size, _p(coarse),
+                                        coarse.size, int(coarse_variant), int(fine_variant),
+                                        float(alpha), _p(_spans(spans)), int(iper), int(n_peaks),
+                                        int(n_fine), int(n_threads), _p(bp), _p(bw))
+    if rc != 0:
+        raise ValueError("oracle rejected the input")
+    return bp, bw

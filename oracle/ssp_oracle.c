@@ -533,3 +533,90 @@ int ssp_oracle_periodogram(const double *t, const double *y, const double *dy,
     free(off);
     return 0;
 }
+
+
+/* ------------------------------------------------------------------------ */
+/* Search-and-refine (the closing outlook of Sec. 6): a coarse periodogram,   */
+/* the top local maxima of each object's coarse power, a dense grid across    */
+/* each peak's coarse spacing, and the periodogram again on those grids.      */
+/* ------------------------------------------------------------------------ */
+/* Local maxima of p[0..n): p[q] >= p[q-1] and p[q] > p[q+1] (a missing
+ * neighbour counts as lower), taken by power, ties by lower index; a maximum
+ * next to one already taken is skipped.  Fewer than k maxima: the rest
+ * repeat the first.  Writes k indices. */
+void ssp_oracle_peaks(const double *p, int64_t n, int k, int64_t *out)
+{
+    int taken = 0;
+    while (taken < k) {
+        int64_t best = -1;
+        for (int64_t q = 0; q < n; q++) {
+            int is_max = (q == 0 || p[q] >= p[q - 1]) && (q == n - 1 || p[q] > p[q + 1]);
+            if (!is_max) continue;
+            int skip = 0;
+            for (int i = 0; i < taken; i++)
+                if (out[i] >= q - 1 && out[i] <= q + 1) skip = 1;
+            if (skip) continue;
+            if (best < 0 || p[q] > p[best]) best = q;
+        }
+        if (best < 0) break;
+        out[taken++] = best;
+    }
+    for (int i = taken; i < k; i++) out[i] = taken > 0 ? out[0] : 0;
+}
+
+/* n_fine frequencies evenly from f[q-1] to f[q+1] (one coarse step beyond q
+ * at either end of the grid; a start at or below 0 moves to f[q]/2) */
+void ssp_oracle_fine_grid(const double *f, int64_t n, int64_t q, int n_fine, double *out)
+{
+    double step_lo = (q > 0) ? f[q] - f[q - 1] : (n > 1 ? f[1] - f[0] : 0.0);
+    double step_hi = (q < n - 1) ? f[q + 1] - f[q] : (n > 1 ? f[n - 1] - f[n - 2] : 0.0);
+    double lo = f[q] - step_lo, hi = f[q] + step_hi;
+    if (!(lo > 0.0)) lo = 0.5 * f[q];
+    for (int i = 0; i < n_fine; i++)
+        out[i] = (n_fine > 1) ? lo + (hi - lo) * (double)i / (double)(n_fine - 1) : f[q];
+}
+
+int ssp_oracle_search_refine(const double *t, const double *y, const double *dy,
+                             const int64_t *n_per_object, int64_t n_objects,
+                             const double *coarse, int64_t n_coarse, int coarse_variant,
+                             int fine_variant, double alpha, const double spans[3], int iper,
+                             int n_peaks, int n_fine, int n_threads, double *out_best_period,
+                             double *out_best_power)
+{
+    if (n_objects < 1 || n_coarse < 2 || n_peaks < 1 || n_fine < 1) return -1;
+    double *cp = (double *)malloc(sizeof(double) * (size_t)(n_objects * n_coarse));
+    double *cb = (double *)malloc(sizeof(double) * (size_t)n_objects);
+    int rc = ssp_oracle_periodogram(t, y, dy, n_per_object, n_objects, coarse, n_coarse,
+                                    coarse_variant, alpha, spans, iper, 0.0, n_threads, cp, cb);
+    if (rc) {
+        free(cp);
+        free(cb);
+        return rc;
+    }
+    const int64_t nf = (int64_t)n_peaks * n_fine;
+    double *fg = (double *)malloc(sizeof(double) * (size_t)nf);
+    double *fp = (double *)malloc(sizeof(double) * (size_t)nf);
+    int64_t *pk = (int64_t *)malloc(sizeof(int64_t) * (size_t)n_peaks);
+    int64_t a = 0;
+    for (int64_t o = 0; o < n_objects && rc == 0; o++) {
+        ssp_oracle_peaks(cp + o * n_coarse, n_coarse, n_peaks, pk);
+        for (int i = 0; i < n_peaks; i++)
+            ssp_oracle_fine_grid(coarse, n_coarse, pk[i], n_fine, fg + (int64_t)i * n_fine);
+        double best_period;
+        rc = ssp_oracle_periodogram(t + a, y + a, dy + a, n_per_object + o, 1, fg, nf,
+                                    fine_variant, alpha, spans, iper, 0.0, n_threads, fp,
+                                    &best_period);
+        int64_t b = 0;
+        for (int64_t q = 1; q < nf; q++)
+            if (fp[q] > fp[b]) b = q;
+        out_best_period[o] = best_period;
+        out_best_power[o] = fp[b];
+        a += n_per_object[o];
+    }
+    free(pk);
+    free(fp);
+    free(fg);
+    free(cp);
+    free(cb);
+    return rc;
+}

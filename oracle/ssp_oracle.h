@@ -64,6 +64,18 @@ int ssp_oracle_periodogram(const double *t, const double *y, const double *dy,
                            const double spans[3], int iper, double span, int n_threads,
                            double *out_power, double *out_best_period);
 
+/* search-and-refine (Sec. 6 outlook): coarse periodogram, top n_peaks local
+ * maxima per object, n_fine frequencies across each peak's coarse spacing,
+ * the fine periodogram; best period and power of the largest fine power */
+void ssp_oracle_peaks(const double *p, int64_t n, int k, int64_t *out);
+void ssp_oracle_fine_grid(const double *f, int64_t n, int64_t q, int n_fine, double *out);
+int ssp_oracle_search_refine(const double *t, const double *y, const double *dy,
+                             const int64_t *n_per_object, int64_t n_objects,
+                             const double *coarse, int64_t n_coarse, int coarse_variant,
+                             int fine_variant, double alpha, const double spans[3], int iper,
+                             int n_peaks, int n_fine, int n_threads, double *out_best_period,
+                             double *out_best_power);
+
 #ifdef __cplusplus
 }
 #endif
