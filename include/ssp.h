@@ -251,6 +251,33 @@ int ssp_autotune(const double *t, const double *y, const double *dy, const int64
 /* Forgets every tuned choice: the fixed rule applies again. */
 void ssp_autotune_clear(void);
 
+/*
+ * Search-and-refine (the outlook of Sec. 6: a cheap coarse search, then the
+ * costly smoother only near its peaks), on host arrays as ssp_periodogram.
+ *  1. The periodogram of coarse_variant on coarse_grid (n_coarse >= 2
+ *     frequencies, strictly increasing).
+ *  2. Per object, the n_peaks (1..64) largest local maxima of that power.
+ *     A local maximum is p[q] >= p[q-1] and p[q] > p[q+1], a missing
+ *     neighbour counting as lower. Ties go to the lower index, a maximum
+ *     next to one already taken is skipped, and fewer than n_peaks maxima
+ *     repeat the first.
+ *  3. Per peak q, n_fine frequencies evenly from f[q-1] to f[q+1] (one coarse
+ *     step beyond q at either end of the grid; a start at or below 0 moves
+ *     to f[q]/2).
+ *  4. The periodogram of fine_variant on those n_peaks * n_fine frequencies.
+ * out_best_period[o] and out_best_power[o] (double, n_objects each) are the
+ * period 1/f and the power of the first largest fine power.  The coarse
+ * grid must resolve the peaks (steps below about 1/(time span)); the step
+ * only sharpens them.  params as ssp_periodogram, with span = 0.
+ * Errors: as ssp_periodogram; SSP_ERR_ARG also for the rules above and
+ * n_peaks * n_fine > 2^22.
+ */
+int ssp_search_refine(const double *t, const double *y, const double *dy,
+                      const int64_t *n_per_object, int64_t n_objects, const double *coarse_grid,
+                      int64_t n_coarse, ssp_variant coarse_variant, ssp_variant fine_variant,
+                      int n_peaks, int n_fine, const ssp_params *params, double *out_best_period,
+                      double *out_best_power);
+
 /* Static text for a status code. */
 const char *ssp_status_string(int status);
 /* Detail of the last error returned on the calling thread ("" if none). */

@@ -22,6 +22,8 @@ cudaError_t prep_launch_fp32(const PrepArgs &, int, cudaStream_t);
 cudaError_t prep_launch_fp64(const PrepArgs &, int, cudaStream_t);
 cudaError_t argmax_launch_fp32(const ArgmaxArgs &, int, cudaStream_t);
 cudaError_t argmax_launch_fp64(const ArgmaxArgs &, int, cudaStream_t);
+cudaError_t peaks_launch_fp32(const PeaksArgs &, int, cudaStream_t);
+cudaError_t peaks_launch_fp64(const PeaksArgs &, int, cudaStream_t);
 cudaError_t pgram_occupancy_fp32_per(int, bool, int, size_t, int *);
 cudaError_t pgram_launch_fp32_per(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
 cudaError_t pgram_occupancy_fp32_clamp(int, bool, int, size_t, int *);
@@ -48,6 +50,10 @@ cudaError_t prep_launch(int p, const PrepArgs &a, int n, cudaStream_t s)
 cudaError_t argmax_launch(int p, const ArgmaxArgs &a, int n, cudaStream_t s)
 {
     return p == SSP_FP64 ? argmax_launch_fp64(a, n, s) : argmax_launch_fp32(a, n, s);
+}
+cudaError_t peaks_launch(int p, const PeaksArgs &a, int n, cudaStream_t s)
+{
+    return p == SSP_FP64 ? peaks_launch_fp64(a, n, s) : peaks_launch_fp32(a, n, s);
 }
 cudaError_t pgram_occupancy(int p, int v, bool g, bool per, int G, size_t smem, int *bps)
 {
@@ -401,9 +407,12 @@ int check_values(const double *t, const double *y, const double *dy, int64_t N, 
     return SSP_OK;
 }
 
+// fbase (device, or null): object o's grid is freq[fbase[o] .. + n_freq);
+// out_best_power (device, or null) receives each object's largest power
 int run_device(const double *t, const double *y, const double *dy, const int64_t *npo,
                int64_t n_obj, const double *freq, int64_t n_freq, ssp_variant variant,
-               const ssp_params &P, void *out_power, double *out_best, cudaStream_t s)
+               const ssp_params &P, void *out_power, double *out_best, cudaStream_t s,
+               const int64_t *fbase = nullptr, double *out_best_power = nullptr)
 {
     const int prec = (int)P.precision;
     Plan plan;
@@ -504,6 +513,7 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
             ga.recompute = 0;
             ga.periodic = P.periodic;
             ga.span = P.span;
+            ga.fbase = fbase;
             slab_cur += b.main.gmem ? b.main.slab_bytes * (size_t)b.main.grid : 0;
             const int ph = variant == SSP_SS ? SSP_PHASE_PGRAM_SS : SSP_PHASE_PGRAM_SP;
             on = prof_begin(ph, s, mk);
@@ -532,9 +542,11 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
         ArgmaxArgs aa{};
         aa.power = out_power;
         aa.freq = freq;
+        aa.fbase = fbase;
         aa.n_freq = n_freq;
         aa.bad = d_bad;
         aa.best_period = out_best;
+        aa.best_power = out_best_power;
         on = prof_begin(SSP_PHASE_ARGMAX, s, mk);
         if ((e = argmax_launch(prec, aa, (int)n_obj, s))) break;
         prof_end(on, mk, s);
@@ -1092,6 +1104,132 @@ void ssp_autotune_clear(void)
     for (auto &a : g_tuned)
         for (auto &b : a)
             for (auto &c : b) c.store(0);
+}
+
+// ---------------------------------------------------------------------------
+// search-and-refine
+// ---------------------------------------------------------------------------
+int ssp_search_refine(const double *t, const double *y, const double *dy,
+                      const int64_t *n_per_object, int64_t n_objects, const double *coarse_grid,
+                      int64_t n_coarse, ssp_variant coarse_variant, ssp_variant fine_variant,
+                      int n_peaks, int n_fine, const ssp_params *params, double *out_best_period,
+                      double *out_best_power)
+{
+    g_err.clear();
+    ssp_params P;
+    ssp_default_params(&P);
+    if (params) P = *params;
+    int rc = check_params(&P);
+    if (rc) return rc;
+    if (P.span > 0.0) return fail(SSP_ERR_ARG, "search-and-refine needs the variable span");
+    rc = check_shape(n_per_object, n_objects, n_coarse, coarse_variant);
+    if (rc) return rc;
+    rc = check_shape(n_per_object, n_objects, 1, fine_variant);
+    if (rc) return rc;
+    if (!t || !y || !dy || !coarse_grid || !out_best_period || !out_best_power)
+        return fail(SSP_ERR_ARG, "NULL array argument");
+    if (n_coarse < 2) return fail(SSP_ERR_ARG, "the coarse grid needs at least 2 frequencies");
+    if (n_peaks < 1 || n_peaks > 64) return fail(SSP_ERR_ARG, "n_peaks must be in 1..64");
+    if (n_fine < 1 || (int64_t)n_peaks * n_fine > (int64_t)1 << 22)
+        return fail(SSP_ERR_ARG, "n_fine must be >= 1 with n_peaks * n_fine <= 2^22");
+    for (int64_t q = 0; q < n_coarse; ++q) {
+        if (!std::isfinite(coarse_grid[q]) || !(coarse_grid[q] > 0.0))
+            return fail(SSP_ERR_ARG, "coarse_grid[%lld] must be finite and > 0", (long long)q);
+        if (q > 0 && !(coarse_grid[q] > coarse_grid[q - 1]))
+            return fail(SSP_ERR_ARG, "the coarse grid must increase strictly");
+    }
+    int64_t N = 0;
+    for (int64_t o = 0; o < n_objects; ++o) N += n_per_object[o];
+    rc = check_values(t, y, dy, N, (int)P.precision);
+    if (rc) return rc;
+    std::call_once(g_pool_once, keep_pool_memory);
+    const int prec = (int)P.precision;
+    const size_t rs = rsize(prec);
+    const int64_t nf = (int64_t)n_peaks * n_fine;
+    cudaStream_t s;
+    SSP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const double budget = P.hbm_fraction * (double)free_b - kSlabReserve;
+    int status = SSP_OK;
+    double *d_coarse = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&d_coarse, 8 * (size_t)n_coarse, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_coarse, coarse_grid, 8 * (size_t)n_coarse, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) status = cuda_fail(e, "coarse grid");
+    int64_t o0 = 0, p0 = 0;
+    while (status == SSP_OK && o0 < n_objects) {
+        // objects per batch: inputs, coarse and fine powers and grids in the budget
+        int64_t o1 = o0, pts = 0;
+        double need = 0.0;
+        while (o1 < n_objects) {
+            const double add = (double)n_per_object[o1] * (24.0 + 8.0 + 2.0 * (double)rs) +
+                               (double)(n_coarse + nf) * (double)rs + 8.0 * (double)nf + 96.0;
+            if (o1 > o0 && need + add > budget) break;
+            need += add;
+            pts += n_per_object[o1];
+            ++o1;
+        }
+        const int64_t nb = o1 - o0;
+        const size_t in_b = align16(8 * (size_t)pts), cp_b = align16(rs * (size_t)(nb * n_coarse));
+        const size_t fp_b = align16(rs * (size_t)(nb * nf)), fg_b = align16(8 * (size_t)(nb * nf));
+        const size_t ob_b = align16(8 * (size_t)nb);
+        unsigned char *blk = nullptr;
+        e = cudaMallocAsync((void **)&blk, 3 * in_b + cp_b + fp_b + fg_b + 4 * ob_b, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            status = fail(SSP_ERR_NOMEM, "batch of %lld objects does not fit", (long long)nb);
+            break;
+        }
+        double *d_t = (double *)blk, *d_y = (double *)(blk + in_b), *d_dy = (double *)(blk + 2 * in_b);
+        void *d_cp = blk + 3 * in_b, *d_fp = blk + 3 * in_b + cp_b;
+        double *d_fg = (double *)(blk + 3 * in_b + cp_b + fp_b);
+        unsigned char *tail = blk + 3 * in_b + cp_b + fp_b + fg_b;
+        double *d_cbest = (double *)tail, *d_fbest = (double *)(tail + ob_b);
+        double *d_fpow = (double *)(tail + 2 * ob_b);
+        int64_t *d_fbase = (int64_t *)(tail + 3 * ob_b);
+        std::vector<int64_t> fbase((size_t)nb);
+        for (int64_t i = 0; i < nb; ++i) fbase[(size_t)i] = i * nf;
+        do {
+            if ((e = cudaMemcpyAsync(d_t, t + p0, 8 * (size_t)pts, cudaMemcpyHostToDevice, s))) break;
+            if ((e = cudaMemcpyAsync(d_y, y + p0, 8 * (size_t)pts, cudaMemcpyHostToDevice, s))) break;
+            if ((e = cudaMemcpyAsync(d_dy, dy + p0, 8 * (size_t)pts, cudaMemcpyHostToDevice, s))) break;
+            if ((e = cudaMemcpyAsync(d_fbase, fbase.data(), 8 * (size_t)nb, cudaMemcpyHostToDevice, s)))
+                break;
+            // coarse search
+            status = run_device(d_t, d_y, d_dy, n_per_object + o0, nb, d_coarse, n_coarse,
+                                coarse_variant, P, d_cp, d_cbest, s);
+            if (status) break;
+            PeaksArgs pa{};
+            pa.power = d_cp;
+            pa.coarse = d_coarse;
+            pa.n_coarse = n_coarse;
+            pa.k = n_peaks;
+            pa.n_fine = n_fine;
+            pa.fine = d_fg;
+            if ((e = peaks_launch(prec, pa, (int)nb, s))) break;
+            // refine on each object's own grids
+            status = run_device(d_t, d_y, d_dy, n_per_object + o0, nb, d_fg, nf, fine_variant, P,
+                                d_fp, d_fbest, s, d_fbase, d_fpow);
+            if (status) break;
+            if ((e = cudaMemcpyAsync(out_best_period + o0, d_fbest, 8 * (size_t)nb,
+                                     cudaMemcpyDeviceToHost, s)))
+                break;
+            if ((e = cudaMemcpyAsync(out_best_power + o0, d_fpow, 8 * (size_t)nb,
+                                     cudaMemcpyDeviceToHost, s)))
+                break;
+        } while (0);
+        if (e != cudaSuccess && status == SSP_OK) status = cuda_fail(e, "search-and-refine");
+        cudaFreeAsync(blk, s);
+        if (status == SSP_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            status = cuda_fail(e, "search-and-refine");
+        o0 = o1;
+        p0 += pts;
+    }
+    if (d_coarse) cudaFreeAsync(d_coarse, s);
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    return status;
 }
 
 }  // extern "C"

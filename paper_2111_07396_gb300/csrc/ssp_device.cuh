@@ -89,6 +89,7 @@ struct PgramArgs {
     int recompute;          // FP64 kernel: only flagged (o, q), float power out
     int periodic;           // 1: periodic windows; 0: windows clamped inside the data
     double span;            // > 0: Listing 1's fixed-span single smooth
+    const int64_t *fbase;   // null: one grid; else object o's grid starts at freq[fbase[o]]
     int power_f32;          // power array holds float
     float near_ss;          // SS margin for n <= 256 (scaled down above)
     float near_sp;          // SP margin in units of eps_fp32 * magnitude scale
@@ -1684,7 +1685,8 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
             if (bad) {
                 pw = __longlong_as_double(0x7ff8000000000000LL);
             } else {
-                const FreqResult r = process_frequency<R, VARIANT>(a, o, n, a.freq[q], fr, sm);
+                const double fq = a.freq[(a.fbase ? a.fbase[o] : 0) + q];
+                const FreqResult r = process_frequency<R, VARIANT>(a, o, n, fq, fr, sm);
                 const double c0 = a.chi0[o];
                 pw = (c0 > 0.0) ? 1.0 - r.chi2 / c0 : 0.0;
                 near = r.near;

@@ -128,8 +128,76 @@ __global__ void __launch_bounds__(256) argmax_kernel(ArgmaxArgs a)
             const long long oi = s_i[k];
             if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) { bv = ov; bi = oi; }
         }
-        a.best_period[o] = (a.bad[o] || bi < 0) ? __longlong_as_double(0x7ff8000000000000LL)
-                                                : 1.0 / a.freq[bi];
+        const double *fq = a.freq + (a.fbase ? a.fbase[o] : 0);
+        const bool nan = a.bad[o] || bi < 0;
+        a.best_period[o] = nan ? __longlong_as_double(0x7ff8000000000000LL) : 1.0 / fq[bi];
+        if (a.best_power) a.best_power[o] = nan ? __longlong_as_double(0x7ff8000000000000LL) : bv;
+    }
+}
+
+// Search-and-refine (the outlook of Sec. 6), one CTA per object: k rounds
+// pick the largest local maximum of the coarse power row (p[q] >= p[q-1]
+// and p[q] > p[q+1], a missing neighbour counting as lower; ties to the
+// lower index) that is not next to one already taken; fewer than k maxima
+// repeat the first.  Each peak q gets n_fine frequencies evenly from
+// f[q-1] to f[q+1] (one coarse step beyond q at either end of the grid; a
+// start at or below 0 moves to f[q]/2).
+template <typename R>
+__global__ void __launch_bounds__(256) peaks_kernel(PeaksArgs a)
+{
+    __shared__ double s_v[8];
+    __shared__ long long s_i[8];
+    __shared__ long long s_taken[64];
+    __shared__ int s_count;
+    const int o = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = blockDim.x >> 5;
+    const R *p = (const R *)a.power + (int64_t)o * a.n_coarse;
+    const int64_t n = a.n_coarse;
+    if (tid == 0) s_count = 0;
+    __syncthreads();
+    for (int round = 0; round < a.k; ++round) {
+        const int taken = s_count;
+        double bv = -INFINITY;
+        long long bi = -1;
+        for (int64_t q = tid; q < n; q += blockDim.x) {
+            const R v = p[q];
+            if (!((q == 0 || v >= p[q - 1]) && (q == n - 1 || v > p[q + 1]))) continue;
+            bool skip = false;
+            for (int i = 0; i < taken; ++i)
+                if (s_taken[i] >= q - 1 && s_taken[i] <= q + 1) skip = true;
+            if (skip) continue;
+            if (bi < 0 || (double)v > bv) { bv = (double)v; bi = q; }   // q ascends: ties keep the lower
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+            const long long oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+        }
+        if (lane == 0) { s_v[warp] = bv; s_i[warp] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < nw; ++w) {
+                const double ov = s_v[w];
+                const long long oi = s_i[w];
+                if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+            }
+            if (bi >= 0) s_taken[s_count++] = bi;
+        }
+        __syncthreads();
+        if (s_count == taken) break;   // no maximum left
+    }
+    const int got = s_count;
+    double *out = a.fine + (int64_t)o * a.k * a.n_fine;
+    for (int i = tid; i < a.k * a.n_fine; i += blockDim.x) {
+        const int pk = i / a.n_fine, j = i - pk * a.n_fine;
+        const long long q = got > 0 ? s_taken[pk < got ? pk : 0] : 0;
+        const double *f = a.coarse;
+        const double step_lo = q > 0 ? f[q] - f[q - 1] : (n > 1 ? f[1] - f[0] : 0.0);
+        const double step_hi = q < n - 1 ? f[q + 1] - f[q] : (n > 1 ? f[n - 1] - f[n - 2] : 0.0);
+        double lo = f[q] - step_lo;
+        const double hi = f[q] + step_hi;
+        if (!(lo > 0.0)) lo = 0.5 * f[q];
+        out[i] = a.n_fine > 1 ? lo + (hi - lo) * (double)j / (double)(a.n_fine - 1) : f[q];
     }
 }
 
@@ -146,6 +214,11 @@ __global__ void __launch_bounds__(256) argmax_kernel(ArgmaxArgs a)
     cudaError_t argmax_launch_##PREC(const ArgmaxArgs &a, int n_obj, cudaStream_t s)          \
     {                                                                                         \
         argmax_kernel<R><<<n_obj, 256, 0, s>>>(a);                                            \
+        return cudaGetLastError();                                                            \
+    }                                                                                         \
+    cudaError_t peaks_launch_##PREC(const PeaksArgs &a, int n_obj, cudaStream_t s)            \
+    {                                                                                         \
+        peaks_kernel<R><<<n_obj, 256, 0, s>>>(a);                                             \
         return cudaGetLastError();                                                            \
     }                                                                                         \
     }

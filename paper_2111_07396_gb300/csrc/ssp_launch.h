@@ -23,9 +23,21 @@ struct PrepArgs {
 struct ArgmaxArgs {
     const void *power;         // [n_obj][n_freq] R
     const double *freq;
+    const int64_t *fbase;      // null: one grid; else object o's grid starts at freq[fbase[o]]
     int64_t n_freq;
     const int *bad;
     double *best_period;       // [n_obj]
+    double *best_power;        // [n_obj] or null
+};
+
+// search-and-refine: per object, the top k local maxima of its coarse power
+// row and a grid of n_fine frequencies across each (see peaks_kernel)
+struct PeaksArgs {
+    const void *power;         // [n_obj][n_coarse] R
+    const double *coarse;      // [n_coarse], increasing
+    int64_t n_coarse;
+    int k, n_fine;
+    double *fine;              // [n_obj][k * n_fine]
 };
 
 // precision: 0 = FP64, 1 = FP32C, kPrecRedo = the FP64 recompute of flagged
@@ -33,6 +45,7 @@ struct ArgmaxArgs {
 constexpr int kPrecRedo = 2;
 cudaError_t prep_launch(int precision, const PrepArgs &a, int n_obj, cudaStream_t s);
 cudaError_t argmax_launch(int precision, const ArgmaxArgs &a, int n_obj, cudaStream_t s);
+cudaError_t peaks_launch(int precision, const PeaksArgs &a, int n_obj, cudaStream_t s);
 // variant: VAR_SS, VAR_SP or VAR_FIXED; per: periodic windows, else clamped.
 // Sets the dynamic shared-memory limit and returns resident CTAs per SM.
 cudaError_t pgram_occupancy(int precision, int variant, bool gmem, bool per, int G, size_t smem,

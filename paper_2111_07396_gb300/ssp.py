@@ -102,6 +102,10 @@ def lib():
         L.ssp_autotune_clear.restype = None
         L.ssp_measure_alu_peaks.argtypes = [P, P]
         L.ssp_measure_alu_peaks.restype = ctypes.c_int
+        L.ssp_search_refine.argtypes = [P, P, P, P, i64, P, i64, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, ctypes.POINTER(ssp_params), P,
+                                        P]
+        L.ssp_search_refine.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -253,6 +257,23 @@ def ssp_measure_alu_peaks():
     if rc:
         raise SSPError(rc, "ALU peak microbenchmark failed")
     return a.value, b.value
+
+
+def ssp_search_refine(t, y, dy, n_per_object, coarse_grid, coarse_variant="sp",
+                      fine_variant="ss", n_peaks=3, n_fine=64, precision="fp32c", alpha=9.0,
+                      spans=None, params=None, periodic=True):
+    """Coarse search, then the fine variant on dense grids around each
+    object's top peaks; returns (best_period[n_objects], best_power[n_objects])."""
+    p = params if params is not None else ssp_default_params(precision, alpha, spans,
+                                                             periodic=periodic)
+    t_, y_, dy_, cg = _f64(t), _f64(y), _f64(dy), _f64(coarse_grid)
+    npo = np.ascontiguousarray(n_per_object, dtype=np.int64)
+    bp, bw = np.empty(npo.size), np.empty(npo.size)
+    _check(lib().ssp_search_refine(_ptr(t_), _ptr(y_), _ptr(dy_), _ptr(npo), int(npo.size),
+                                   _ptr(cg), int(cg.size), VARIANTS[coarse_variant],
+                                   VARIANTS[fine_variant], int(n_peaks), int(n_fine),
+                                   ctypes.byref(p), _ptr(bp), _ptr(bw)))
+    return bp, bw
 
 
 def ssp_autotune_clear() -> None:

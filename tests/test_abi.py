@@ -126,3 +126,15 @@ def test_autotune_rejects_bad_arguments_before_cuda():
             ssp.ssp_autotune(**args)
         assert ei.value.status == status
     ssp.ssp_autotune_clear()   # needs no device
+
+
+def test_search_refine_rejects_bad_arguments_before_cuda():
+    t, y, dy = np.arange(8.0), np.ones(8), np.ones(8)
+    base = dict(t=t, y=y, dy=dy, n_per_object=[8], coarse_grid=[0.3, 0.4, 0.5])
+    for kw in (dict(coarse_grid=[0.3]), dict(coarse_grid=[0.3, 0.2]), dict(n_peaks=0),
+               dict(n_peaks=65), dict(n_fine=0), dict(coarse_grid=[0.0, 0.4])):
+        args = dict(base)
+        args.update(kw)
+        with pytest.raises(ssp.SSPError) as ei:
+            ssp.ssp_search_refine(**args)
+        assert ei.value.status == ssp.SSP_ERR_ARG
