@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "libssp.so")
 SOURCES = ["ssp_api.cu", "ssp_server.cu", "ssp_fp32.cu", "ssp_fp32_clamp.cu", "ssp_fp64.cu",
-           "ssp_fp64_clamp.cu", "ssp_redo.cu", "ssp_redo_clamp.cu", "ssp_peaks.cu"]
+           "ssp_fp64_clamp.cu", "ssp_redo.cu", "ssp_redo_clamp.cu", "ssp_fp32_shared.cu",
+           "ssp_fp64_shared.cu", "ssp_redo_shared.cu", "ssp_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

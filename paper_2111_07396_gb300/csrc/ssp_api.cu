@@ -36,12 +36,18 @@ cudaError_t pgram_occupancy_redo_per(int, bool, int, size_t, int *);
 cudaError_t pgram_launch_redo_per(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
 cudaError_t pgram_occupancy_redo_clamp(int, bool, int, size_t, int *);
 cudaError_t pgram_launch_redo_clamp(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_fp32_shared(int, bool, int, size_t, int *);
+cudaError_t pgram_launch_fp32_shared(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_fp64_shared(int, bool, int, size_t, int *);
+cudaError_t pgram_launch_fp64_shared(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_redo_shared(int, bool, int, size_t, int *);
+cudaError_t pgram_launch_redo_shared(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
 size_t pgram_small_bytes_fp32(int, int);
-size_t pgram_frame_bytes_fp32(int, int);
+size_t pgram_frame_bytes_fp32(int, int, bool);
 size_t pgram_small_bytes_fp64(int, int);
-size_t pgram_frame_bytes_fp64(int, int);
+size_t pgram_frame_bytes_fp64(int, int, bool);
 size_t pgram_small_bytes_redo(int, int);
-size_t pgram_frame_bytes_redo(int, int);
+size_t pgram_frame_bytes_redo(int, int, bool);
 
 cudaError_t prep_launch(int p, const PrepArgs &a, int n, cudaStream_t s)
 {
@@ -55,8 +61,13 @@ cudaError_t peaks_launch(int p, const PeaksArgs &a, int n, cudaStream_t s)
 {
     return p == SSP_FP64 ? peaks_launch_fp64(a, n, s) : peaks_launch_fp32(a, n, s);
 }
-cudaError_t pgram_occupancy(int p, int v, bool g, bool per, int G, size_t smem, int *bps)
+cudaError_t pgram_occupancy(int p, int v, bool g, bool per, bool shared, int G, size_t smem,
+                            int *bps)
 {
+    if (shared)   // periodic windows only
+        return p == SSP_FP64 ? pgram_occupancy_fp64_shared(v, g, G, smem, bps)
+             : p == kPrecRedo ? pgram_occupancy_redo_shared(v, g, G, smem, bps)
+                              : pgram_occupancy_fp32_shared(v, g, G, smem, bps);
     if (per)
         return p == SSP_FP64 ? pgram_occupancy_fp64_per(v, g, G, smem, bps)
              : p == kPrecRedo ? pgram_occupancy_redo_per(v, g, G, smem, bps)
@@ -65,9 +76,13 @@ cudaError_t pgram_occupancy(int p, int v, bool g, bool per, int G, size_t smem, 
          : p == kPrecRedo ? pgram_occupancy_redo_clamp(v, g, G, smem, bps)
                           : pgram_occupancy_fp32_clamp(v, g, G, smem, bps);
 }
-cudaError_t pgram_launch(int p, int v, bool g, bool per, int grid, int G, size_t smem,
+cudaError_t pgram_launch(int p, int v, bool g, bool per, bool shared, int grid, int G, size_t smem,
                          const PgramArgs &a, cudaStream_t s)
 {
+    if (shared)   // periodic windows only
+        return p == SSP_FP64 ? pgram_launch_fp64_shared(v, g, grid, G, smem, a, s)
+             : p == kPrecRedo ? pgram_launch_redo_shared(v, g, grid, G, smem, a, s)
+                              : pgram_launch_fp32_shared(v, g, grid, G, smem, a, s);
     if (per)
         return p == SSP_FP64 ? pgram_launch_fp64_per(v, g, grid, G, smem, a, s)
              : p == kPrecRedo ? pgram_launch_redo_per(v, g, grid, G, smem, a, s)
@@ -82,11 +97,11 @@ size_t pgram_small_bytes(int p, int G, int variant)
          : p == kPrecRedo ? pgram_small_bytes_redo(G, variant)
                           : pgram_small_bytes_fp32(G, variant);
 }
-size_t pgram_frame_bytes(int p, int n, int variant)
+size_t pgram_frame_bytes(int p, int n, int variant, bool keep_perm)
 {
-    return p == SSP_FP64 ? pgram_frame_bytes_fp64(n, variant)
-         : p == kPrecRedo ? pgram_frame_bytes_redo(n, variant)
-                          : pgram_frame_bytes_fp32(n, variant);
+    return p == SSP_FP64 ? pgram_frame_bytes_fp64(n, variant, keep_perm)
+         : p == kPrecRedo ? pgram_frame_bytes_redo(n, variant, keep_perm)
+                          : pgram_frame_bytes_fp32(n, variant, keep_perm);
 }
 }  // namespace ssp
 
@@ -215,6 +230,7 @@ struct LaunchCfg {
 
 struct Bucket {
     int G = 32, n_max = 0;
+    bool shared = false;    // some item covers several objects with identical times
     LaunchCfg main, redo;   // redo: FP64 recompute of flagged FP32C frequencies
     std::vector<int> objects;
     std::vector<int4> items;
@@ -238,16 +254,16 @@ int device_limits(int *num_sms, size_t *max_smem)
 }
 
 // frame placement and persistent grid of one kernel for one bucket
-int configure(int precision, int variant, bool per, int G, int n_max, int sms, size_t max_smem,
-              LaunchCfg &c)
+int configure(int precision, int variant, bool per, bool shared, int G, int n_max, int sms,
+              size_t max_smem, LaunchCfg &c)
 {
     const size_t small = align16(pgram_small_bytes(precision, G, variant));
-    const size_t frame = align16(pgram_frame_bytes(precision, n_max, variant));
+    const size_t frame = align16(pgram_frame_bytes(precision, n_max, variant, shared));
     c.gmem = small + frame + 1024 > max_smem;
     c.smem = c.gmem ? small : small + frame;
     c.slab_bytes = c.gmem ? frame : 0;
     int bps = 0;
-    cudaError_t e = pgram_occupancy(precision, variant, c.gmem, per, G, c.smem, &bps);
+    cudaError_t e = pgram_occupancy(precision, variant, c.gmem, per, shared, G, c.smem, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy");
     if (bps < 1) return fail(SSP_ERR_NOMEM, "a CTA frame for n = %d does not fit", n_max);
     c.grid = bps * sms;
@@ -256,8 +272,10 @@ int configure(int precision, int variant, bool per, int G, int n_max, int sms, s
 
 // Length buckets (one launch each, sized for the bucket's largest object),
 // work items (object, frequency range) ordered longest first.
+// group (host, or null): group[o] = number of objects o, o+1, ... that share
+// object o's times when o leads such a run, 0 for the run's other objects
 int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision, int variant,
-               bool per, Plan &plan)
+               bool per, Plan &plan, const int *group = nullptr)
 {
     int sms = 0;
     size_t max_smem = 0;
@@ -268,9 +286,10 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
     for (int r = 0; r < kRanges; ++r) {
         Bucket b;
         for (int64_t o = 0; o < n_obj; ++o)
-            if (range_of((int)npo[o]) == r) {
+            if (range_of((int)npo[o]) == r && (!group || group[o] > 0)) {
                 b.objects.push_back((int)o);
                 b.n_max = std::max(b.n_max, (int)npo[o]);
+                if (group && group[o] > 1) b.shared = true;
             }
         if (b.objects.empty()) continue;
         b.G = group_size(b.n_max, variant, precision);
@@ -279,10 +298,10 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
     plan.items_total = 0;
     plan.slab_total = 0;
     for (Bucket &b : plan.buckets) {
-        rc = configure(precision, variant, per, b.G, b.n_max, sms, max_smem, b.main);
+        rc = configure(precision, variant, per, b.shared, b.G, b.n_max, sms, max_smem, b.main);
         if (rc) return rc;
         if (plan.redo) {
-            rc = configure(kPrecRedo, variant, per, b.G, b.n_max, sms, max_smem, b.redo);
+            rc = configure(kPrecRedo, variant, per, b.shared, b.G, b.n_max, sms, max_smem, b.redo);
             if (rc) return rc;
         }
         const int resident = b.main.grid;
@@ -292,11 +311,13 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
         per_obj = std::max<int64_t>(1, std::min<int64_t>(per_obj, n_freq));
         const int64_t chunk = (n_freq + per_obj - 1) / per_obj;
         std::vector<std::pair<int64_t, int4>> keyed;
-        for (int o : b.objects)
+        for (int o : b.objects) {
+            const int m = group ? group[o] : 1;
             for (int64_t q0 = 0; q0 < n_freq; q0 += chunk) {
                 const int q1 = (int)std::min<int64_t>(n_freq, q0 + chunk);
-                keyed.push_back({-(int64_t)npo[o] * (q1 - q0), make_int4(o, (int)q0, q1, 0)});
+                keyed.push_back({-(int64_t)npo[o] * m * (q1 - q0), make_int4(o, (int)q0, q1, m)});
             }
+        }
         std::stable_sort(keyed.begin(), keyed.end(),
                          [](const auto &x, const auto &y) { return x.first < y.first; });
         b.items.resize(keyed.size());
@@ -407,18 +428,78 @@ int check_values(const double *t, const double *y, const double *dy, int64_t N, 
     return SSP_OK;
 }
 
+// Objects of one batch whose time arrays are bitwise equal (same survey
+// cadence) share each frequency's fold and sort.  order lists the batch's
+// objects (indices from o0) with every such run adjacent, its leader first;
+// group holds the run length at each leader and 0 at the others.
+struct Grouping {
+    std::vector<int64_t> order, npo;
+    std::vector<int> group;
+    bool any = false;
+};
+
+Grouping group_by_times(const double *t, const int64_t *npo, int64_t o0, int64_t o1, int64_t p0)
+{
+    const int64_t nb = o1 - o0;
+    std::vector<int64_t> off((size_t)nb + 1, p0);
+    for (int64_t k = 0; k < nb; ++k) off[k + 1] = off[k] + npo[o0 + k];
+    std::vector<std::pair<uint64_t, int64_t>> hk((size_t)nb);
+    for (int64_t k = 0; k < nb; ++k) {
+        uint64_t h = 1469598103934665603ull ^ (uint64_t)npo[o0 + k];   // FNV-1a
+        const unsigned char *b = (const unsigned char *)(t + off[k]);
+        for (size_t i = 0; i < 8 * (size_t)npo[o0 + k]; ++i) h = (h ^ b[i]) * 1099511628211ull;
+        hk[(size_t)k] = {h, k};
+    }
+    std::sort(hk.begin(), hk.end());
+    std::vector<int64_t> lead((size_t)nb, -1);   // each object's group leader
+    for (size_t a = 0; a < hk.size();) {
+        size_t b = a;
+        while (b < hk.size() && hk[b].first == hk[a].first) ++b;
+        std::vector<int64_t> leaders;
+        for (size_t i = a; i < b; ++i) {
+            const int64_t k = hk[i].second, n = npo[o0 + k];
+            for (int64_t L : leaders)
+                if (npo[o0 + L] == n &&
+                    std::memcmp(t + off[L], t + off[k], 8 * (size_t)n) == 0) {
+                    lead[(size_t)k] = L;
+                    break;
+                }
+            if (lead[(size_t)k] < 0) {
+                lead[(size_t)k] = k;
+                leaders.push_back(k);
+            }
+        }
+        a = b;
+    }
+    std::vector<std::vector<int64_t>> members((size_t)nb);
+    for (int64_t k = 0; k < nb; ++k) members[(size_t)lead[(size_t)k]].push_back(k);
+    Grouping g;
+    for (int64_t k = 0; k < nb; ++k) {
+        if (lead[(size_t)k] != k) continue;
+        const auto &m = members[(size_t)k];
+        for (size_t i = 0; i < m.size(); ++i) {
+            g.order.push_back(m[i]);
+            g.npo.push_back(npo[o0 + m[i]]);
+            g.group.push_back(i == 0 ? (int)m.size() : 0);
+        }
+        if (m.size() > 1) g.any = true;
+    }
+    return g;
+}
+
 // fbase (device, or null): object o's grid is freq[fbase[o] .. + n_freq);
 // out_best_power (device, or null) receives each object's largest power
 int run_device(const double *t, const double *y, const double *dy, const int64_t *npo,
                int64_t n_obj, const double *freq, int64_t n_freq, ssp_variant variant,
                const ssp_params &P, void *out_power, double *out_best, cudaStream_t s,
-               const int64_t *fbase = nullptr, double *out_best_power = nullptr)
+               const int64_t *fbase = nullptr, double *out_best_power = nullptr,
+               const int *group = nullptr)
 {
     const int prec = (int)P.precision;
     Plan plan;
     const int kv = kernel_variant(variant, P);
     const bool per = P.periodic != 0;
-    int rc = build_plan(npo, n_obj, n_freq, prec, kv, per, plan);
+    int rc = build_plan(npo, n_obj, n_freq, prec, kv, per, plan, group);
     if (rc) return rc;
     std::vector<int64_t> off((size_t)n_obj + 1, 0);
     for (int64_t o = 0; o < n_obj; ++o) off[o + 1] = off[o] + npo[o];
@@ -517,7 +598,7 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
             slab_cur += b.main.gmem ? b.main.slab_bytes * (size_t)b.main.grid : 0;
             const int ph = variant == SSP_SS ? SSP_PHASE_PGRAM_SS : SSP_PHASE_PGRAM_SP;
             on = prof_begin(ph, s, mk);
-            if ((e = pgram_launch(prec, kv, b.main.gmem, per, b.main.grid, b.G, b.main.smem,
+            if ((e = pgram_launch(prec, kv, b.main.gmem, per, b.shared, b.main.grid, b.G, b.main.smem,
                                   ga, s)))
                 break;
             prof_end(on, mk, s);
@@ -531,7 +612,7 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
                 ga.recompute = 1;
                 slab_cur += b.redo.gmem ? b.redo.slab_bytes * (size_t)b.redo.grid : 0;
                 on = prof_begin(SSP_PHASE_REDO, s, mk);
-                if ((e = pgram_launch(kPrecRedo, kv, b.redo.gmem, per, b.redo.grid, b.G,
+                if ((e = pgram_launch(kPrecRedo, kv, b.redo.gmem, per, b.shared, b.redo.grid, b.G,
                                       b.redo.smem, ga, s)))
                     break;
                 prof_end(on, mk, s);
@@ -693,14 +774,14 @@ int run_device_noalloc(const double *t, const double *y, const double *dy, const
             ga.recompute = 0;
             ga.periodic = P.periodic;
             ga.span = P.span;
-            if ((e = pgram_launch(prec, kv, false, per, b.main.grid, b.G, b.main.smem, ga, s)))
+            if ((e = pgram_launch(prec, kv, false, per, false, b.main.grid, b.G, b.main.smem, ga, s)))
                 break;
             if (plan.redo) {
                 ga.yc = d_yc64;
                 ga.wv = d_wv64;
                 ga.item_counter = d_counters + 2 * k + 1;
                 ga.recompute = 1;
-                if ((e = pgram_launch(kPrecRedo, kv, false, per, b.redo.grid, b.G, b.redo.smem,
+                if ((e = pgram_launch(kPrecRedo, kv, false, per, false, b.redo.grid, b.G, b.redo.smem,
                                       ga, s)))
                     break;
             }
@@ -944,6 +1025,49 @@ int ssp_periodogram(const double *t, const double *y, const double *dy,
                *d_dy = (double *)(blk + 2 * align16(in_b));
         void *d_pw = blk + 3 * align16(in_b);
         double *d_best = (double *)(blk + 3 * align16(in_b) + align16(pw_b));
+        // (shared sorts are built for periodic windows)
+        const Grouping gp = P.periodic ? group_by_times(t, n_per_object, o0, o1, p0) : Grouping{};
+        if (gp.any) {
+            // objects sharing their times run next to each other, leader first
+            std::vector<double> st((size_t)pts), sy((size_t)pts), sdy((size_t)pts);
+            std::vector<int64_t> off((size_t)nb + 1, p0);
+            for (int64_t k = 0; k < nb; ++k) off[k + 1] = off[k] + n_per_object[o0 + k];
+            size_t at = 0;
+            for (int64_t k : gp.order) {
+                const size_t n = (size_t)n_per_object[o0 + k];
+                std::memcpy(&st[at], t + off[k], 8 * n);
+                std::memcpy(&sy[at], y + off[k], 8 * n);
+                std::memcpy(&sdy[at], dy + off[k], 8 * n);
+                at += n;
+            }
+            std::vector<unsigned char> hpw(pw_b);
+            std::vector<double> hbest((size_t)nb);
+            do {
+                if ((e = cudaMemcpyAsync(d_t, st.data(), in_b, cudaMemcpyHostToDevice, s))) break;
+                if ((e = cudaMemcpyAsync(d_y, sy.data(), in_b, cudaMemcpyHostToDevice, s))) break;
+                if ((e = cudaMemcpyAsync(d_dy, sdy.data(), in_b, cudaMemcpyHostToDevice, s))) break;
+                status = run_device(d_t, d_y, d_dy, gp.npo.data(), nb, d_freq, n_freq, variant, P,
+                                    d_pw, d_best, s, nullptr, nullptr, gp.group.data());
+                if (status) break;
+                if ((e = cudaMemcpyAsync(hpw.data(), d_pw, pw_b, cudaMemcpyDeviceToHost, s))) break;
+                if ((e = cudaMemcpyAsync(hbest.data(), d_best, 8 * (size_t)nb,
+                                         cudaMemcpyDeviceToHost, s)))
+                    break;
+                if ((e = cudaStreamSynchronize(s))) break;
+                const size_t row = rs * (size_t)n_freq;
+                for (int64_t k = 0; k < nb; ++k) {
+                    const int64_t o = o0 + gp.order[(size_t)k];
+                    std::memcpy((unsigned char *)out_power + row * (size_t)o,
+                                hpw.data() + row * (size_t)k, row);
+                    out_best_period[o] = hbest[(size_t)k];
+                }
+            } while (0);
+            if (e && status == SSP_OK) status = cuda_fail(e, "batch with shared times");
+            cudaFreeAsync(blk, s);
+            o0 = o1;
+            p0 += pts;
+            continue;
+        }
         do {
             if ((e = cudaMemcpyAsync(d_t, t + p0, in_b, cudaMemcpyHostToDevice, s))) break;
             if ((e = cudaMemcpyAsync(d_y, y + p0, in_b, cudaMemcpyHostToDevice, s))) break;

@@ -182,14 +182,20 @@ __host__ __device__ inline size_t tie_offset(int n, int ncols)
 // columns a variant keeps: SS uses X, WT, Y and C0..C6; SP only X, WT, Y
 __host__ __device__ inline int frame_cols(int variant) { return variant == VAR_SS ? 10 : 3; }
 
+// keep_perm: objects with identical times share one sort (their frame keeps
+// perm for every member's gather); an SS frame then holds perm past the tie
+// bitmask, clear of the smoother columns that overlay the sort region
 template <typename R>
-__host__ __device__ inline size_t frame_bytes(int n, int variant)
+__host__ __device__ inline size_t frame_bytes(int n, int variant, bool keep_perm = false)
 {
-    return tie_offset<R>(n, frame_cols(variant)) + align16(4 * tie_words(n));
+    size_t b = tie_offset<R>(n, frame_cols(variant)) + align16(4 * tie_words(n));
+    if (keep_perm && variant == VAR_SS) b += align16(2 * (size_t)pow2_at_least(n));
+    return b;
 }
 
 template <typename R>
-__device__ inline Frame<R> carve_frame(unsigned char *base, int n, int variant)
+__device__ inline Frame<R> carve_frame(unsigned char *base, int n, int variant,
+                                       bool keep_perm = false)
 {
     Frame<R> f;
     const size_t col = align16(sizeof(R) * (size_t)n), xwy = xwy_bytes<R>(n);
@@ -210,6 +216,9 @@ __device__ inline Frame<R> carve_frame(unsigned char *base, int n, int variant)
     f.cnt = (uint32_t *)(s + 2 * a4 + ap);
     f.ph = (double *)(s + 2 * a4 + ap + align16(4 * (size_t)bucket_count(n)));
     f.tie = (uint32_t *)(base + tie_offset<R>(n, frame_cols(variant)));
+    if (keep_perm && variant == VAR_SS)
+        f.perm = (uint16_t *)(base + tie_offset<R>(n, frame_cols(variant)) +
+                              align16(4 * tie_words(n)));
     f.per = 1;
     return f;
 }
@@ -1215,14 +1224,27 @@ __device__ inline FreqResult fixed_span_pass(const PgramArgs &a, const Frame<R> 
 // one (object, frequency)
 // ---------------------------------------------------------------------------
 template <typename R, int VARIANT, typename A>
-__device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, double f,
-                                        const Frame<R> &fr, const Small<R, A> &sm)
+__device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, int n, double f,
+                                        const Frame<R> &fr, const Small<R, A> &sm, bool reuse)
 {
     const int tid = threadIdx.x, G = blockDim.x;
     const int64_t base = a.off[obj];
     const R *yc = (const R *)a.yc + base;
     const R *wv = (const R *)a.wv + base;
-    const double *tt = a.tt + base;
+    bool ties, flat;
+    if (reuse) {
+        // the group leader's sort holds: X, the tie bits and perm are those
+        // of this object's identical times; only y and w are its own
+        for (int j = tid; j < n; j += G) {
+            const uint32_t i = fr.perm[j];
+            fr.WT[j] = wv[i];
+            fr.Y[j] = yc[i];
+        }
+        __syncthreads();
+        ties = sm.flags[0] != 0;
+        flat = sm.flags[1] != 0;
+    } else {
+    const double *tt = a.tt + a.off[lead];
 
     // ---- fold and sort ----
     fold_and_sort(fr, n, sm, tt, f);
@@ -1263,9 +1285,14 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
         if ((tid & 31) == 0) fr.tie[j0 >> 5] = word;
         tie |= tj;
     }
-    const bool ties = __syncthreads_or(tie) != 0;
-    const bool flat = (sizeof(R) == 8) ? !(fr.ph[fr.perm[n - 1]] > fr.ph[fr.perm[0]])
-                                       : (fr.key[n - 1] == fr.key[0] && fr.klo[n - 1] == fr.klo[0]);
+    ties = __syncthreads_or(tie) != 0;
+    flat = (sizeof(R) == 8) ? !(fr.ph[fr.perm[n - 1]] > fr.ph[fr.perm[0]])
+                            : (fr.key[n - 1] == fr.key[0] && fr.klo[n - 1] == fr.klo[0]);
+    if (tid == 0) {   // for the group's later objects
+        sm.flags[0] = ties;
+        sm.flags[1] = flat;
+    }
+    }
 
     // ---- degenerate abscissae: weighted mean (Listing 1) ----
     if (flat) {
@@ -1655,7 +1682,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int n, doub
 // FP32C launches flag frequencies whose decisions came within their margins;
 // the FP64 kernel's recompute launch then redoes exactly those frequencies
 // and overwrites their (float) power.
-template <typename R, int VARIANT, bool GMEM, bool PLAIN, bool PER>
+template <typename R, int VARIANT, bool GMEM, bool PLAIN, bool PER, bool SHARED>
 __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
 {
     typedef typename AccSel<R, PLAIN>::T A;
@@ -1672,31 +1699,40 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
         __syncthreads();
         if (it >= a.n_items) break;
         const int4 item = a.items[it];
-        const int o = item.x;
+        const int o = item.x;                 // first object of the item
+        // SHARED: objects o..o+m-1 share their times, and with them each
+        // frequency's fold and sort
+        const int m = SHARED && item.w > 1 ? item.w : 1;
         const int n = (int)(a.off[o + 1] - a.off[o]);
-        Frame<R> fr = carve_frame<R>(big, n, VARIANT);
+        Frame<R> fr = carve_frame<R>(big, n, VARIANT, SHARED);
         fr.per = PER;
-        const bool bad = a.bad[o] != 0;
         for (int q = item.y; q < item.z; ++q) {
-            const int64_t at = (int64_t)o * a.n_freq + q;
-            if (a.recompute && (bad || a.near[at] == 0)) continue;   // block-uniform
-            double pw;
-            bool near = false;
-            if (bad) {
-                pw = __longlong_as_double(0x7ff8000000000000LL);
-            } else {
-                const double fq = a.freq[(a.fbase ? a.fbase[o] : 0) + q];
-                const FreqResult r = process_frequency<R, VARIANT>(a, o, n, fq, fr, sm);
-                const double c0 = a.chi0[o];
-                pw = (c0 > 0.0) ? 1.0 - r.chi2 / c0 : 0.0;
-                near = r.near;
+            bool sorted = false;
+            for (int k = 0; k < m; ++k) {
+                const int obj = o + k;
+                const int64_t at = (int64_t)obj * a.n_freq + q;
+                const bool bad = a.bad[obj] != 0;
+                if (a.recompute && (bad || a.near[at] == 0)) continue;   // block-uniform
+                double pw;
+                bool near = false;
+                if (bad) {
+                    pw = __longlong_as_double(0x7ff8000000000000LL);
+                } else {
+                    const double fq = a.freq[(a.fbase ? a.fbase[o] : 0) + q];
+                    const FreqResult r =
+                        process_frequency<R, VARIANT>(a, obj, o, n, fq, fr, sm, SHARED && sorted);
+                    sorted = true;
+                    const double c0 = a.chi0[obj];
+                    pw = (c0 > 0.0) ? 1.0 - r.chi2 / c0 : 0.0;
+                    near = r.near;
+                }
+                if (threadIdx.x == 0) {
+                    if (a.power_f32) ((float *)a.power)[at] = (float)pw;
+                    else ((double *)a.power)[at] = pw;
+                    if (near && a.near) a.near[at] = 1;
+                }
+                __syncthreads();
             }
-            if (threadIdx.x == 0) {
-                if (a.power_f32) ((float *)a.power)[at] = (float)pw;
-                else ((double *)a.power)[at] = pw;
-                if (near && a.near) a.near[at] = 1;
-            }
-            __syncthreads();
         }
     }
 }

@@ -224,18 +224,19 @@ __global__ void __launch_bounds__(256) peaks_kernel(PeaksArgs a)
     }
 
 // periodogram kernels of one precision, accumulator and window mode (PER:
-// periodic windows, else clamped inside the data); SUF names the functions
-#define SSP_INSTANTIATE_PGRAM(R, PLAIN, PER, SUF)                                             \
+// periodic windows, else clamped inside the data); SHARED: work items may
+// cover several objects with identical times; SUF names the functions
+#define SSP_INSTANTIATE_PGRAM(R, PLAIN, PER, SHARED, SUF)                                             \
     namespace ssp {                                                                           \
     template <int V, bool GM>                                                                 \
     static cudaError_t occ_##SUF(int G, size_t smem, int *bps)                                \
     {                                                                                         \
-        cudaError_t e = cudaFuncSetAttribute(pgram_kernel<R, V, GM, PLAIN, PER>,              \
+        cudaError_t e = cudaFuncSetAttribute(pgram_kernel<R, V, GM, PLAIN, PER, SHARED>,              \
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                              (int)smem);                                      \
         if (e != cudaSuccess) return e;                                                       \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                 \
-            bps, pgram_kernel<R, V, GM, PLAIN, PER>, G, smem);                                \
+            bps, pgram_kernel<R, V, GM, PLAIN, PER, SHARED>, G, smem);                                \
     }                                                                                         \
     cudaError_t pgram_occupancy_##SUF(int variant, bool gmem, int G, size_t smem, int *bps)   \
     {                                                                                         \
@@ -255,20 +256,20 @@ __global__ void __launch_bounds__(256) peaks_kernel(PeaksArgs a)
     {                                                                                         \
         switch (variant) {                                                                    \
         case VAR_SS:                                                                          \
-            if (gmem) pgram_kernel<R, VAR_SS, true, PLAIN, PER><<<grid, G, smem, s>>>(a);     \
-            else pgram_kernel<R, VAR_SS, false, PLAIN, PER><<<grid, G, smem, s>>>(a);         \
+            if (gmem) pgram_kernel<R, VAR_SS, true, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);     \
+            else pgram_kernel<R, VAR_SS, false, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);         \
             break;                                                                            \
         case VAR_SP:                                                                          \
-            if (gmem) pgram_kernel<R, VAR_SP, true, PLAIN, PER><<<grid, G, smem, s>>>(a);     \
-            else pgram_kernel<R, VAR_SP, false, PLAIN, PER><<<grid, G, smem, s>>>(a);         \
+            if (gmem) pgram_kernel<R, VAR_SP, true, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);     \
+            else pgram_kernel<R, VAR_SP, false, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);         \
             break;                                                                            \
         case VAR_SPG:                                                                         \
-            if (gmem) pgram_kernel<R, VAR_SPG, true, PLAIN, PER><<<grid, G, smem, s>>>(a);    \
-            else pgram_kernel<R, VAR_SPG, false, PLAIN, PER><<<grid, G, smem, s>>>(a);        \
+            if (gmem) pgram_kernel<R, VAR_SPG, true, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);    \
+            else pgram_kernel<R, VAR_SPG, false, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);        \
             break;                                                                            \
         default:                                                                              \
-            if (gmem) pgram_kernel<R, VAR_FIXED, true, PLAIN, PER><<<grid, G, smem, s>>>(a);  \
-            else pgram_kernel<R, VAR_FIXED, false, PLAIN, PER><<<grid, G, smem, s>>>(a);      \
+            if (gmem) pgram_kernel<R, VAR_FIXED, true, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);  \
+            else pgram_kernel<R, VAR_FIXED, false, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);      \
         }                                                                                     \
         return cudaGetLastError();                                                            \
     }                                                                                         \
@@ -281,5 +282,8 @@ __global__ void __launch_bounds__(256) peaks_kernel(PeaksArgs a)
     {                                                                                         \
         return small_bytes<typename AccSel<R, PLAIN>::T>(G, variant);                         \
     }                                                                                         \
-    size_t pgram_frame_bytes_##PREC(int n, int variant) { return frame_bytes<R>(n, variant); } \
+    size_t pgram_frame_bytes_##PREC(int n, int variant, bool keep_perm)                       \
+    {                                                                                         \
+        return frame_bytes<R>(n, variant, keep_perm);                                         \
+    }                                                                                         \
     }

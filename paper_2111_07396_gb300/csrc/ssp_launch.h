@@ -48,12 +48,14 @@ cudaError_t argmax_launch(int precision, const ArgmaxArgs &a, int n_obj, cudaStr
 cudaError_t peaks_launch(int precision, const PeaksArgs &a, int n_obj, cudaStream_t s);
 // variant: VAR_SS, VAR_SP or VAR_FIXED; per: periodic windows, else clamped.
 // Sets the dynamic shared-memory limit and returns resident CTAs per SM.
-cudaError_t pgram_occupancy(int precision, int variant, bool gmem, bool per, int G, size_t smem,
-                            int *blocks_per_sm);
-cudaError_t pgram_launch(int precision, int variant, bool gmem, bool per, int grid, int G,
-                         size_t smem, const PgramArgs &a, cudaStream_t s);
+// shared: work items may cover several objects with identical times
+// (periodic windows only).
+cudaError_t pgram_occupancy(int precision, int variant, bool gmem, bool per, bool shared, int G,
+                            size_t smem, int *blocks_per_sm);
+cudaError_t pgram_launch(int precision, int variant, bool gmem, bool per, bool shared, int grid,
+                         int G, size_t smem, const PgramArgs &a, cudaStream_t s);
 
 size_t pgram_small_bytes(int precision, int G, int variant);
-size_t pgram_frame_bytes(int precision, int n, int variant);
+size_t pgram_frame_bytes(int precision, int n, int variant, bool keep_perm);
 
 }  // namespace ssp
