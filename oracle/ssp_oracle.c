@@ -31,10 +31,16 @@
  *   periodogram     Alg. 1 end to end, power = 1 - chi2/chi0 (computePgram's
  *                   formula is not printed; this normalisation is a reading),
  *                   best period from the first maximum (findPeriod).
+ *   supsmu_spg      the other reading of Sec. 3: one span per frequency, the
+ *                   least summed squared generalized-validation residual.
+ *   search_refine   the outlook of Sec. 6: coarse periodogram, top local
+ *                   maxima, dense grids across them, the periodogram again.
  *
- * Parity status: supsmu_sp has no value printed in the paper to pin it to; it
- * is pinned only against brute force of its own reading ("parity unpinned"
- * against the paper).
+ * Test infrastructure only: the library never calls it.
+ *
+ * Parity status: supsmu_sp and supsmu_spg have no value printed in the paper
+ * to pin them to; they are pinned only against brute force of their own
+ * readings ("parity unpinned" against the paper).
  */
 #include <math.h>
 #include <pthread.h>
