@@ -36,8 +36,6 @@
  *   search_refine   the outlook of Sec. 6: coarse periodogram, top local
  *                   maxima, dense grids across them, the periodogram again.
  *
- * Test infrastructure only: the library never calls it.
- *
  * Parity status: supsmu_sp and supsmu_spg have no value printed in the paper
  * to pin them to; they are pinned only against brute force of their own
  * readings ("parity unpinned" against the paper).
