@@ -58,6 +58,8 @@ constexpr float kNearSP = 64.f;
 constexpr float kNearLev = 1e-4f;
 constexpr float kNearSlope = 1e-4f;
 constexpr float kRefitFrac = 1.f / 128.f;  // history guard of the sliding sums
+// windows of at most this many points are initialised by direct summation
+constexpr int kDirectInit = 32;
 // SP: a point whose fit could move the power by more than kSensTau through
 // the FP32 error of its residuals (bass enhancement divides by the smallest;
 // each residual is taken to err by its slope times the rounding of X plus
@@ -813,6 +815,11 @@ __device__ void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R, A> &
     s.zero();
     // three segments of constant shift: slots before 0, inside, after n-1
     const int ea = win_lo(fr, c, h, n), eb = ea + 2 * h;
+    if (2 * h + 1 <= kDirectInit) {
+        // a short window costs less summed point by point than from prefixes
+        for (int e = ea; e <= eb; ++e) win_add<R, NCH, DIFF>(s, fr, v, e, n, o, R(1));
+        return;
+    }
 #pragma unroll 1
     for (int seg = -1; seg <= 1; ++seg) {
         int pa, pb;
