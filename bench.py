@@ -55,16 +55,19 @@ UNIT = "pt*f/s"
 #      + span choice/bass (8) + clamp/interpolation (8) + chi2 (3) = 366.
 # SP = 3 fits + 3 generalized-validation residuals (3 each) + span choice (8)
 #      + interpolation (8) + chi2 (3) = 148.
+# SPG = 3 fits + 3 generalized-validation terms + chi2 (3) = 132: one span for
+#      the whole fold, so no per-point choice or interpolation.
 OPS_PER_PTF = {"ss": 3 * 49 + 3 * 40 + 40 + 40 + 8 + 8 + 3,
-               "sp": 3 * 40 + 3 * 3 + 8 + 8 + 3}
+               "sp": 3 * 40 + 3 * 3 + 8 + 8 + 3,
+               "spg": 3 * 40 + 3 * 3 + 3}
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per full-size launch of the FP32C periodogram
 # kernels, from one ncu capture (profiles/pgram_kernel_c2_n3000.md).  They
 # apply only to the kernel sources they were taken on: bench.py reports them
 # while the hash of those sources still matches, else null.
 TRAFFIC_SOURCES = ("ssp_device.cuh", "ssp_kernels.cuh", "ssp_fold.h", "ssp_launch.h", "ssp_fp32.cu")
-TRAFFIC = {"sha256": "02f5563d70a38f767e56af45aac37e261588ce89a8b5cb44d4fe8464b6213c69",
-           "ss": 1561600, "sp": 1174528 + 15614208}
+TRAFFIC = {"sha256": "064fab7519bcd5c0dc58deae8f10978e9d83ececd2293d983211cb2e815462a9",
+           "ss": 1560576 + 0, "sp": 1728256 + 17997056}
 
 
 def traffic_per_launch(variant):
@@ -91,6 +94,9 @@ def parse():
     ap.add_argument("--duration", type=float, default=60.0, help="--serve: seconds of arrivals")
     ap.add_argument("--serve-freq", type=int, default=10_000, help="--serve: trial frequencies")
     ap.add_argument("--matrix", default="", help="comma list of configurations (c1..c4)")
+    ap.add_argument("--extras", action="store_true",
+                    help="shared-fold and search-and-refine measurements")
+    ap.add_argument("--matrix-variants", default="ss,sp", help="--matrix: comma list of ss, sp, spg")
     return ap.parse_args()
 
 
@@ -170,7 +176,7 @@ def cpu_baseline(cat, p32=None, budget_s=12.0, max_freq=4096, obj=0, variants=("
     import oracle
     t, y, dy = cat.obj(obj)
     n = t.size
-    codes = [{"ss": oracle.SS, "sp": oracle.SP}[v] for v in variants]
+    codes = [{"ss": oracle.SS, "sp": oracle.SP, "spg": oracle.SPG}[v] for v in variants]
     rng = np.random.default_rng(7)
     order = rng.permutation(cat.freq.size)
     cores = os.cpu_count() or 1
@@ -522,7 +528,7 @@ def run_matrix(args):
         put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
         fq = put(cat.freq)
         sub = cat if name != "c4" else cat.subset(list(range(min(N, 40))))
-        for v in ("ss", "sp"):
+        for v in [v for v in args.matrix_variants.split(",") if v]:
             tune = None
             if name == "c3":
                 t0 = time.perf_counter()
@@ -562,7 +568,7 @@ def run_matrix(args):
             clocks = clk.summary()
             mhz = clocks["sm_mhz"] if clocks else 1432.0
             peak = FP32_LANES_PER_SM * sms * mhz * 1e6 / 1e12
-            kname = "pgram_" + v
+            kname = "pgram_ss" if v == "ss" else "pgram_sp"   # SPG launches time as SP
             k_ms = prof32[kname][1]
             same = float(np.mean(np.argmax(p32s, axis=1) == np.argmax(p64s, axis=1)))
             big = int(np.argmax(cat.n_per_object))
@@ -588,6 +594,75 @@ def run_matrix(args):
                 ssp.ssp_autotune_clear()
 
 
+def run_extras(args):
+    """Two measurements through the host entry points, each after one warm-up
+    call: (1) objects sharing one cadence, folded and sorted once per group,
+    against the same work with jittered times; (2) search-and-refine (coarse
+    SP, then SS on 64-frequency grids around the top 3 peaks) against SS over
+    the whole coarse grid, on 2,000 sparse-catalog objects."""
+    from paper_2111_07396_gb300 import build as ssp_build
+    from paper_2111_07396_gb300 import ssp, synth
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    ssp_build.build()
+    ssp.lib()
+
+    def wall(fn):
+        fn()
+        t0 = time.perf_counter()
+        out = fn()
+        return time.perf_counter() - t0, out
+
+    shared, jit = synth.shared_cadence(), synth.shared_cadence(jitter=True)
+    for v in ("ss", "sp"):
+        with ClockSampler(0) as clk:
+            ts, (ps, _) = wall(lambda: ssp.ssp_periodogram(shared.t, shared.y, shared.dy,
+                                                           shared.n_per_object, shared.freq,
+                                                           variant=v))
+            tj, (pj, _) = wall(lambda: ssp.ssp_periodogram(jit.t, jit.y, jit.dy, jit.n_per_object,
+                                                           jit.freq, variant=v))
+        print(json.dumps({
+            "metric": "point*frequency evals/s", "unit": UNIT, "extra": "shared_fold", "variant": v,
+            "shared": {"value": shared.pt_freq / ts, "s": ts},
+            "separate": {"value": jit.pt_freq / tj, "s": tj}, "speedup": tj / ts,
+            "max_abs_diff": float(np.max(np.abs(ps - pj))), "clocks": clk.summary(),
+            "config": {"workload": "48 objects on one 3,000-point cadence, 4,000 freqs in "
+                                   "[0.01, 20); separate = times jittered by k*1e-9 d",
+                       "api": "ssp_periodogram (host arrays)", "precision": "fp32c"}}),
+            flush=True)
+
+    cat = synth.config3(n_objects=2000, n_freq=20_000)
+    step = float(cat.freq[1] - cat.freq[0])
+    with ClockSampler(0) as clk:
+        tr, (bp_r, _) = wall(lambda: ssp.ssp_search_refine(cat.t, cat.y, cat.dy, cat.n_per_object,
+                                                           cat.freq, coarse_variant="sp",
+                                                           fine_variant="ss", n_peaks=3,
+                                                           n_fine=64))
+        tf, (_, bp_f) = wall(lambda: ssp.ssp_periodogram(cat.t, cat.y, cat.dy, cat.n_per_object,
+                                                         cat.freq, variant="ss"))
+    near = np.abs(1.0 / bp_r - 1.0 / bp_f) <= step
+    shapes = np.asarray(cat.shapes)
+    truth = 1.0 / cat.periods
+    by_shape = {}
+    for sh in ("sin", "box", "noise"):
+        m = shapes == sh
+        by_shape[sh] = {"objects": int(m.sum()),
+                        "refine_matches_full_grid": float(np.mean(near[m])),
+                        "refine_finds_true_f": float(np.mean(np.abs(1.0 / bp_r[m] - truth[m]) <= step)),
+                        "full_grid_finds_true_f": float(np.mean(np.abs(1.0 / bp_f[m] - truth[m]) <= step))}
+    print(json.dumps({
+        "metric": "objects/s", "unit": "objects/s", "extra": "search_refine",
+        "refine": {"value": cat.n_per_object.size / tr, "s": tr},
+        "ss_full_grid": {"value": cat.n_per_object.size / tf, "s": tf}, "speedup": tf / tr,
+        "best_freq_within_one_step": float(np.mean(near)), "by_shape": by_shape,
+        "clocks": clk.summary(),
+        "config": {"workload": "2,000 sparse-catalog objects (n ~ logU(30, 500), 2,000 d), "
+                               "coarse grid 20,000 freqs in [0.01, 10); SP coarse, SS on 3 x 64",
+                   "api": "ssp_search_refine / ssp_periodogram (host arrays)",
+                   "precision": "fp32c"}}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -596,6 +671,8 @@ def main():
         run_serve(args)
     elif args.matrix:
         run_matrix(args)
+    elif args.extras:
+        run_extras(args)
     else:
         run_ours(args)
 

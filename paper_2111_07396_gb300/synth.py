@@ -203,6 +203,24 @@ def config5_arrivals(rate: float = 2000.0, duration: float = 60.0, n_freq: int =
     return arrivals, cat, variants
 
 
+def shared_cadence(n_objects: int = 48, n: int = 3000, n_freq: int = 4000, jitter: bool = False):
+    """Many stars on one survey field's cadence: n times ~ U(0, 1000) shared by
+    every object, sinusoids with P ~ U(0.3, 20) d and amplitude 0.2 over a
+    15-mag mean, white noise 0.05 = dy; n_freq frequencies in [0.01, 20).
+    jitter=True adds k * 1e-9 d to object k's times, so no two objects share
+    them (the same work without the shared fold)."""
+    g = _rng(6, 0)
+    t = np.sort(g.uniform(0.0, 1000.0, n))
+    objs, periods = [], []
+    for k in range(n_objects):
+        P = float(g.uniform(0.3, 20.0))
+        y = 15.0 + 0.2 * np.sin(2 * np.pi * t / P) + g.normal(0.0, 0.05, n)
+        objs.append((t + 1e-9 * k if jitter else t, y, np.full(n, 0.05)))
+        periods.append(P)
+    return _pack("shared" if not jitter else "jittered", objs, uniform_grid(0.01, 20.0, n_freq),
+                 periods, ["sinusoid"] * n_objects)
+
+
 def single_object(t, y, dy, freq, name="custom") -> Catalog:
     t = np.ascontiguousarray(t, dtype=np.float64)
     return _pack(name, [(t, np.ascontiguousarray(y, dtype=np.float64),
