@@ -96,6 +96,11 @@ def parse():
     ap.add_argument("--matrix", default="", help="comma list of configurations (c1..c4)")
     ap.add_argument("--extras", action="store_true",
                     help="shared-fold and search-and-refine measurements")
+    ap.add_argument("--subset-objects", type=int, default=0,
+                    help="--matrix: keep the first K objects of each configuration")
+    ap.add_argument("--subset-freq", type=int, default=0,
+                    help="--matrix: keep F frequencies, evenly spaced over the grid")
+    ap.add_argument("--no-oracle", action="store_true", help="--matrix: skip the oracle sample")
     ap.add_argument("--matrix-variants", default="ss,sp", help="--matrix: comma list of ss, sp, spg")
     return ap.parse_args()
 
@@ -524,6 +529,10 @@ def run_matrix(args):
     stream = torch.cuda.Stream(device=dev)
     for name in [c for c in args.matrix.split(",") if c]:
         cat = gens[name]()
+        if args.subset_objects:
+            cat = cat.subset(list(range(min(args.subset_objects, cat.n_per_object.size))))
+        if args.subset_freq and args.subset_freq < cat.freq.size:
+            cat = cat.with_freq(cat.freq[::cat.freq.size // args.subset_freq][:args.subset_freq])
         N, nf = int(cat.n_per_object.size), int(cat.freq.size)
         put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
         fq = put(cat.freq)
@@ -572,7 +581,8 @@ def run_matrix(args):
             k_ms = prof32[kname][1]
             same = float(np.mean(np.argmax(p32s, axis=1) == np.argmax(p64s, axis=1)))
             big = int(np.argmax(cat.n_per_object))
-            cpu = cpu_baseline(cat, budget_s=8.0, max_freq=512, obj=big, variants=(v,))
+            cpu = None if args.no_oracle else cpu_baseline(cat, budget_s=8.0, max_freq=512, obj=big,
+                                                           variants=(v,))
             line = {"metric": "point*frequency evals/s", "config": name, "variant": v,
                     "objects": N, "points": int(np.sum(cat.n_per_object)), "n_freq": nf,
                     "fp32c": {"value": ptf / (ms32 / 1e3), "ms": ms32,

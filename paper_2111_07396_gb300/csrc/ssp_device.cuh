@@ -87,6 +87,7 @@ struct PgramArgs {
     double alpha;
     unsigned char *slab;    // per-CTA frames when they do not fit shared memory
     size_t slab_bytes;
+    int cnt_smem;           // slab frames: sort bucket counts in shared memory
     unsigned char *near;    // [n_obj][n_freq] FP32C: decision near a threshold
     int recompute;          // FP64 kernel: only flagged (o, q), float power out
     int periodic;           // 1: periodic windows; 0: windows clamped inside the data
@@ -124,10 +125,9 @@ struct Frame {
     R *C[7];                // smoother columns
     uint32_t *tie;          // bit j: sorted points j and j+1 have the same
                             // folded phase (exact fold output, not rounded X)
-    uint32_t *key, *klo;    // phase as 64-bit fixed point, high / low word: by
-                            // original index after the fold, in sorted order
-                            // after the sort
-    uint32_t *skh, *skl;    // sort scratch: keys by bucket position
+    uint64_t *key;          // phase as 64-bit fixed point: by original index
+                            // after the fold, in sorted order after the sort
+    uint64_t *sk;           // sort scratch: keys by bucket position
     uint16_t *slot, *tmp, *perm;  // sort scratch; perm: original index of
                                   // each sorted point (n <= 65535)
     uint32_t *cnt;          // bucket counts / starts
@@ -149,7 +149,7 @@ __host__ __device__ inline size_t tie_words(int n) { return ((size_t)n + 31) / 3
 
 // Frame layout.  X, WT and Y come first; while the phases are sorted that
 // region holds the scatter scratch instead (keys by bucket position, slots
-// and scattered indices).  The sort region follows: key and klo (the fold
+// and scattered indices).  The sort region follows: the 64-bit keys (the fold
 // output by original index, then the keys in sorted order), perm, the bucket
 // counts and, for FP64, the phases by original index.  SS columns C0..C6 also
 // follow X, WT, Y and overlay the sort region, which is dead once the gather
@@ -206,14 +206,12 @@ __device__ inline Frame<R> carve_frame(unsigned char *base, int n, int variant,
     f.X = (R *)base;
     f.WT = (R *)(base + col);
     f.Y = (R *)(base + 2 * col);
-    f.skh = (uint32_t *)base;
-    f.skl = (uint32_t *)(base + a4);
+    f.sk = (uint64_t *)base;   // 8n bytes <= 2 a4
     f.slot = (uint16_t *)(base + 2 * a4);
     f.tmp = (uint16_t *)(base + 2 * a4 + a2);
     for (int k = 0; k < 7; ++k) f.C[k] = (R *)(base + xwy + k * col);
     unsigned char *s = base + xwy;
-    f.key = (uint32_t *)s;
-    f.klo = (uint32_t *)(s + a4);
+    f.key = (uint64_t *)s;     // 8n bytes <= 2 a4
     f.perm = (uint16_t *)(s + 2 * a4);
     f.cnt = (uint32_t *)(s + 2 * a4 + ap);
     f.ph = (double *)(s + 2 * a4 + ap + align16(4 * (size_t)bucket_count(n)));
@@ -427,10 +425,8 @@ __device__ inline double fold_fp64(double tt, double f)
 template <typename R>
 __device__ inline bool key_less(const Frame<R> &fr, uint32_t i, uint32_t j)
 {
-    const uint32_t ki = fr.key[i], kj = fr.key[j];
+    const uint64_t ki = fr.key[i], kj = fr.key[j];
     if (ki != kj) return ki < kj;
-    const uint32_t li = fr.klo[i], lj = fr.klo[j];
-    if (li != lj) return li < lj;
     if (sizeof(R) == 8) {
         const double a = fr.ph[i], b = fr.ph[j];
         if (a != b) return a < b;   // phases below 2^-64 apart (tiny phases only)
@@ -471,7 +467,7 @@ __device__ __noinline__ void bitonic_argsort(const Frame<R> fr, int n)
 // n/2 buckets, each bucket ranked by full key, then original index (FP64:
 // binary64 phase between equal keys, then index); buckets more crowded than
 // kBucketRankMax fall back to a bitonic sort.  On return perm holds the
-// original index of each sorted point and key/klo the sorted keys.
+// original index of each sorted point and key the sorted keys.
 template <typename R, typename A>
 __device__ void fold_and_sort(const Frame<R> &fr, int n, const Small<R, A> &sm, const double *tt,
                               double f)
@@ -490,10 +486,8 @@ __device__ void fold_and_sort(const Frame<R> &fr, int n, const Small<R, A> &sm, 
         } else {
             fx = fold_fixed64(tt[i], f);
         }
-        const uint32_t kh = (uint32_t)(fx >> 32);
-        fr.key[i] = kh;
-        fr.klo[i] = (uint32_t)fx;
-        fr.slot[i] = (uint16_t)atomicAdd(&fr.cnt[kh >> shift], 1u);
+        fr.key[i] = fx;
+        fr.slot[i] = (uint16_t)atomicAdd(&fr.cnt[(uint32_t)(fx >> 32) >> shift], 1u);
     }
     __syncthreads();
     const int crowd = block_exclusive_scan(fr.cnt, nb, sm.ired);
@@ -502,37 +496,33 @@ __device__ void fold_and_sort(const Frame<R> &fr, int n, const Small<R, A> &sm, 
         // sorted keys by way of the scatter scratch
         for (int p = tid; p < n; p += G) {
             const uint32_t i = fr.perm[p];
-            fr.skh[p] = fr.key[i];
-            fr.skl[p] = fr.klo[i];
+            fr.sk[p] = fr.key[i];
         }
         __syncthreads();
-        for (int p = tid; p < n; p += G) {
-            fr.key[p] = fr.skh[p];
-            fr.klo[p] = fr.skl[p];
-        }
+        for (int p = tid; p < n; p += G) fr.key[p] = fr.sk[p];
         __syncthreads();
         return;
     }
     // scatter index and key to the bucket's slots
     for (int i = tid; i < n; i += G) {
-        const uint32_t kh = fr.key[i];
-        const int p = (int)fr.cnt[kh >> shift] + fr.slot[i];
+        const uint64_t k = fr.key[i];
+        const int p = (int)fr.cnt[(uint32_t)(k >> 32) >> shift] + fr.slot[i];
         fr.tmp[p] = (uint16_t)i;
-        fr.skh[p] = kh;
-        fr.skl[p] = fr.klo[i];
+        fr.sk[p] = k;
     }
     __syncthreads();
     // rank within the bucket (its members sit next to each other)
     for (int p = tid; p < n; p += G) {
-        const uint32_t i = fr.tmp[p], kh = fr.skh[p], kl = fr.skl[p];
-        const uint32_t b = kh >> shift;
+        const uint32_t i = fr.tmp[p];
+        const uint64_t k = fr.sk[p];
+        const uint32_t b = (uint32_t)(k >> 32) >> shift;
         const int lo = (int)fr.cnt[b];
         const int hi = (b + 1 < (uint32_t)nb) ? (int)fr.cnt[b + 1] : n;
         int rank = 0;
         for (int q = lo; q < hi; ++q) {
-            const uint32_t qh = fr.skh[q], ql = fr.skl[q];
-            bool less = qh < kh || (qh == kh && ql < kl);
-            if (qh == kh && ql == kl) {
+            const uint64_t qk = fr.sk[q];
+            bool less = qk < k;
+            if (qk == k) {
                 const uint32_t iq = fr.tmp[q];
                 less = iq < i;
                 if (sizeof(R) == 8 && fr.ph[iq] != fr.ph[i]) less = fr.ph[iq] < fr.ph[i];
@@ -540,8 +530,7 @@ __device__ void fold_and_sort(const Frame<R> &fr, int n, const Small<R, A> &sm, 
             rank += less ? 1 : 0;
         }
         fr.perm[lo + rank] = (uint16_t)i;
-        fr.key[lo + rank] = kh;
-        fr.klo[lo + rank] = kl;
+        fr.key[lo + rank] = k;
     }
     __syncthreads();
 }
@@ -1166,7 +1155,7 @@ __device__ __noinline__ double warp_fit_fp64(const Frame<R> fr, const double *y6
         int sh;
         const int p = slot_point(e, n, sh);
         const uint32_t i = fr.perm[p];
-        const double x = (double)(((uint64_t)fr.key[p] << 32) | fr.klo[p]) * 5.421010862427522e-20 + sh;
+        const double x = (double)fr.key[p] * 5.421010862427522e-20 + sh;
         const double w = w64[i], y = y64[i], dx = x - xj;
         sw += w;
         sa += w * dx;
@@ -1265,7 +1254,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
         bool tj = false;
         if (j < n) {
             const uint32_t i = fr.perm[j];
-            const uint32_t kh = fr.key[j], kl = fr.klo[j];
+            const uint64_t kj = fr.key[j];
+            const uint32_t kh = (uint32_t)(kj >> 32);
             R x;
             if (sizeof(R) == 8) {
                 x = (R)fr.ph[i];
@@ -1276,8 +1266,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
                 if (kh >= (1u << 24)) {
                     x = (R)(__uint2float_rz(kh) * 2.3283064365386963e-10f);   // * 2^-32
                 } else {
-                    const uint64_t fx = ((uint64_t)kh << 32) | kl;
-                    x = (R)(__ull2float_rz(fx) * 5.421010862427522e-20f);    // * 2^-64
+                    x = (R)(__ull2float_rz(kj) * 5.421010862427522e-20f);    // * 2^-64
                 }
             }
             fr.X[j] = x;
@@ -1285,7 +1274,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
             fr.Y[j] = yc[i];
             if (j + 1 < n) {
                 tj = (sizeof(R) == 8) ? (fr.ph[i] == fr.ph[fr.perm[j + 1]])
-                                      : (kh == fr.key[j + 1] && kl == fr.klo[j + 1]);
+                                      : (kj == fr.key[j + 1]);
             }
         }
         const uint32_t word = __ballot_sync(0xffffffffu, tj);
@@ -1294,7 +1283,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
     }
     ties = __syncthreads_or(tie) != 0;
     flat = (sizeof(R) == 8) ? !(fr.ph[fr.perm[n - 1]] > fr.ph[fr.perm[0]])
-                            : (fr.key[n - 1] == fr.key[0] && fr.klo[n - 1] == fr.klo[0]);
+                            : (fr.key[n - 1] == fr.key[0]);
     if (tid == 0) {   // for the group's later objects
         sm.flags[0] = ties;
         sm.flags[1] = flat;
@@ -1434,8 +1423,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
         const double *w64 = a.wv64 ? a.wv64 + base : nullptr;
         double vsm64 = 0.0;
         if (sizeof(R) == 4 && y64) {
-            const double xi = (double)(((uint64_t)fr.key[qi] << 32) | fr.klo[qi]) * 5.421010862427522e-20;
-            const double xq = (double)(((uint64_t)fr.key[qj] << 32) | fr.klo[qj]) * 5.421010862427522e-20;
+            const double xi = (double)fr.key[qi] * 5.421010862427522e-20;
+            const double xq = (double)fr.key[qj] * 5.421010862427522e-20;
             vsm64 = 1.0e-6 * (xq - xi) * (xq - xi);
         }
         // a point whose bound E on its chi2 change exceeds this is refitted
@@ -1515,7 +1504,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
                 todo &= todo - 1;
                 const int je = __shfl_sync(0xffffffffu, j, src);
                 const uint32_t pe = fr.perm[je];
-                const double xe = (double)(((uint64_t)fr.key[je] << 32) | fr.klo[je]) * 5.421010862427522e-20;
+                const double xe = (double)fr.key[je] * 5.421010862427522e-20;
                 const double t0 = warp_fit_fp64<R>(fr, y64, w64, je, h0, n, vsm64, xe);
                 const double t1 = warp_fit_fp64<R>(fr, y64, w64, je, h1, n, vsm64, xe);
                 const double t2 = warp_fit_fp64<R>(fr, y64, w64, je, h2, n, vsm64, xe);
@@ -1713,6 +1702,9 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
         const int n = (int)(a.off[o + 1] - a.off[o]);
         Frame<R> fr = carve_frame<R>(big, n, VARIANT, SHARED);
         fr.per = PER;
+        // a frame in global memory still counts its sort buckets in shared
+        // memory: the counting pass is one atomic per point
+        if (GMEM && a.cnt_smem) fr.cnt = (uint32_t *)(smem + align16(small_bytes<A>(G, VARIANT)));
         for (int q = item.y; q < item.z; ++q) {
             bool sorted = false;
             for (int k = 0; k < m; ++k) {
