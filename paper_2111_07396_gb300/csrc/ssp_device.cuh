@@ -119,9 +119,23 @@ __host__ __device__ inline int pow2_at_least(int n)
     return p;
 }
 
+// (phase, weight) of one point, read and written together
+template <typename R> struct Vec2;
+template <> struct Vec2<float> { typedef float2 T; };
+template <> struct Vec2<double> { typedef double2 T; };
+template <typename R>
+__device__ inline typename Vec2<R>::T vec2(R a, R b)
+{
+    typename Vec2<R>::T v;
+    v.x = a;
+    v.y = b;
+    return v;
+}
+
 template <typename R>
 struct Frame {
-    R *X, *WT, *Y;          // sorted phase, weight, centred magnitude
+    typename Vec2<R>::T *XW;  // sorted phase (x) and weight (y)
+    R *Y;                     // centred magnitude
     R *C[7];                // smoother columns
     uint32_t *tie;          // bit j: sorted points j and j+1 have the same
                             // folded phase (exact fold output, not rounded X)
@@ -147,12 +161,12 @@ __device__ inline int win_lo(const Frame<R> &fr, int j, int h, int n)
 
 __host__ __device__ inline size_t tie_words(int n) { return ((size_t)n + 31) / 32; }
 
-// Frame layout.  X, WT and Y come first; while the phases are sorted that
-// region holds the scatter scratch instead (keys by bucket position, slots
-// and scattered indices).  The sort region follows: the 64-bit keys (the fold
+// Frame layout.  XW (phase and weight, interleaved) and Y come first; while
+// the phases are sorted that region holds the scatter scratch instead (keys
+// by bucket position, slots and scattered indices).  The sort region follows: the 64-bit keys (the fold
 // output by original index, then the keys in sorted order), perm, the bucket
 // counts and, for FP64, the phases by original index.  SS columns C0..C6 also
-// follow X, WT, Y and overlay the sort region, which is dead once the gather
+// follow XW, Y and overlay the sort region, which is dead once the gather
 // has run; SP keeps the sorted keys for its exact refits.  The tie bitmask
 // follows whichever region ends later, because the gather writes it while it
 // still reads the sort's output.
@@ -181,7 +195,7 @@ __host__ __device__ inline size_t tie_offset(int n, int ncols)
     return cols > s ? cols : s;
 }
 
-// columns a variant keeps: SS uses X, WT, Y and C0..C6; SP only X, WT, Y
+// columns a variant keeps: SS uses XW (two columns), Y and C0..C6; SP only XW, Y
 __host__ __device__ inline int frame_cols(int variant) { return variant == VAR_SS ? 10 : 3; }
 
 // keep_perm: objects with identical times share one sort (their frame keeps
@@ -203,8 +217,7 @@ __device__ inline Frame<R> carve_frame(unsigned char *base, int n, int variant,
     const size_t col = align16(sizeof(R) * (size_t)n), xwy = xwy_bytes<R>(n);
     const size_t a4 = align16(4 * (size_t)n), a2 = align16(2 * (size_t)n);
     const size_t ap = align16(2 * (size_t)pow2_at_least(n));
-    f.X = (R *)base;
-    f.WT = (R *)(base + col);
+    f.XW = (typename Vec2<R>::T *)base;   // 2 n sizeof(R) bytes <= 2 col
     f.Y = (R *)(base + 2 * col);
     f.sk = (uint64_t *)base;   // 8n bytes <= 2 a4
     f.slot = (uint16_t *)(base + 2 * a4);
@@ -376,12 +389,32 @@ __device__ inline int block_exclusive_scan(uint32_t *cnt, int nb, int *ired)
 {
     const int G = blockDim.x, tid = threadIdx.x;
     const int per = (nb + G - 1) / G;
-    const int a = min(nb, tid * per), b = min(nb, a + per);
-    uint32_t sum = 0, mx = 0;
-    for (int i = a; i < b; ++i) {
-        uint32_t c = cnt[i];
-        sum += c;
-        mx = c > mx ? c : mx;
+    const int a = min(nb, tid * per), len = min(nb, a + per) - a;
+    // Blocks of 16 or more counts: each thread walks its block starting at
+    // offset sk, so that the lanes of a warp, whose blocks lie per words
+    // apart, read 32 different banks; head is the sum of the counts before
+    // sk.  (nb and G are powers of two, so a non-empty block holds exactly
+    // per counts; any other shape walks in order.)  Shorter blocks conflict
+    // at most 8 ways and walk in order: there the rotation costs more than
+    // it saves.
+    const int lg = __ffs(per) - 1;   // log2(per) when per is a power of two
+    const int sk = (per >= 16 && len == per && (per & (per - 1)) == 0)
+                       ? (tid >> (lg >= 5 ? 0 : 5 - lg)) & (per - 1) : 0;
+    uint32_t sum = 0, mx = 0, head = 0;
+    if (sk == 0) {
+        for (int i = a; i < a + len; ++i) {
+            const uint32_t c = cnt[i];
+            sum += c;
+            mx = c > mx ? c : mx;
+        }
+    } else {
+        for (int k = 0; k < len; ++k) {
+            const int r = k + sk < len ? k + sk : k + sk - len;
+            const uint32_t c = cnt[a + r];
+            sum += c;
+            mx = c > mx ? c : mx;
+            head += r < sk ? c : 0u;
+        }
     }
     // inclusive warp scan of per-thread sums
     const int lane = tid & 31, warp = tid >> 5, nw = (G + 31) >> 5;
@@ -399,11 +432,25 @@ __device__ inline int block_exclusive_scan(uint32_t *cnt, int nb, int *ired)
     for (int k = 0; k < warp; ++k) wbase += (uint32_t)ired[k];
     int gmax = 0;
     for (int k = 0; k < nw; ++k) gmax = max(gmax, ired[16 + k]);
-    uint32_t run = wbase + inc - sum;
-    for (int i = a; i < b; ++i) {
-        uint32_t c = cnt[i];
-        cnt[i] = run;
-        run += c;
+    const uint32_t start = wbase + inc - sum;   // exclusive prefix at a
+    uint32_t run = start + head;                 // ... and at a + sk
+    if (sk == 0) {
+        for (int i = a; i < a + len; ++i) {
+            const uint32_t c = cnt[i];
+            cnt[i] = run;
+            run += c;
+        }
+    } else {
+        for (int k = 0; k < len; ++k) {
+            int r = k + sk;
+            if (r >= len) {
+                r -= len;
+                if (r == 0) run = start;
+            }
+            const uint32_t c = cnt[a + r];
+            cnt[a + r] = run;
+            run += c;
+        }
     }
     __syncthreads();
     return gmax;
@@ -602,8 +649,9 @@ __device__ inline void win_add(Win<R, NCH> &s, const Frame<R> &fr, const R *cons
 {
     R shf;
     const int p = slot_point_r<R>(e, n, shf);
-    const R dx = (fr.X[p] - o) + shf;
-    const R w = sign * fr.WT[p];
+    const typename Vec2<R>::T xw = fr.XW[p];
+    const R dx = (xw.x - o) + shf;
+    const R w = sign * xw.y;
     const R wdx = w * dx;
     s.W += w;
     s.A += wdx;
@@ -683,7 +731,8 @@ __device__ void build_xy_prefix(const Frame<R> &fr, const Small<R, A> &sm, const
     const int L = blockDim.x + 1;
     R w_ = R(0), a_ = R(0), b_ = R(0), sc = R(0), sd = R(0);
     for (int j = c0; j < c1; ++j) {
-        const R w = fr.WT[j], d = fr.X[j] - o, wv = w * vy[j];
+        const typename Vec2<R>::T xw = fr.XW[j];
+        const R w = xw.y, d = xw.x - o, wv = w * vy[j];
         w_ += w;
         a_ += w * d;
         b_ += w * d * d;
@@ -718,7 +767,8 @@ __device__ void build_channel_prefix(const Frame<R> &fr, const Small<R, A> &sm, 
 #pragma unroll
     for (int ch = 0; ch < NCH; ++ch) sc[ch] = sd[ch] = R(0);
     for (int j = c0; j < c1; ++j) {
-        const R w = fr.WT[j], d = fr.X[j] - o;
+        const typename Vec2<R>::T xw = fr.XW[j];
+        const R w = xw.y, d = xw.x - o;
         R val[NCH];
 #pragma unroll
         for (int ch = 0; ch < NS; ++ch) {
@@ -775,8 +825,9 @@ template <typename R, int NCH, bool DIFF>
 __device__ inline void win_add_slot(Win<R, NCH> &s, const Frame<R> &fr, const R *const *v, int p,
                                     R sh, R o)
 {
-    const R dx = (fr.X[p] - o) + sh;
-    const R w = fr.WT[p];
+    const typename Vec2<R>::T xw = fr.XW[p];
+    const R dx = (xw.x - o) + sh;
+    const R w = xw.y;
     const R wdx = w * dx;
     s.W += w;
     s.A += wdx;
@@ -937,7 +988,8 @@ __device__ __noinline__ Fit<R, NCH> win_refit_fp64(const Frame<R> fr, const Chan
     for (int e = lo; e <= lo + 2 * h; ++e) {
         int sh;
         int p = slot_point(e, n, sh);
-        double w = (double)fr.WT[p], x = (double)fr.X[p] + sh;
+        const typename Vec2<R>::T xw = fr.XW[p];
+        double w = (double)xw.y, x = (double)xw.x + sh;
         sw += w;
         swx += w * x;
 #pragma unroll
@@ -950,13 +1002,14 @@ __device__ __noinline__ Fit<R, NCH> win_refit_fp64(const Frame<R> fr, const Chan
     for (int e = lo; e <= lo + 2 * h; ++e) {
         int sh;
         int p = slot_point(e, n, sh);
-        double w = (double)fr.WT[p], dx = (double)fr.X[p] + sh - xm;
+        const typename Vec2<R>::T xw = fr.XW[p];
+        double w = (double)xw.y, dx = (double)xw.x + sh - xm;
         sxx += w * dx * dx;
 #pragma unroll
         for (int c = 0; c < NCH; ++c) sxv[c] += w * dx * (double)chan<R, NCH, DIFF>(v, c, p);
     }
     const bool slope = sxx > vsmlsq;
-    const double dxj = (double)fr.X[j] - xm;
+    const double dxj = (double)fr.XW[j].x - xm;
     f.rW = (R)(1.0 / sw);
     f.slope = slope;
     f.rS = slope ? (R)(1.0 / sxx) : R(0);
@@ -975,7 +1028,7 @@ __device__ inline void win_fit_checked(Fit<R, NCH> &f, const Win<R, NCH> &s, con
                                        const R *const *v, int j, int h, int n, R o, R vsmlsq,
                                        bool &near, R refit_frac)
 {
-    win_fit<R, NCH>(f, s, fr.X[j] - o, vsmlsq);
+    win_fit<R, NCH>(f, s, fr.XW[j].x - o, vsmlsq);
     if (sizeof(R) == 4) {
         const R sxx = f.sxx;
         if (sxx < s.hiB * refit_frac && s.hiB > R(0)) {
@@ -1123,7 +1176,7 @@ __device__ inline void run_push(RunAvg<R, K> &ra, const Frame<R> &fr, int j, boo
         emit(j, vals);
         return;
     }
-    const R wj = fr.WT[j];
+    const R wj = fr.XW[j].y;
     ra.w += wj;
 #pragma unroll
     for (int k = 0; k < K; ++k) ra.s[k] += wj * vals[k];
@@ -1202,7 +1255,7 @@ __device__ inline FreqResult fixed_span_pass(const PgramArgs &a, const Frame<R> 
         ra.reset(c0);
         auto emit = [&](int i, const R (&v)[1]) {
             const R d = fr.Y[i] - v[0];
-            chi2.add(fr.WT[i] * d * d);
+            chi2.add(fr.XW[i].y * d * d);
         };
         for (int j = c0; j < c1; ++j) {
             Fit<R, 1> f1;
@@ -1233,7 +1286,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
         // of this object's identical times; only y and w are its own
         for (int j = tid; j < n; j += G) {
             const uint32_t i = fr.perm[j];
-            fr.WT[j] = wv[i];
+            fr.XW[j].y = wv[i];
             fr.Y[j] = yc[i];
         }
         __syncthreads();
@@ -1269,8 +1322,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
                     x = (R)(__ull2float_rz(kj) * 5.421010862427522e-20f);    // * 2^-64
                 }
             }
-            fr.X[j] = x;
-            fr.WT[j] = wv[i];
+            fr.XW[j] = vec2<R>(x, wv[i]);
             fr.Y[j] = yc[i];
             if (j + 1 < n) {
                 tj = (sizeof(R) == 8) ? (fr.ph[i] == fr.ph[fr.perm[j + 1]])
@@ -1294,8 +1346,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
     if (flat) {
         double sw = 0.0, swy = 0.0;
         for (int j = tid; j < n; j += G) {
-            sw += (double)fr.WT[j];
-            swy += (double)fr.WT[j] * (double)fr.Y[j];
+            sw += (double)fr.XW[j].y;
+            swy += (double)fr.XW[j].y * (double)fr.Y[j];
         }
         sw = block_sum(sw, sm.red);
         swy = block_sum(swy, sm.red);
@@ -1303,13 +1355,13 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
         double c2 = 0.0;
         for (int j = tid; j < n; j += G) {
             const double d = (double)(fr.Y[j] - m);
-            c2 += (double)fr.WT[j] * d * d;
+            c2 += (double)fr.XW[j].y * d * d;
         }
         return FreqResult{block_sum(c2, sm.red), false};
     }
 
     const int qi = n / 4 - 1, qj = 3 * (qi + 1) - 1;
-    const R scale = fr.X[qj] - fr.X[qi];
+    const R scale = fr.XW[qj].x - fr.XW[qi].x;
     const R vsmlsq = (R)1.0e-6 * scale * scale;
     const int h0 = half_width(n, a.spans[0]);
     const int h1 = half_width(n, a.spans[1]);
@@ -1327,7 +1379,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
     }
     __syncthreads();
     const int c0 = sm.cs[tid], c1 = sm.cs[tid + 1];
-    const R o = (c0 < c1) ? fr.X[c0] : R(0);
+    const R o = (c0 < c1) ? fr.XW[c0].x : R(0);
 
     KSum<R> chi2;
     bool near = false;
@@ -1359,7 +1411,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const R d = fr.Y[i] - v[k];
-                    xs[k].add(fr.WT[i] * d * d);
+                    xs[k].add(fr.XW[i].y * d * d);
                 }
             };
             for (int j = c0; j < c1; ++j) {
@@ -1367,7 +1419,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
                 win_fit_checked<R, 1>(f0, w0, fr, vy, j, h0, n, o, vsmlsq, near, rf);
                 win_fit_checked<R, 1>(f1, w1, fr, vy, j, h1, n, o, vsmlsq, near, rf);
                 win_fit_checked<R, 1>(f2, w2, fr, vy, j, h2, n, o, vsmlsq, near, rf);
-                const R yj = fr.Y[j], wj = fr.WT[j];
+                const R yj = fr.Y[j], wj = fr.XW[j].y;
                 const R g0 = fabs(yj - f0.s[0]) * (f0.slope ? gl0 : gc0);
                 const R g1 = fabs(yj - f1.s[0]) * (f1.slope ? gl1 : gc1);
                 const R g2 = fabs(yj - f2.s[0]) * (f2.slope ? gl2 : gc2);
@@ -1434,7 +1486,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
         ra.reset(c0);
         auto emit = [&](int i, const R (&v)[1]) {
             const R d = fr.Y[i] - v[0];
-            chi2.add(fr.WT[i] * d * d);
+            chi2.add(fr.XW[i].y * d * d);
         };
         for (int k = 0; k < kmax; ++k) {
             const bool act = k < len;
@@ -1473,7 +1525,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
                     if (fabs(g0 - g1) <= (R)a.near_sp * (R)1.1920929e-7 * fmax(scale, ymax)) {
                         const R rs = fmax(fmax(s0, s1), s2) - fmin(fmin(s0, s1), s2);
                         const bool in_run = ties && (tie_next(fr, j) || (j > 0 && tie_next(fr, j - 1)));
-                        contested = in_run || fr.WT[j] * rs * (R(2) * fabs(yj - val[0]) + rs) > sens_lim;
+                        contested = in_run || fr.XW[j].y * rs * (R(2) * fabs(yj - val[0]) + rs) > sens_lim;
                     }
                     // bound on the power change from the FP32 error of the
                     // residuals through bass enhancement and interpolation:
@@ -1492,7 +1544,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
                         const R sp_ = sp;
                         const R dvds = (sp_ - K.s1 < R(0)) ? fabs(s0 - s1) * (-K.inv01)
                                                            : fabs(s2 - s1) * K.inv21;
-                        const R E = R(2) * fr.WT[j] * fabs(yj - val[0]) *
+                        const R E = R(2) * fr.XW[j].y * fabs(yj - val[0]) *
                                     ((K.s2 - sk) * dvds * tmp * (ge / gm + we / g2));
                         if (E > sens_lim) contested = true;
                     }
@@ -1559,7 +1611,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
                 win_fit_checked<R, 1>(f0, w0, fr, vy, j, h0, n, o, vsmlsq, near, rf);
                 win_fit_checked<R, 1>(f1, w1, fr, vy, j, h1, n, o, vsmlsq, near, rf);
                 win_fit_checked<R, 1>(f2, w2, fr, vy, j, h2, n, o, vsmlsq, near, rf);
-                const R yj = fr.Y[j], wj = fr.WT[j];
+                const R yj = fr.Y[j], wj = fr.XW[j].y;
                 const R d0 = R(1) - wj * (f0.rW + f0.dxj * f0.dxj * f0.rS);
                 const R d1 = R(1) - wj * (f1.rW + f1.dxj * f1.dxj * f1.rS);
                 const R d2 = R(1) - wj * (f2.rW + f2.dxj * f2.dxj * f2.rS);
@@ -1656,7 +1708,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
             ra.reset(c0);
             auto emit = [&](int i, const R (&v)[1]) {
                 const R d = fr.Y[i] - v[0];
-                chi2.add(fr.WT[i] * d * d);
+                chi2.add(fr.XW[i].y * d * d);
             };
             for (int j = c0; j < c1; ++j) {
                 Fit<R, 1> f0;
