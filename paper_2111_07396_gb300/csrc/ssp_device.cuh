@@ -1193,41 +1193,68 @@ __device__ inline void run_push(RunAvg<R, K> &ra, const Frame<R> &fr, int j, boo
 }
 
 
-// Binary64 line fit of window [j - h, j + h] at centre j, summed by the 32
+// Binary64 line fits at centre j of the three span windows, summed by the 32
 // lanes of a warp: exact phases (the sorted 64-bit fixed-point keys) and
-// binary64 magnitudes and weights read through perm.
-// Every lane returns the fit; all lanes of the warp must call it together.
+// binary64 magnitudes and weights read through perm.  The windows share their
+// centre and nest (h0 <= h1 <= h2, periodic or clamped), so each point is
+// loaded and summed once: into the tweeter window, or the ring that the
+// midrange window adds around it, or the woofer's ring around that (one walk
+// each); the midrange and woofer sums are then the running totals.
+// Every lane returns the fits; all lanes of the warp must call it together.
+struct Fit3 {
+    double s[3];
+};
+// Adds the slots [ea, ea + na) and [eb, eb + nb) (a window, or the ring that
+// a wider window adds around a narrower one) to acc, one pass for both parts.
 template <typename R>
-__device__ __noinline__ double warp_fit_fp64(const Frame<R> fr, const double *y64, const double *w64, int j,
-                                int h, int n, double vsmlsq64, double xj)
+__device__ inline void warp_sum_ring(const Frame<R> &fr, const double *y64, const double *w64,
+                                     int ea, int na, int eb, int nb, int n, double xj,
+                                     double (&acc)[5])
 {
-    const int lane = threadIdx.x & 31;
-    double sw = 0.0, sa = 0.0, sb = 0.0, sc = 0.0, sd = 0.0;
-    const int lo = win_lo(fr, j, h, n);
-    for (int e = lo + lane; e <= lo + 2 * h; e += 32) {
+    for (int v = (int)(threadIdx.x & 31); v < na + nb; v += 32) {
+        const int e = v < na ? ea + v : eb + (v - na);
         int sh;
         const int p = slot_point(e, n, sh);
         const uint32_t i = fr.perm[p];
         const double x = (double)fr.key[p] * 5.421010862427522e-20 + sh;
         const double w = w64[i], y = y64[i], dx = x - xj;
-        sw += w;
-        sa += w * dx;
-        sb += w * dx * dx;
-        sc += w * y;
-        sd += w * dx * y;
+        acc[0] += w;
+        acc[1] += w * dx;
+        acc[2] += w * dx * dx;
+        acc[3] += w * y;
+        acc[4] += w * dx * y;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        sw += __shfl_xor_sync(0xffffffffu, sw, o);
-        sa += __shfl_xor_sync(0xffffffffu, sa, o);
-        sb += __shfl_xor_sync(0xffffffffu, sb, o);
-        sc += __shfl_xor_sync(0xffffffffu, sc, o);
-        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+}
+template <typename R>
+__device__ __noinline__ Fit3 warp_fit3_fp64(const Frame<R> fr, const double *y64, const double *w64,
+                                            int j, int h0, int h1, int h2, int n, double vsmlsq64,
+                                            double xj)
+{
+    const int lo0 = win_lo(fr, j, h0, n), lo1 = win_lo(fr, j, h1, n), lo2 = win_lo(fr, j, h2, n);
+    const int hi0 = lo0 + 2 * h0, hi1 = lo1 + 2 * h1, hi2 = lo2 + 2 * h2;
+    double t[3][5];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) t[k][q] = 0.0;
+    warp_sum_ring(fr, y64, w64, lo0, hi0 - lo0 + 1, 0, 0, n, xj, t[0]);
+    warp_sum_ring(fr, y64, w64, lo1, lo0 - lo1, hi0 + 1, hi1 - hi0, n, xj, t[1]);
+    warp_sum_ring(fr, y64, w64, lo2, lo1 - lo2, hi1 + 1, hi2 - hi1, n, xj, t[2]);
+    Fit3 f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            for (int o = 16; o > 0; o >>= 1) t[k][q] += __shfl_xor_sync(0xffffffffu, t[k][q], o);
+            if (k > 0) t[k][q] += t[k - 1][q];   // ring + the window inside it
+        }
+        const double xb = t[k][1] / t[k][0];   // xbar - x_j
+        const double sxx = t[k][2] - xb * t[k][1];
+        const double sxv = t[k][4] - xb * t[k][3];
+        const double b = sxx > vsmlsq64 ? sxv / sxx : 0.0;
+        f.s[k] = t[k][3] / t[k][0] + b * (0.0 - xb);
     }
-    const double xb = sa / sw;              // xbar - x_j
-    const double sxx = sb - xb * sa;
-    const double sxv = sd - xb * sc;
-    const double a = sxx > vsmlsq64 ? sxv / sxx : 0.0;
-    return sc / sw + a * (0.0 - xb);
+    return f;
 }
 
 struct FreqResult {
@@ -1557,9 +1584,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
                 const int je = __shfl_sync(0xffffffffu, j, src);
                 const uint32_t pe = fr.perm[je];
                 const double xe = (double)fr.key[je] * 5.421010862427522e-20;
-                const double t0 = warp_fit_fp64<R>(fr, y64, w64, je, h0, n, vsm64, xe);
-                const double t1 = warp_fit_fp64<R>(fr, y64, w64, je, h1, n, vsm64, xe);
-                const double t2 = warp_fit_fp64<R>(fr, y64, w64, je, h2, n, vsm64, xe);
+                const Fit3 t = warp_fit3_fp64<R>(fr, y64, w64, je, h0, h1, h2, n, vsm64, xe);
+                const double t0 = t.s[0], t1 = t.s[1], t2 = t.s[2];
                 if (lane == src) {
                     // the choice and the fit in binary64 from exact inputs
                     const double ye = y64[pe];
