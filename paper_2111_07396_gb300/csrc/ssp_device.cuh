@@ -1193,68 +1193,77 @@ __device__ inline void run_push(RunAvg<R, K> &ra, const Frame<R> &fr, int j, boo
 }
 
 
-// Binary64 line fits at centre j of the three span windows, summed by the 32
-// lanes of a warp: exact phases (the sorted 64-bit fixed-point keys) and
-// binary64 magnitudes and weights read through perm.  The windows share their
-// centre and nest (h0 <= h1 <= h2, periodic or clamped), so each point is
-// loaded and summed once: into the tweeter window, or the ring that the
-// midrange window adds around it, or the woofer's ring around that (one walk
-// each); the midrange and woofer sums are then the running totals.
-// Every lane returns the fits; all lanes of the warp must call it together.
-struct Fit3 {
-    double s[3];
-};
-// Adds the slots [ea, ea + na) and [eb, eb + nb) (a window, or the ring that
-// a wider window adds around a narrower one) to acc, one pass for both parts.
+// Settles one contested SP centre je in binary64: the line fits of its three
+// span windows from exact phases (the sorted 64-bit fixed-point keys) and
+// binary64 magnitudes and weights read through perm, then the span choice and
+// interpolation.  The windows share their centre and nest (h0 <= h1 <= h2,
+// periodic or clamped), so each point is loaded and summed once: into the
+// tweeter window, or the ring the midrange window adds around it, or the
+// woofer's ring around that (each ring's two segments in one walk); the wider
+// windows' sums are running totals.  sl: bit k set when span k's fit kept its
+// slope, which picks the validation factor as in the FP32 choice.
+// The code runs rarely, from a cold instruction cache, so it is out of line and
+// written once per step (only the walk is unrolled).  All lanes of the warp call it
+// together with the same centre; every lane returns the smooth.
 template <typename R>
-__device__ inline void warp_sum_ring(const Frame<R> &fr, const double *y64, const double *w64,
-                                     int ea, int na, int eb, int nb, int n, double xj,
-                                     double (&acc)[5])
+__device__ __noinline__ double sp_settle_fp64(const Frame<R> fr, const double *y64, const double *w64,
+                                              int je, int h0, int h1, int h2, int n, double vsmlsq64,
+                                              int sl, bool lim0, bool lim1, const double *spans,
+                                              double alpha)
 {
-    for (int v = (int)(threadIdx.x & 31); v < na + nb; v += 32) {
-        const int e = v < na ? ea + v : eb + (v - na);
-        int sh;
-        const int p = slot_point(e, n, sh);
-        const uint32_t i = fr.perm[p];
-        const double x = (double)fr.key[p] * 5.421010862427522e-20 + sh;
-        const double w = w64[i], y = y64[i], dx = x - xj;
-        acc[0] += w;
-        acc[1] += w * dx;
-        acc[2] += w * dx * dx;
-        acc[3] += w * y;
-        acc[4] += w * dx * y;
-    }
-}
-template <typename R>
-__device__ __noinline__ Fit3 warp_fit3_fp64(const Frame<R> fr, const double *y64, const double *w64,
-                                            int j, int h0, int h1, int h2, int n, double vsmlsq64,
-                                            double xj)
-{
-    const int lo0 = win_lo(fr, j, h0, n), lo1 = win_lo(fr, j, h1, n), lo2 = win_lo(fr, j, h2, n);
-    const int hi0 = lo0 + 2 * h0, hi1 = lo1 + 2 * h1, hi2 = lo2 + 2 * h2;
-    double t[3][5];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int q = 0; q < 5; ++q) t[k][q] = 0.0;
-    warp_sum_ring(fr, y64, w64, lo0, hi0 - lo0 + 1, 0, 0, n, xj, t[0]);
-    warp_sum_ring(fr, y64, w64, lo1, lo0 - lo1, hi0 + 1, hi1 - hi0, n, xj, t[1]);
-    warp_sum_ring(fr, y64, w64, lo2, lo1 - lo2, hi1 + 1, hi2 - hi1, n, xj, t[2]);
-    Fit3 f;
-#pragma unroll
+    const double xj = (double)fr.key[je] * 5.421010862427522e-20;
+    const int lo[3] = {win_lo(fr, je, h0, n), win_lo(fr, je, h1, n), win_lo(fr, je, h2, n)};
+    const int hw[3] = {h0, h1, h2};
+    double sw = 0.0, sa = 0.0, sb = 0.0, sc = 0.0, sd = 0.0, fit[3];
+#pragma unroll 1
     for (int k = 0; k < 3; ++k) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            for (int o = 16; o > 0; o >>= 1) t[k][q] += __shfl_xor_sync(0xffffffffu, t[k][q], o);
-            if (k > 0) t[k][q] += t[k - 1][q];   // ring + the window inside it
+        const int hi = lo[k] + 2 * hw[k];
+        // slots [ea, ea + na) and [eb, eb + nb): window 0, or ring k
+        const int ea = lo[k], na = k ? lo[k - 1] - lo[k] : 2 * hw[0] + 1;
+        const int eb = k ? lo[k - 1] + 2 * hw[k - 1] + 1 : 0, nb = k ? hi - (eb - 1) : 0;
+        double aw = 0.0, aa = 0.0, ab = 0.0, ac = 0.0, ad = 0.0;
+#pragma unroll 4   // a few loads in flight per lane
+        for (int v = (int)(threadIdx.x & 31); v < na + nb; v += 32) {
+            const int e = v < na ? ea + v : eb + (v - na);
+            int sh;
+            const int p = slot_point(e, n, sh);
+            const uint32_t i = fr.perm[p];
+            const double x = (double)fr.key[p] * 5.421010862427522e-20 + sh;
+            const double w = w64[i], y = y64[i], dx = x - xj;
+            aw += w;
+            aa += w * dx;
+            ab += w * dx * dx;
+            ac += w * y;
+            ad += w * dx * y;
         }
-        const double xb = t[k][1] / t[k][0];   // xbar - x_j
-        const double sxx = t[k][2] - xb * t[k][1];
-        const double sxv = t[k][4] - xb * t[k][3];
+        for (int o = 16; o > 0; o >>= 1) {
+            aw += __shfl_xor_sync(0xffffffffu, aw, o);
+            aa += __shfl_xor_sync(0xffffffffu, aa, o);
+            ab += __shfl_xor_sync(0xffffffffu, ab, o);
+            ac += __shfl_xor_sync(0xffffffffu, ac, o);
+            ad += __shfl_xor_sync(0xffffffffu, ad, o);
+        }
+        sw += aw;
+        sa += aa;
+        sb += ab;
+        sc += ac;
+        sd += ad;
+        const double xb = sa / sw;   // xbar - x_j
+        const double sxx = sb - xb * sa;
+        const double sxv = sd - xb * sc;
         const double b = sxx > vsmlsq64 ? sxv / sxx : 0.0;
-        f.s[k] = t[k][3] / t[k][0] + b * (0.0 - xb);
+        fit[k] = sc / sw + b * (0.0 - xb);
     }
-    return f;
+    const double ye = y64[fr.perm[je]];
+    double e[3];
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+        const double d = 1.0 - (((sl >> k) & 1) ? 2.0 : 1.0) / (double)(2 * hw[k] + 1);
+        e[k] = fabs(ye - fit[k]) / d;
+    }
+    const SpanK<double> K64 = span_consts<double>(spans, alpha);
+    const double sp = choose_span<double>(K64, e[0], e[1], e[2], e[2], K64.s2, lim0, lim1);
+    return interpolate_span<double>(K64, sp, fit[0], fit[1], fit[2]);
 }
 
 struct FreqResult {
@@ -1582,22 +1591,11 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
                 const int src = __ffs(todo) - 1;
                 todo &= todo - 1;
                 const int je = __shfl_sync(0xffffffffu, j, src);
-                const uint32_t pe = fr.perm[je];
-                const double xe = (double)fr.key[je] * 5.421010862427522e-20;
-                const Fit3 t = warp_fit3_fp64<R>(fr, y64, w64, je, h0, h1, h2, n, vsm64, xe);
-                const double t0 = t.s[0], t1 = t.s[1], t2 = t.s[2];
-                if (lane == src) {
-                    // the choice and the fit in binary64 from exact inputs
-                    const double ye = y64[pe];
-                    const double d0 = 1.0 - (sl0 ? 2.0 : 1.0) / (double)m0;
-                    const double d1 = 1.0 - (sl1 ? 2.0 : 1.0) / (double)m1;
-                    const double d2 = 1.0 - (sl2 ? 2.0 : 1.0) / (double)m2;
-                    const double e0 = fabs(ye - t0) / d0, e1 = fabs(ye - t1) / d1;
-                    const double e2 = fabs(ye - t2) / d2;
-                    const SpanK<double> K64 = span_consts<double>(a.spans, a.alpha);
-                    const double sp = choose_span<double>(K64, e0, e1, e2, e2, K64.s2, lim0, lim1);
-                    val[0] = (R)interpolate_span<double>(K64, sp, t0, t1, t2);
-                }
+                const int sl = __shfl_sync(0xffffffffu, (sl0 ? 1 : 0) | (sl1 ? 2 : 0) | (sl2 ? 4 : 0),
+                                           src);
+                const double v = sp_settle_fp64<R>(fr, y64, w64, je, h0, h1, h2, n, vsm64, sl, lim0,
+                                                   lim1, a.spans, a.alpha);
+                if (lane == src) val[0] = (R)v;
             }
             if (act) {
                 run_push<R, 1>(ra, fr, j, ties, val, emit);
