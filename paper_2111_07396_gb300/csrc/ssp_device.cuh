@@ -151,12 +151,16 @@ struct Frame {
 
 // first slot of the 2h+1-point window of centre j: j - h with periodic
 // wrap, else the window slid to lie inside the data (Listing 1 iper = 1)
+__device__ inline int win_lo_mode(int per, int j, int h, int n)
+{
+    if (per) return j - h;
+    const int lo = j - h;
+    return lo < 0 ? 0 : (lo > n - 1 - 2 * h ? n - 1 - 2 * h : lo);
+}
 template <typename R>
 __device__ inline int win_lo(const Frame<R> &fr, int j, int h, int n)
 {
-    if (fr.per) return j - h;
-    const int lo = j - h;
-    return lo < 0 ? 0 : (lo > n - 1 - 2 * h ? n - 1 - 2 * h : lo);
+    return win_lo_mode(fr.per, j, h, n);
 }
 
 __host__ __device__ inline size_t tie_words(int n) { return ((size_t)n + 31) / 32; }
@@ -967,28 +971,30 @@ __device__ inline void win_fit(Fit<R, NCH> &f, const Win<R, NCH> &s, R xj_minus_
 // largest moment they have held; where the centred spread is below a fixed
 // part of that (a tight cluster after wide windows, or a far origin), this
 // centre's window is refitted directly in FP64.
-// (out of line, arguments by value: the rare call must not force the
-// caller's fits, frame or channel table into local memory)
+// (out of line, taking only the pointers it reads, by value: the rare call
+// must not force the caller's fits, frame or channel table into local memory,
+// nor put a frame copy in the hot loop's code)
 template <typename R, int NCH>
 struct Chans {
     const R *p[NCH];
 };
 template <typename R, int NCH, bool DIFF = false>
-__device__ __noinline__ Fit<R, NCH> win_refit_fp64(const Frame<R> fr, const Chans<R, NCH> cv, int j,
-                                                   int h, int n, double vsmlsq)
+__device__ __noinline__ Fit<R, NCH> win_refit_fp64(const typename Vec2<R>::T *XW, int per,
+                                                   const Chans<R, NCH> cv, int j, int h, int n,
+                                                   double vsmlsq)
 {
     const R *v[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) v[c] = cv.p[c];
     Fit<R, NCH> f;
-    const int lo = win_lo(fr, j, h, n);
+    const int lo = win_lo_mode(per, j, h, n);
     double sw = 0.0, swx = 0.0, swv[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) swv[c] = 0.0;
     for (int e = lo; e <= lo + 2 * h; ++e) {
         int sh;
         int p = slot_point(e, n, sh);
-        const typename Vec2<R>::T xw = fr.XW[p];
+        const typename Vec2<R>::T xw = XW[p];
         double w = (double)xw.y, x = (double)xw.x + sh;
         sw += w;
         swx += w * x;
@@ -1002,14 +1008,14 @@ __device__ __noinline__ Fit<R, NCH> win_refit_fp64(const Frame<R> fr, const Chan
     for (int e = lo; e <= lo + 2 * h; ++e) {
         int sh;
         int p = slot_point(e, n, sh);
-        const typename Vec2<R>::T xw = fr.XW[p];
+        const typename Vec2<R>::T xw = XW[p];
         double w = (double)xw.y, dx = (double)xw.x + sh - xm;
         sxx += w * dx * dx;
 #pragma unroll
         for (int c = 0; c < NCH; ++c) sxv[c] += w * dx * (double)chan<R, NCH, DIFF>(v, c, p);
     }
     const bool slope = sxx > vsmlsq;
-    const double dxj = (double)fr.XW[j].x - xm;
+    const double dxj = (double)XW[j].x - xm;
     f.rW = (R)(1.0 / sw);
     f.slope = slope;
     f.rS = slope ? (R)(1.0 / sxx) : R(0);
@@ -1035,7 +1041,7 @@ __device__ inline void win_fit_checked(Fit<R, NCH> &f, const Win<R, NCH> &s, con
             Chans<R, NCH> cv;
 #pragma unroll
             for (int c = 0; c < NCH; ++c) cv.p[c] = (DIFF && c == NCH - 1) ? nullptr : v[c];
-            f = win_refit_fp64<R, NCH, DIFF>(fr, cv, j, h, n, (double)vsmlsq);
+            f = win_refit_fp64<R, NCH, DIFF>(fr.XW, fr.per, cv, j, h, n, (double)vsmlsq);
             f.sxx = sxx;
         }
         if (fabs(sxx - vsmlsq) <= (R)kNearSlope * vsmlsq) near = true;
@@ -1211,7 +1217,9 @@ __device__ __noinline__ double sp_settle_fp64(const Frame<R> fr, const double *y
                                               int sl, bool lim0, bool lim1, const double *spans,
                                               double alpha)
 {
-    const double xj = (double)fr.key[je] * 5.421010862427522e-20;
+    const uint64_t *key = fr.key;
+    const uint16_t *perm = fr.perm;
+    const double xj = (double)key[je] * 5.421010862427522e-20;
     const int lo[3] = {win_lo(fr, je, h0, n), win_lo(fr, je, h1, n), win_lo(fr, je, h2, n)};
     const int hw[3] = {h0, h1, h2};
     double sw = 0.0, sa = 0.0, sb = 0.0, sc = 0.0, sd = 0.0, fit[3];
@@ -1227,8 +1235,8 @@ __device__ __noinline__ double sp_settle_fp64(const Frame<R> fr, const double *y
             const int e = v < na ? ea + v : eb + (v - na);
             int sh;
             const int p = slot_point(e, n, sh);
-            const uint32_t i = fr.perm[p];
-            const double x = (double)fr.key[p] * 5.421010862427522e-20 + sh;
+            const uint32_t i = perm[p];
+            const double x = (double)key[p] * 5.421010862427522e-20 + sh;
             const double w = w64[i], y = y64[i], dx = x - xj;
             aw += w;
             aa += w * dx;
@@ -1254,7 +1262,7 @@ __device__ __noinline__ double sp_settle_fp64(const Frame<R> fr, const double *y
         const double b = sxx > vsmlsq64 ? sxv / sxx : 0.0;
         fit[k] = sc / sw + b * (0.0 - xb);
     }
-    const double ye = y64[fr.perm[je]];
+    const double ye = y64[perm[je]];
     double e[3];
 #pragma unroll 1
     for (int k = 0; k < 3; ++k) {
