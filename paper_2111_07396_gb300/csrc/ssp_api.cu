@@ -24,24 +24,24 @@ cudaError_t argmax_launch_fp32(const ArgmaxArgs &, int, cudaStream_t);
 cudaError_t argmax_launch_fp64(const ArgmaxArgs &, int, cudaStream_t);
 cudaError_t peaks_launch_fp32(const PeaksArgs &, int, cudaStream_t);
 cudaError_t peaks_launch_fp64(const PeaksArgs &, int, cudaStream_t);
-cudaError_t pgram_occupancy_fp32_per(int, bool, int, size_t, int *);
-cudaError_t pgram_launch_fp32_per(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
-cudaError_t pgram_occupancy_fp32_clamp(int, bool, int, size_t, int *);
-cudaError_t pgram_launch_fp32_clamp(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
-cudaError_t pgram_occupancy_fp64_per(int, bool, int, size_t, int *);
-cudaError_t pgram_launch_fp64_per(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
-cudaError_t pgram_occupancy_fp64_clamp(int, bool, int, size_t, int *);
-cudaError_t pgram_launch_fp64_clamp(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
-cudaError_t pgram_occupancy_redo_per(int, bool, int, size_t, int *);
-cudaError_t pgram_launch_redo_per(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
-cudaError_t pgram_occupancy_redo_clamp(int, bool, int, size_t, int *);
-cudaError_t pgram_launch_redo_clamp(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
-cudaError_t pgram_occupancy_fp32_shared(int, bool, int, size_t, int *);
-cudaError_t pgram_launch_fp32_shared(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
-cudaError_t pgram_occupancy_fp64_shared(int, bool, int, size_t, int *);
-cudaError_t pgram_launch_fp64_shared(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
-cudaError_t pgram_occupancy_redo_shared(int, bool, int, size_t, int *);
-cudaError_t pgram_launch_redo_shared(int, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_fp32_per(int, bool, bool, int, size_t, int *);
+cudaError_t pgram_launch_fp32_per(int, bool, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_fp32_clamp(int, bool, bool, int, size_t, int *);
+cudaError_t pgram_launch_fp32_clamp(int, bool, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_fp64_per(int, bool, bool, int, size_t, int *);
+cudaError_t pgram_launch_fp64_per(int, bool, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_fp64_clamp(int, bool, bool, int, size_t, int *);
+cudaError_t pgram_launch_fp64_clamp(int, bool, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_redo_per(int, bool, bool, int, size_t, int *);
+cudaError_t pgram_launch_redo_per(int, bool, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_redo_clamp(int, bool, bool, int, size_t, int *);
+cudaError_t pgram_launch_redo_clamp(int, bool, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_fp32_shared(int, bool, bool, int, size_t, int *);
+cudaError_t pgram_launch_fp32_shared(int, bool, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_fp64_shared(int, bool, bool, int, size_t, int *);
+cudaError_t pgram_launch_fp64_shared(int, bool, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
+cudaError_t pgram_occupancy_redo_shared(int, bool, bool, int, size_t, int *);
+cudaError_t pgram_launch_redo_shared(int, bool, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
 size_t pgram_small_bytes_fp32(int, int);
 size_t pgram_frame_bytes_fp32(int, int, bool);
 size_t pgram_small_bytes_fp64(int, int);
@@ -61,35 +61,35 @@ cudaError_t peaks_launch(int p, const PeaksArgs &a, int n, cudaStream_t s)
 {
     return p == SSP_FP64 ? peaks_launch_fp64(a, n, s) : peaks_launch_fp32(a, n, s);
 }
-cudaError_t pgram_occupancy(int p, int v, bool g, bool per, bool shared, int G, size_t smem,
-                            int *bps)
+cudaError_t pgram_occupancy(int p, int v, bool g, bool lng, bool per, bool shared, int G,
+                            size_t smem, int *bps)
 {
     if (shared)   // periodic windows only
-        return p == SSP_FP64 ? pgram_occupancy_fp64_shared(v, g, G, smem, bps)
-             : p == kPrecRedo ? pgram_occupancy_redo_shared(v, g, G, smem, bps)
-                              : pgram_occupancy_fp32_shared(v, g, G, smem, bps);
+        return p == SSP_FP64 ? pgram_occupancy_fp64_shared(v, g, lng, G, smem, bps)
+             : p == kPrecRedo ? pgram_occupancy_redo_shared(v, g, lng, G, smem, bps)
+                              : pgram_occupancy_fp32_shared(v, g, lng, G, smem, bps);
     if (per)
-        return p == SSP_FP64 ? pgram_occupancy_fp64_per(v, g, G, smem, bps)
-             : p == kPrecRedo ? pgram_occupancy_redo_per(v, g, G, smem, bps)
-                              : pgram_occupancy_fp32_per(v, g, G, smem, bps);
-    return p == SSP_FP64 ? pgram_occupancy_fp64_clamp(v, g, G, smem, bps)
-         : p == kPrecRedo ? pgram_occupancy_redo_clamp(v, g, G, smem, bps)
-                          : pgram_occupancy_fp32_clamp(v, g, G, smem, bps);
+        return p == SSP_FP64 ? pgram_occupancy_fp64_per(v, g, lng, G, smem, bps)
+             : p == kPrecRedo ? pgram_occupancy_redo_per(v, g, lng, G, smem, bps)
+                              : pgram_occupancy_fp32_per(v, g, lng, G, smem, bps);
+    return p == SSP_FP64 ? pgram_occupancy_fp64_clamp(v, g, lng, G, smem, bps)
+         : p == kPrecRedo ? pgram_occupancy_redo_clamp(v, g, lng, G, smem, bps)
+                          : pgram_occupancy_fp32_clamp(v, g, lng, G, smem, bps);
 }
-cudaError_t pgram_launch(int p, int v, bool g, bool per, bool shared, int grid, int G, size_t smem,
-                         const PgramArgs &a, cudaStream_t s)
+cudaError_t pgram_launch(int p, int v, bool g, bool lng, bool per, bool shared, int grid, int G,
+                         size_t smem, const PgramArgs &a, cudaStream_t s)
 {
     if (shared)   // periodic windows only
-        return p == SSP_FP64 ? pgram_launch_fp64_shared(v, g, grid, G, smem, a, s)
-             : p == kPrecRedo ? pgram_launch_redo_shared(v, g, grid, G, smem, a, s)
-                              : pgram_launch_fp32_shared(v, g, grid, G, smem, a, s);
+        return p == SSP_FP64 ? pgram_launch_fp64_shared(v, g, lng, grid, G, smem, a, s)
+             : p == kPrecRedo ? pgram_launch_redo_shared(v, g, lng, grid, G, smem, a, s)
+                              : pgram_launch_fp32_shared(v, g, lng, grid, G, smem, a, s);
     if (per)
-        return p == SSP_FP64 ? pgram_launch_fp64_per(v, g, grid, G, smem, a, s)
-             : p == kPrecRedo ? pgram_launch_redo_per(v, g, grid, G, smem, a, s)
-                              : pgram_launch_fp32_per(v, g, grid, G, smem, a, s);
-    return p == SSP_FP64 ? pgram_launch_fp64_clamp(v, g, grid, G, smem, a, s)
-         : p == kPrecRedo ? pgram_launch_redo_clamp(v, g, grid, G, smem, a, s)
-                          : pgram_launch_fp32_clamp(v, g, grid, G, smem, a, s);
+        return p == SSP_FP64 ? pgram_launch_fp64_per(v, g, lng, grid, G, smem, a, s)
+             : p == kPrecRedo ? pgram_launch_redo_per(v, g, lng, grid, G, smem, a, s)
+                              : pgram_launch_fp32_per(v, g, lng, grid, G, smem, a, s);
+    return p == SSP_FP64 ? pgram_launch_fp64_clamp(v, g, lng, grid, G, smem, a, s)
+         : p == kPrecRedo ? pgram_launch_redo_clamp(v, g, lng, grid, G, smem, a, s)
+                          : pgram_launch_fp32_clamp(v, g, lng, grid, G, smem, a, s);
 }
 size_t pgram_small_bytes(int p, int G, int variant)
 {
@@ -225,6 +225,7 @@ int group_size(int n, int variant, int precision)
 struct LaunchCfg {
     bool gmem = false;
     bool cnt_smem = false;   // gmem: the sort's bucket counts in shared memory
+    bool lng = false;        // SS kernel that initialises windows out of line
     size_t smem = 0, slab_bytes = 0;
     int grid = 0;
 };
@@ -269,7 +270,12 @@ int configure(int precision, int variant, bool per, bool shared, int G, int n_ma
     c.smem = c.gmem ? small + (c.cnt_smem ? cnt : 0) : small + frame;
     c.slab_bytes = c.gmem ? frame : 0;
     int bps = 0;
-    cudaError_t e = pgram_occupancy(precision, variant, c.gmem, per, shared, G, c.smem, &bps);
+    // objects of many points (long windows, few centres per thread) take the SS
+    // kernel whose window initialisation is out of line (FP32C: the only
+    // precision it is built for)
+    c.lng = variant == VAR_SS && precision == SSP_FP32C && n_max > kLongN;
+    cudaError_t e = pgram_occupancy(precision, variant, c.gmem, c.lng, per, shared, G, c.smem,
+                                    &bps);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy");
     if (bps < 1) return fail(SSP_ERR_NOMEM, "a CTA frame for n = %d does not fit", n_max);
     c.grid = bps * sms;
@@ -605,7 +611,7 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
             slab_cur += b.main.gmem ? b.main.slab_bytes * (size_t)b.main.grid : 0;
             const int ph = variant == SSP_SS ? SSP_PHASE_PGRAM_SS : SSP_PHASE_PGRAM_SP;
             on = prof_begin(ph, s, mk);
-            if ((e = pgram_launch(prec, kv, b.main.gmem, per, b.shared, b.main.grid, b.G, b.main.smem,
+            if ((e = pgram_launch(prec, kv, b.main.gmem, b.main.lng, per, b.shared, b.main.grid, b.G, b.main.smem,
                                   ga, s)))
                 break;
             prof_end(on, mk, s);
@@ -620,7 +626,7 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
                 ga.recompute = 1;
                 slab_cur += b.redo.gmem ? b.redo.slab_bytes * (size_t)b.redo.grid : 0;
                 on = prof_begin(SSP_PHASE_REDO, s, mk);
-                if ((e = pgram_launch(kPrecRedo, kv, b.redo.gmem, per, b.shared, b.redo.grid, b.G,
+                if ((e = pgram_launch(kPrecRedo, kv, b.redo.gmem, b.redo.lng, per, b.shared, b.redo.grid, b.G,
                                       b.redo.smem, ga, s)))
                     break;
                 prof_end(on, mk, s);
@@ -782,14 +788,14 @@ int run_device_noalloc(const double *t, const double *y, const double *dy, const
             ga.recompute = 0;
             ga.periodic = P.periodic;
             ga.span = P.span;
-            if ((e = pgram_launch(prec, kv, false, per, false, b.main.grid, b.G, b.main.smem, ga, s)))
+            if ((e = pgram_launch(prec, kv, false, b.main.lng, per, false, b.main.grid, b.G, b.main.smem, ga, s)))
                 break;
             if (plan.redo) {
                 ga.yc = d_yc64;
                 ga.wv = d_wv64;
                 ga.item_counter = d_counters + 2 * k + 1;
                 ga.recompute = 1;
-                if ((e = pgram_launch(kPrecRedo, kv, false, per, false, b.redo.grid, b.G, b.redo.smem,
+                if ((e = pgram_launch(kPrecRedo, kv, false, b.redo.lng, per, false, b.redo.grid, b.G, b.redo.smem,
                                       ga, s)))
                     break;
             }

@@ -60,6 +60,9 @@ constexpr float kNearSlope = 1e-4f;
 constexpr float kRefitFrac = 1.f / 128.f;  // history guard of the sliding sums
 // windows of at most this many points are initialised by direct summation
 constexpr int kDirectInit = 32;
+// SS launches whose objects exceed this many points use the kernel that
+// initialises windows out of line (FP32C)
+constexpr int kLongN = 1536;
 // SP: a point whose fit could move the power by more than kSensTau through
 // the FP32 error of its residuals (bass enhancement divides by the smallest;
 // each residual is taken to err by its slope times the rounding of X plus
@@ -849,8 +852,8 @@ __device__ inline void win_add_slot(Win<R, NCH> &s, const Frame<R> &fr, const R 
 // the extended-precision prefixes (raw moments about 0, shifted by -1/+1 for
 // the wrapped parts, then moved to origin o), the ragged ends point by point.
 template <typename R, int NCH, bool DIFF = false, typename A>
-__device__ void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R, A> &sm,
-                         const R *const *v, int c, int h, int n, R o)
+__device__ inline void win_init_body(Win<R, NCH> &s, const Frame<R> &fr, const Small<R, A> &sm,
+                                     const R *const *v, int c, int h, int n, R o)
 {
     const int G = blockDim.x, L = G + 1;
     A W = acc_from<A>(R(0)), S1 = W, S2 = W, C[NCH], D[NCH];
@@ -939,6 +942,51 @@ __device__ void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R, A> &
     if (sizeof(R) == 4) s.hiB = fmax(s.hiB, s.B);
 }
 
+// Window initialisation, in line or (OOL) out of line.  Out of line there is
+// one copy of the code per channel layout instead of one per call site, which
+// keeps the SS passes' instruction footprint small; the call takes only what
+// the initialisation reads (phases and weights, window mode, channels, chunk
+// starts and prefixes), but saves and restores the caller's live registers.
+// Long objects (few centres per thread, long windows) gain: C2 SS runs 7%
+// faster.  Short ones lose (C3 SS 4% slower), so the kernels for them keep
+// it in line.
+template <typename R, int NCH>
+struct Chans {
+    const R *p[NCH];
+};
+template <typename R, int NCH, bool DIFF, typename A>
+__device__ __noinline__ Win<R, NCH> win_init_ool(const typename Vec2<R>::T *XW, int per,
+                                                 const Chans<R, NCH> cv, int *cs, A *px, A *pc,
+                                                 int c, int h, int n, R o)
+{
+    Frame<R> fr{};
+    fr.XW = const_cast<typename Vec2<R>::T *>(XW);
+    fr.per = per;
+    Small<R, A> sm{};
+    sm.cs = cs;
+    sm.px = px;
+    sm.pc = pc;
+    const R *v[NCH];
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) v[ch] = cv.p[ch];
+    Win<R, NCH> s;
+    win_init_body<R, NCH, DIFF>(s, fr, sm, v, c, h, n, o);
+    return s;
+}
+template <typename R, int NCH, bool DIFF = false, bool OOL = false, typename A>
+__device__ inline void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<R, A> &sm,
+                                const R *const *v, int c, int h, int n, R o)
+{
+    if constexpr (OOL) {
+        Chans<R, NCH> cv;
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) cv.p[ch] = (DIFF && ch == NCH - 1) ? nullptr : v[ch];
+        s = win_init_ool<R, NCH, DIFF, A>(fr.XW, fr.per, cv, sm.cs, sm.px, sm.pc, c, h, n, o);
+    } else {
+        win_init_body<R, NCH, DIFF>(s, fr, sm, v, c, h, n, o);
+    }
+}
+
 // the line fit of a window evaluated at the centre j
 template <typename R, int NCH>
 struct Fit {
@@ -974,10 +1022,6 @@ __device__ inline void win_fit(Fit<R, NCH> &f, const Win<R, NCH> &s, R xj_minus_
 // (out of line, taking only the pointers it reads, by value: the rare call
 // must not force the caller's fits, frame or channel table into local memory,
 // nor put a frame copy in the hot loop's code)
-template <typename R, int NCH>
-struct Chans {
-    const R *p[NCH];
-};
 template <typename R, int NCH, bool DIFF = false>
 __device__ __noinline__ Fit<R, NCH> win_refit_fp64(const typename Vec2<R>::T *XW, int per,
                                                    const Chans<R, NCH> cv, int j, int h, int n,
@@ -1316,7 +1360,7 @@ __device__ inline FreqResult fixed_span_pass(const PgramArgs &a, const Frame<R> 
 // ---------------------------------------------------------------------------
 // one (object, frequency)
 // ---------------------------------------------------------------------------
-template <typename R, int VARIANT, typename A>
+template <typename R, int VARIANT, bool LONG, typename A>
 __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, int n, double f,
                                         const Frame<R> &fr, const Small<R, A> &sm, bool reuse)
 {
@@ -1628,9 +1672,9 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
         __syncthreads();
         if (c0 < c1) {
             Win<R, 1> w0, w1, w2;
-            win_init<R, 1>(w0, fr, sm, vy, c0, h0, n, o);
-            win_init<R, 1>(w1, fr, sm, vy, c0, h1, n, o);
-            win_init<R, 1>(w2, fr, sm, vy, c0, h2, n, o);
+            win_init<R, 1, false, LONG>(w0, fr, sm, vy, c0, h0, n, o);
+            win_init<R, 1, false, LONG>(w1, fr, sm, vy, c0, h1, n, o);
+            win_init<R, 1, false, LONG>(w2, fr, sm, vy, c0, h2, n, o);
             RunAvg<R, 3> ra;
             ra.reset(c0);
             auto emit = [&](int i, const R (&v)[3]) {
@@ -1680,7 +1724,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
         __syncthreads();
         if (c0 < c1) {
             Win<R, NB> w1;
-            win_init<R, NB, DIFF>(w1, fr, sm, vr, c0, h1, n, o);
+            win_init<R, NB, DIFF, LONG>(w1, fr, sm, vr, c0, h1, n, o);
             RunAvg<R, NB> ra;
             ra.reset(c0);
             auto emit = [&](int i, const R (&v)[NB]) {
@@ -1711,7 +1755,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
         __syncthreads();
         if (c0 < c1) {
             Win<R, 1> w1;
-            win_init<R, 1>(w1, fr, sm, vs, c0, h1, n, o);
+            win_init<R, 1, false, LONG>(w1, fr, sm, vs, c0, h1, n, o);
             RunAvg<R, 1> ra;
             ra.reset(c0);
             auto emit = [&](int i, const R (&v)[1]) {
@@ -1735,7 +1779,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
         __syncthreads();
         if (c0 < c1) {
             Win<R, 1> w0;
-            win_init<R, 1>(w0, fr, sm, vv, c0, h0, n, o);
+            win_init<R, 1, false, LONG>(w0, fr, sm, vv, c0, h0, n, o);
             RunAvg<R, 1> ra;
             ra.reset(c0);
             auto emit = [&](int i, const R (&v)[1]) {
@@ -1762,7 +1806,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
 // FP32C launches flag frequencies whose decisions came within their margins;
 // the FP64 kernel's recompute launch then redoes exactly those frequencies
 // and overwrites their (float) power.
-template <typename R, int VARIANT, bool GMEM, bool PLAIN, bool PER, bool SHARED>
+// LONG: SS initialises its windows out of line (objects of many points)
+template <typename R, int VARIANT, bool GMEM, bool PLAIN, bool PER, bool SHARED, bool LONG = false>
 __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
 {
     typedef typename AccSel<R, PLAIN>::T A;
@@ -1803,7 +1848,7 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
                 } else {
                     const double fq = a.freq[(a.fbase ? a.fbase[o] : 0) + q];
                     const FreqResult r =
-                        process_frequency<R, VARIANT>(a, obj, o, n, fq, fr, sm, SHARED && sorted);
+                        process_frequency<R, VARIANT, LONG>(a, obj, o, n, fq, fr, sm, SHARED && sorted);
                     sorted = true;
                     const double c0 = a.chi0[obj];
                     pw = (c0 > 0.0) ? 1.0 - r.chi2 / c0 : 0.0;

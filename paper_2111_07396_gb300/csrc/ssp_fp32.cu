@@ -4,4 +4,4 @@
 #include "ssp_kernels.cuh"
 SSP_INSTANTIATE_PREP(float, fp32)
 SSP_INSTANTIATE_SIZES(float, false, fp32)
-SSP_INSTANTIATE_PGRAM(float, false, true, false, fp32_per)
+SSP_INSTANTIATE_PGRAM(float, false, true, false, fp32_per, true)

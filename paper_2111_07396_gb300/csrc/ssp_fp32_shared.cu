@@ -2,4 +2,4 @@
 // cover several objects with identical times: one fold and sort per frequency
 // for all of them.
 #include "ssp_kernels.cuh"
-SSP_INSTANTIATE_PGRAM(float, false, true, true, fp32_shared)
+SSP_INSTANTIATE_PGRAM(float, false, true, true, fp32_shared, true)

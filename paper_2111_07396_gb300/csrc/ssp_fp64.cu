@@ -4,4 +4,4 @@
 #include "ssp_kernels.cuh"
 SSP_INSTANTIATE_PREP(double, fp64)
 SSP_INSTANTIATE_SIZES(double, false, fp64)
-SSP_INSTANTIATE_PGRAM(double, false, true, false, fp64_per)
+SSP_INSTANTIATE_PGRAM(double, false, true, false, fp64_per, false)

@@ -225,51 +225,62 @@ __global__ void __launch_bounds__(256) peaks_kernel(PeaksArgs a)
 
 // periodogram kernels of one precision, accumulator and window mode (PER:
 // periodic windows, else clamped inside the data); SHARED: work items may
-// cover several objects with identical times; SUF names the functions
-#define SSP_INSTANTIATE_PGRAM(R, PLAIN, PER, SHARED, SUF)                                             \
+// cover several objects with identical times; WL: also the SS kernels that
+// initialise windows out of line, for long objects; SUF names the functions
+#define SSP_INSTANTIATE_PGRAM(R, PLAIN, PER, SHARED, SUF, WL)                                  \
     namespace ssp {                                                                           \
-    template <int V, bool GM>                                                                 \
+    template <int V, bool GM, bool L>                                                         \
     static cudaError_t occ_##SUF(int G, size_t smem, int *bps)                                \
     {                                                                                         \
-        cudaError_t e = cudaFuncSetAttribute(pgram_kernel<R, V, GM, PLAIN, PER, SHARED>,              \
+        cudaError_t e = cudaFuncSetAttribute(pgram_kernel<R, V, GM, PLAIN, PER, SHARED, L>,   \
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                              (int)smem);                                      \
         if (e != cudaSuccess) return e;                                                       \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                 \
-            bps, pgram_kernel<R, V, GM, PLAIN, PER, SHARED>, G, smem);                                \
+            bps, pgram_kernel<R, V, GM, PLAIN, PER, SHARED, L>, G, smem);                     \
     }                                                                                         \
-    cudaError_t pgram_occupancy_##SUF(int variant, bool gmem, int G, size_t smem, int *bps)   \
+    template <int V, bool L>                                                                  \
+    static cudaError_t occ2_##SUF(bool gmem, int G, size_t smem, int *bps)                    \
     {                                                                                         \
-        switch (variant) {                                                                    \
-        case VAR_SS: return gmem ? occ_##SUF<VAR_SS, true>(G, smem, bps)                      \
-                                 : occ_##SUF<VAR_SS, false>(G, smem, bps);                    \
-        case VAR_SP: return gmem ? occ_##SUF<VAR_SP, true>(G, smem, bps)                      \
-                                 : occ_##SUF<VAR_SP, false>(G, smem, bps);                    \
-        case VAR_SPG: return gmem ? occ_##SUF<VAR_SPG, true>(G, smem, bps)                    \
-                                  : occ_##SUF<VAR_SPG, false>(G, smem, bps);                  \
-        default: return gmem ? occ_##SUF<VAR_FIXED, true>(G, smem, bps)                       \
-                             : occ_##SUF<VAR_FIXED, false>(G, smem, bps);                     \
-        }                                                                                     \
+        return gmem ? occ_##SUF<V, true, L>(G, smem, bps) : occ_##SUF<V, false, L>(G, smem, bps); \
     }                                                                                         \
-    cudaError_t pgram_launch_##SUF(int variant, bool gmem, int grid, int G, size_t smem,      \
-                                   const PgramArgs &a, cudaStream_t s)                        \
+    cudaError_t pgram_occupancy_##SUF(int variant, bool gmem, bool lng, int G, size_t smem,   \
+                                      int *bps)                                               \
     {                                                                                         \
         switch (variant) {                                                                    \
         case VAR_SS:                                                                          \
-            if (gmem) pgram_kernel<R, VAR_SS, true, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);     \
-            else pgram_kernel<R, VAR_SS, false, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);         \
+            if constexpr (WL) {                                                               \
+                if (lng) return occ2_##SUF<VAR_SS, true>(gmem, G, smem, bps);                 \
+            }                                                                                 \
+            return occ2_##SUF<VAR_SS, false>(gmem, G, smem, bps);                             \
+        case VAR_SP: return occ2_##SUF<VAR_SP, false>(gmem, G, smem, bps);                    \
+        case VAR_SPG: return occ2_##SUF<VAR_SPG, false>(gmem, G, smem, bps);                  \
+        default: return occ2_##SUF<VAR_FIXED, false>(gmem, G, smem, bps);                     \
+        }                                                                                     \
+    }                                                                                         \
+    template <int V, bool L>                                                                  \
+    static void launch2_##SUF(bool gmem, int grid, int G, size_t smem, const PgramArgs &a,    \
+                              cudaStream_t s)                                                 \
+    {                                                                                         \
+        if (gmem) pgram_kernel<R, V, true, PLAIN, PER, SHARED, L><<<grid, G, smem, s>>>(a);   \
+        else pgram_kernel<R, V, false, PLAIN, PER, SHARED, L><<<grid, G, smem, s>>>(a);       \
+    }                                                                                         \
+    cudaError_t pgram_launch_##SUF(int variant, bool gmem, bool lng, int grid, int G,         \
+                                   size_t smem, const PgramArgs &a, cudaStream_t s)           \
+    {                                                                                         \
+        switch (variant) {                                                                    \
+        case VAR_SS:                                                                          \
+            if constexpr (WL) {                                                               \
+                if (lng) {                                                                    \
+                    launch2_##SUF<VAR_SS, true>(gmem, grid, G, smem, a, s);                   \
+                    break;                                                                    \
+                }                                                                             \
+            }                                                                                 \
+            launch2_##SUF<VAR_SS, false>(gmem, grid, G, smem, a, s);                          \
             break;                                                                            \
-        case VAR_SP:                                                                          \
-            if (gmem) pgram_kernel<R, VAR_SP, true, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);     \
-            else pgram_kernel<R, VAR_SP, false, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);         \
-            break;                                                                            \
-        case VAR_SPG:                                                                         \
-            if (gmem) pgram_kernel<R, VAR_SPG, true, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);    \
-            else pgram_kernel<R, VAR_SPG, false, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);        \
-            break;                                                                            \
-        default:                                                                              \
-            if (gmem) pgram_kernel<R, VAR_FIXED, true, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);  \
-            else pgram_kernel<R, VAR_FIXED, false, PLAIN, PER, SHARED><<<grid, G, smem, s>>>(a);      \
+        case VAR_SP: launch2_##SUF<VAR_SP, false>(gmem, grid, G, smem, a, s); break;          \
+        case VAR_SPG: launch2_##SUF<VAR_SPG, false>(gmem, grid, G, smem, a, s); break;        \
+        default: launch2_##SUF<VAR_FIXED, false>(gmem, grid, G, smem, a, s);                  \
         }                                                                                     \
         return cudaGetLastError();                                                            \
     }                                                                                         \

@@ -50,10 +50,11 @@ cudaError_t peaks_launch(int precision, const PeaksArgs &a, int n_obj, cudaStrea
 // Sets the dynamic shared-memory limit and returns resident CTAs per SM.
 // shared: work items may cover several objects with identical times
 // (periodic windows only).
-cudaError_t pgram_occupancy(int precision, int variant, bool gmem, bool per, bool shared, int G,
-                            size_t smem, int *blocks_per_sm);
-cudaError_t pgram_launch(int precision, int variant, bool gmem, bool per, bool shared, int grid,
-                         int G, size_t smem, const PgramArgs &a, cudaStream_t s);
+// lng: the SS kernel that initialises its windows out of line (FP32C).
+cudaError_t pgram_occupancy(int precision, int variant, bool gmem, bool lng, bool per, bool shared,
+                            int G, size_t smem, int *blocks_per_sm);
+cudaError_t pgram_launch(int precision, int variant, bool gmem, bool lng, bool per, bool shared,
+                         int grid, int G, size_t smem, const PgramArgs &a, cudaStream_t s);
 
 size_t pgram_small_bytes(int precision, int G, int variant);
 size_t pgram_frame_bytes(int precision, int n, int variant, bool keep_perm);

@@ -3,4 +3,4 @@
 // accurate to about 1e-8, far inside the FP32C tolerance its results serve.
 #include "ssp_kernels.cuh"
 SSP_INSTANTIATE_SIZES(double, true, redo)
-SSP_INSTANTIATE_PGRAM(double, true, true, false, redo_per)
+SSP_INSTANTIATE_PGRAM(double, true, true, false, redo_per, false)
