@@ -1138,6 +1138,12 @@ __device__ inline SpanK<R> span_consts(const double *spans, double alpha)
 // limit value instead.
 // d01 (when use_d01) is the directly smoothed r0 - r1: it settles tweeter
 // against midrange where r0 and r1 round to the same value.
+// (residual ratio)^(10 - alpha) for alpha other than 9: out of line, so that
+// the inlined power function does not sit in the per-point loops that take
+// the default alpha's plain ratio
+static __device__ __noinline__ float span_pow(float x, float e) { return powf(x, e); }
+static __device__ __noinline__ double span_pow(double x, double e) { return pow(x, e); }
+
 template <typename R>
 __device__ inline R choose_span(const SpanK<R> &K, R r0, R r1, R r2, R res_woof, R fallback,
                                 bool lim0, bool lim1, bool use_d01 = false, R d01 = R(0))
@@ -1154,7 +1160,7 @@ __device__ inline R choose_span(const SpanK<R> &K, R r0, R r1, R r2, R res_woof,
     if (K.bass && below && resmin > R(0)) {
         R tmp = fdiv(resmin, res_woof);
         if (tmp < R(1.0e-7)) tmp = R(1.0e-7);
-        const R pw = (K.ex == R(1)) ? tmp : (sizeof(R) == 4 ? (R)powf((float)tmp, (float)K.ex) : (R)pow((double)tmp, (double)K.ex));
+        const R pw = (K.ex == R(1)) ? tmp : span_pow(tmp, K.ex);
         s += (K.s2 - s) * pw;
     }
     return s;

@@ -211,3 +211,22 @@ def test_window_modes(variant, code, periodic, span):
         assert gate_error(got, ref) <= TOL[precision], precision
         if precision == "fp64":
             np.testing.assert_array_equal(best, ref_best)
+
+
+@pytest.mark.parametrize("alpha", [0.0, 4.5, 10.0])
+@pytest.mark.parametrize("variant,code", VARIANTS[:2])
+def test_bass_alpha(variant, code, alpha):
+    # bass enhancement off (alpha 0), with a general exponent (10 - alpha =
+    # 5.5) and with exponent 0 (alpha 10); the default alpha 9 is the plain
+    # residual ratio that every other test takes
+    c1 = synth.config1(n_freq=500)
+    cat = synth.concat([c1, synth.config3(n_objects=4, n_freq=500).with_freq(c1.freq)])
+    cat.freq = c1.freq
+    ref, ref_best = oracle.periodogram(cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq, code,
+                                       alpha=alpha)
+    for precision in ("fp64", "fp32c"):
+        got, best = ssp.ssp_periodogram(cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq,
+                                        variant=variant, precision=precision, alpha=alpha)
+        assert gate_error(got, ref) <= TOL[precision], precision
+        if precision == "fp64":
+            np.testing.assert_array_equal(best, ref_best)
