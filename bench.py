@@ -223,7 +223,10 @@ def run_reference(args):
     t, y, dy = cat.obj(0)
     n = t.size
     cores = os.cpu_count() or 1
-    per_step = max(2 * cores, 32)
+    # 16 frequencies per core: about half a second a step on 16 cores, so the
+    # default 3 + 10 steps take seconds and the rate is not dominated by the
+    # threads' start-up
+    per_step = min(cat.freq.size, max(16 * cores, 32))
     rng = np.random.default_rng(11)
 
     def step(k):
