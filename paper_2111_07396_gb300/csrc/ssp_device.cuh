@@ -51,8 +51,10 @@ constexpr int kBucketRankMax = 64;   // larger buckets switch to the bitonic sor
 //    window spread within kNearSlope of vsmlsq.
 // SP choices are settled in place instead: where the tweeter and midrange
 // generalized-validation residuals are closer than kNearSP * eps_fp32 times
-// the magnitude scale at that point, the warp refits those two windows in
-// binary64 from the exact phases and binary64 inputs and decides from those.
+// the magnitude scale (the larger of the point's and the object's largest
+// centred magnitude), and the other choice could move the power by more than
+// kSensTau, the warp refits the three span windows in binary64 from the exact
+// phases and binary64 inputs and takes the choice from those.
 constexpr float kNearSS = 1e-6f;
 constexpr float kNearSP = 64.f;
 constexpr float kNearLev = 1e-4f;
