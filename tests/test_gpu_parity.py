@@ -230,3 +230,32 @@ def test_bass_alpha(variant, code, alpha):
         assert gate_error(got, ref) <= TOL[precision], precision
         if precision == "fp64":
             np.testing.assert_array_equal(best, ref_best)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+@pytest.mark.parametrize("variant,code,env", [
+    ("sp", oracle.SP, {"SSP_NEAR_SP": "100000", "SSP_SENS_TAU": "0"}),
+    ("ss", oracle.SS, {"SSP_REFIT_FRAC": "100000"}),
+])
+def test_forced_binary64_paths(variant, code, env, periodic, monkeypatch):
+    # The FP32C path's binary64 fallbacks run only where a decision or a window
+    # is marginal.  Widening their triggers (read at each launch) sends nearly
+    # every centre through them: SP settles each contested centre in binary64
+    # over its three nested windows; SS refits every window in binary64.  The
+    # result must still be the oracle's.
+    c1 = synth.config1(n_freq=120)
+    # minimum size, duplicated times (tie runs), 385 and 1,537 points (the
+    # latter takes the SS kernel whose windows initialise out of line)
+    cat = synth.concat([c1, _edge_catalog().subset([0, 1, 6, 8])])
+    cat.freq = c1.freq
+    iper = 2 if periodic else 1
+    ref, _ = oracle.periodogram(cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq, code, iper=iper)
+    args = (cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq)
+    plain, _ = ssp.ssp_periodogram(*args, variant=variant, precision="fp32c", periodic=periodic)
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    got, _ = ssp.ssp_periodogram(*args, variant=variant, precision="fp32c", periodic=periodic)
+    assert gate_error(got, ref) <= TOL["fp32c"]
+    # the binary64 values differ from the FP32 sliding sums' in their last bits:
+    # proof that the forced path ran
+    assert not np.array_equal(got, plain)
