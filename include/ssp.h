@@ -53,6 +53,29 @@ typedef enum {
                       compensated chi2; power written as float */
 } ssp_precision;
 
+/*
+ * SSP_FP32C re-takes in binary64 the decisions that FP32 rounding could flip.
+ * Its margins have defaults chosen for the 2e-4 tolerance; each can be
+ * overridden, for testing and tuning only, by an environment variable read at
+ * every launch (a value of 1e6 or more, or an empty one, keeps the default; a
+ * negative margin disables its test):
+ *   SSP_NEAR_SS     SS tweeter-vs-midrange margin for n <= 256 (default 1e-6,
+ *                   relative; scaled down for larger n).  Flags the frequency
+ *                   for the binary64 recompute.
+ *   SSP_NEAR_SP     SP near-tie margin in FP32 ulps of the magnitude scale
+ *                   (default 64).
+ *   SSP_SENS_TAU    SP: power budget per point; a near-tie whose other choice
+ *                   could move the power by more is settled in binary64
+ *                   (default 1e-6).
+ *   SSP_SENS_ULPS   SP: rounding of a residual, in ulps of its scale, in that
+ *                   bound (default 2).
+ *   SSP_REFIT_FRAC  a window whose centred spread fell below this fraction of
+ *                   the largest moment its sliding sums held is refitted in
+ *                   binary64 (default 1/128).
+ * Wider margins cost time and keep accuracy; narrower ones can break the
+ * tolerance.
+ */
+
 typedef enum {
     SSP_OK = 0,
     SSP_ERR_ARG = -1,         /* invalid argument or input value */

@@ -345,9 +345,9 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
 
 size_t rsize(int precision) { return precision == SSP_FP64 ? 8 : 4; }
 
-// margins below which FP32C span choices count as contested; SSP_NEAR_SS
-// and SSP_NEAR_SP override them (calibration of the FP64 recompute; a
-// negative value disables that test)
+// FP32C margins, overridable for testing and tuning by SSP_NEAR_SS,
+// SSP_NEAR_SP, SSP_SENS_TAU, SSP_SENS_ULPS and SSP_REFIT_FRAC (a value of 1e6
+// or more keeps the default; a negative margin disables its test)
 float near_margin(const char *env, float dflt)
 {
     const char *e = std::getenv(env);
