@@ -80,6 +80,25 @@ def traffic_per_launch(variant):
 L2_FLUSH_BYTES = 512 << 20
 
 
+def max_over_ranks(dist, x, device="cpu"):
+    """The largest of every rank's x (the job's time is its slowest rank's);
+    x itself for a single process.  Any backend: NCCL on the GPUs, gloo in
+    the tests."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank_step, steps, seconds):
+    """Whole-job throughput: every rank processes its own replica of the
+    workload (weak scaling), so the job does world x the units of one rank in
+    the slowest rank's time."""
+    return world * units_per_rank_step * steps / seconds
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,13 +335,9 @@ def run_ours(args):
         ssp.ssp_profile_enable(False)
         prof = ssp.ssp_profile_read(reset=True)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if dist is not None:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(dist, float(sum(step_ms)), dev)
     ptf_step = 2 * n * nf
-    value = world * ptf_step * args.steps / (total_ms / 1e3)
+    value = job_rate(world, ptf_step, args.steps, total_ms / 1e3)
     clocks = clk.summary()
 
     # FP32C results of the last step, and the same work in FP64
@@ -377,14 +392,10 @@ def run_ours(args):
     for _ in range(args.steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0, dev)
     h2d = 2 * (3 * 8 * n + 8 * nf)
     d2h = 2 * (4 * nf + 8)
-    e2e = {"value": world * ptf_step * args.steps / e2e_s, "unit": UNIT,
+    e2e = {"value": job_rate(world, ptf_step, args.steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "api": "ssp_periodogram (host pointers, pinned), SS + SP"}
 
