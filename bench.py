@@ -277,7 +277,7 @@ def run_ours(args):
 
     from paper_2111_07396_gb300 import build as ssp_build
     from paper_2111_07396_gb300 import ssp
-    from tests.parity import gate_error
+    from tests.parity import FLOOR, chi2_rel_error, gate_error
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -365,6 +365,8 @@ def run_ours(args):
         for v in ("ss", "sp"):
             ref = out64[v][0].cpu().numpy()[0]
             acc[v] = {"max_gate_err_vs_fp64": gate_error(p32[v], ref),
+                      "max_chi2_rel_err_vs_fp64": chi2_rel_error(p32[v], ref),
+                      "values_gated_by_floor": int(np.sum(np.abs(ref) < FLOOR)),
                       "max_abs_err_vs_fp64": float(np.max(np.abs(p32[v] - ref))),
                       "best_index_same": bool(np.argmax(p32[v]) == np.argmax(ref)),
                       "tolerance": 2e-4}
@@ -531,7 +533,7 @@ def run_matrix(args):
 
     from paper_2111_07396_gb300 import build as ssp_build
     from paper_2111_07396_gb300 import ssp, synth
-    from tests.parity import gate_error
+    from tests.parity import FLOOR, chi2_rel_error, gate_error
 
     if int(os.environ.get("RANK", "0")) != 0:
         return
@@ -604,6 +606,8 @@ def run_matrix(args):
                     "fp64": {"value": ptf_sub / (ms64 / 1e3), "ms": ms64,
                              "objects": ns},
                     "fp32c_vs_fp64": {"max_gate_err": gate_error(p32s, p64s),
+                                      "max_chi2_rel_err": chi2_rel_error(p32s, p64s),
+                                      "values_gated_by_floor": int(np.sum(np.abs(p64s) < FLOOR)),
                                       "max_abs_err": float(np.max(np.abs(p32s - p64s))),
                                       "best_index_same": same,
                                       "best_period_same": float(np.mean(b32[:ns] == b64s))},
