@@ -890,10 +890,11 @@ int ssp_fold_fixed(const double *tt, int64_t n, double f, uint64_t *out)
     g_err.clear();
     if (n < 0 || (n > 0 && (!tt || !out))) return fail(SSP_ERR_ARG, "bad array arguments");
     if (!std::isfinite(f) || !(f > 0.0)) return fail(SSP_ERR_ARG, "f must be finite and > 0");
+    const ssp::FoldFreq F = ssp::fold_freq(f);
     for (int64_t i = 0; i < n; ++i) {
         if (!std::isfinite(tt[i]) || tt[i] < 0.0)
             return fail(SSP_ERR_ARG, "tt[%lld] must be finite and >= 0", (long long)i);
-        out[i] = ssp::fold_fixed64(tt[i], f);
+        out[i] = ssp::fold_fixed64_fast(tt[i], F);
     }
     return SSP_OK;
 }

@@ -336,7 +336,7 @@ struct Small {
     A *px;         // [3][G + 1]
     A *pc;         // [2 * nch][G + 1]
     A *scan;       // [16][8] warp totals of a scan
-    double *red;   // [32] reduction scratch
+    double *red;   // [96] reduction scratch
     int *ired;     // [32]
     int *flags;    // [4]
 };
@@ -351,7 +351,7 @@ __host__ __device__ inline size_t small_bytes(int G, int variant)
     const size_t a = sizeof(A);
     return align16(4 * (size_t)(G + 1)) + align16(a * 3 * (size_t)(G + 1)) +
            align16(a * 2 * (size_t)max_channels(variant) * (size_t)(G + 1)) + 16 * 8 * a +
-           32 * 8 + 32 * 4 + 16;
+           96 * 8 + 32 * 4 + 16;
 }
 
 template <typename R, typename A>
@@ -367,8 +367,8 @@ __device__ inline Small<R, A> carve_small(unsigned char *base, int G, int varian
     s.scan = (A *)base;
     base += 16 * 8 * sizeof(A);
     s.red = (double *)base;
-    s.ired = (int *)(base + 256);
-    s.flags = (int *)(base + 256 + 128);
+    s.ired = (int *)(base + 768);
+    s.flags = (int *)(base + 768 + 128);
     return s;
 }
 
@@ -528,6 +528,7 @@ template <typename R, typename A>
 __device__ void fold_and_sort(const Frame<R> &fr, int n, const Small<R, A> &sm, const double *tt,
                               double f)
 {
+    const FoldFreq F = fold_freq(f);
     const int tid = threadIdx.x, G = blockDim.x;
     const int nb = bucket_count(n);
     const int shift = 32 - (31 - __clz(nb));
@@ -540,7 +541,7 @@ __device__ void fold_and_sort(const Frame<R> &fr, int n, const Small<R, A> &sm, 
             fr.ph[i] = ph;
             fx = __double2ull_rz(ph * 18446744073709551616.0);
         } else {
-            fx = fold_fixed64(tt[i], f);
+            fx = fold_fixed64_fast(tt[i], F);
         }
         fr.key[i] = fx;
         fr.slot[i] = (uint16_t)atomicAdd(&fr.cnt[(uint32_t)(fx >> 32) >> shift], 1u);
@@ -832,11 +833,11 @@ __device__ inline int chunk_upper(const int *cs, int G, int n, int q)
 // one point at slot p (0 <= p < n) with abscissa shift sh (-1, 0, +1)
 template <typename R, int NCH, bool DIFF>
 __device__ inline void win_add_slot(Win<R, NCH> &s, const Frame<R> &fr, const R *const *v, int p,
-                                    R sh, R o)
+                                    R sh, R o, R sgn)
 {
     const typename Vec2<R>::T xw = fr.XW[p];
     const R dx = (xw.x - o) + sh;
-    const R w = xw.y;
+    const R w = sgn * xw.y;
     const R wdx = w * dx;
     s.W += w;
     s.A += wdx;
@@ -875,11 +876,21 @@ __device__ inline void win_init_body(Win<R, NCH> &s, const Frame<R> &fr, const S
         if (seg < 0) { pa = ea + n; pb = n - 1; if (ea >= 0) continue; }
         else if (seg == 0) { pa = ea < 0 ? 0 : ea; pb = eb >= n ? n - 1 : eb; }
         else { pa = 0; pb = eb - n; if (eb < n) continue; }
-        const int ua = chunk_lower(sm.cs, G, n, pa);
-        const int ub = chunk_upper(sm.cs, G, n, pb + 1);
-        // points added one by one: [pa, pa + nl) and [pr, pr + (nt - nl))
-        int nl = pb - pa + 1, nt = nl, pr = pa;
+        int ua = chunk_lower(sm.cs, G, n, pa);
+        int ub = chunk_upper(sm.cs, G, n, pb + 1);
+        // points walked one by one: [la, la + nl) with sign sl, then
+        // [pr + nl, pr + nt) with sign sr
+        int nl = pb - pa + 1, nt = nl, pr = pa, la = pa;
+        R sl = R(1), sr = R(1);
         if (ua < ub) {
+            // Each ragged end is walked from the nearer chunk boundary: the
+            // points between the window's end and the chunk boundary inside
+            // it are added, or those between it and the boundary outside it
+            // subtracted from a whole chunk's sums, whichever are fewer.
+            const bool wide_l = ua > 0 && pa - sm.cs[ua - 1] < sm.cs[ua] - pa;
+            const bool wide_r = ub < G && sm.cs[ub + 1] - (pb + 1) < (pb + 1) - sm.cs[ub];
+            if (wide_l) { --ua; sl = R(-1); }
+            if (wide_r) { ++ub; sr = R(-1); }
             // chunks ua..ub-1 lie inside [pa, pb]
             const A w = acc_add(sm.px[0 * L + ub], acc_neg(sm.px[0 * L + ua]));
             A s1 = acc_add(sm.px[1 * L + ub], acc_neg(sm.px[1 * L + ua]));
@@ -908,12 +919,15 @@ __device__ inline void win_init_body(Win<R, NCH> &s, const Frame<R> &fr, const S
             }
             // ragged ends, both in one loop
             const int fa = sm.cs[ua], fb = sm.cs[ub];
-            nl = fa - pa;
-            nt = nl + (pb - fb + 1);
-            pr = fb - nl;
+            la = wide_l ? fa : pa;
+            nl = wide_l ? pa - fa : fa - pa;
+            const int ra = wide_r ? pb + 1 : fb;
+            nt = nl + (wide_r ? fb - (pb + 1) : pb + 1 - fb);
+            pr = ra - nl;
         }
         for (int k = 0; k < nt; ++k)
-            win_add_slot<R, NCH, DIFF>(s, fr, v, k < nl ? pa + k : pr + k, (R)seg, o);
+            win_add_slot<R, NCH, DIFF>(s, fr, v, k < nl ? la + k : pr + k, (R)seg, o,
+                                       k < nl ? sl : sr);
     }
     // about o: A = S1 - o W, B = S2 - 2 o S1 + o^2 W, D = D - o C
     const A oW = acc_mul(W, o);
@@ -1265,11 +1279,15 @@ __device__ inline void run_push(RunAvg<R, K> &ra, const Frame<R> &fr, int j, boo
 // together with the same centre; every lane returns the smooth.
 template <typename R>
 __device__ __noinline__ double sp_settle_fp64(const Frame<R> fr, const double *y64, const double *w64,
-                                              int je, int h0, int h1, int h2, int n, double vsmlsq64,
+                                              int je, int h0, int h1, int h2, int n, int qi, int qj,
                                               int sl, bool lim0, bool lim1, const double *spans,
                                               double alpha)
 {
     const uint64_t *key = fr.key;
+    // Listing 1's vsmlsq from the exact phases at the scale indices qi, qj
+    const double xqi = (double)key[qi] * 5.421010862427522e-20;
+    const double xqj = (double)key[qj] * 5.421010862427522e-20;
+    const double vsmlsq64 = 1.0e-6 * (xqj - xqi) * (xqj - xqi);
     const uint16_t *perm = fr.perm;
     const double xj = (double)key[je] * 5.421010862427522e-20;
     const int lo[3] = {win_lo(fr, je, h0, n), win_lo(fr, je, h1, n), win_lo(fr, je, h2, n)};
@@ -1331,14 +1349,128 @@ struct FreqResult {
     bool near;   // FP32C: some decision fell within its margin
 };
 
+// Per-object constants of a work item, computed once per item so that the
+// per-frequency code does no binary64 arithmetic on the FP32C path: Listing
+// 1's window half widths (binary64 expressions), the span constants, the SS
+// tweeter/midrange margin at this n, and the SP sensitivity budget.
+template <typename R>
+struct ObjK {
+    int h0, h1, h2, hs;   // half widths of the three spans, and of the fixed span
+    bool lim0, lim1;      // the tweeter's / midrange's window differs from the woofer's
+    SpanK<R> K;
+    float margin;         // SS: tweeter-vs-midrange margin
+    R sens_lim, ymax;     // SP: chi2 budget per point, largest centred magnitude
+};
+template <typename R>
+__device__ inline ObjK<R> obj_consts(const PgramArgs &a, int n, int obj)
+{
+    ObjK<R> k;
+    k.h0 = half_width(n, a.spans[0]);
+    k.h1 = half_width(n, a.spans[1]);
+    k.h2 = half_width(n, a.spans[2]);
+    k.hs = a.span > 0.0 ? half_width(n, a.span) : 0;
+    k.lim0 = k.h0 != k.h2;
+    k.lim1 = k.h1 != k.h2;
+    k.K = span_consts<R>(a.spans, a.alpha);
+    k.margin = a.near_ss * fminf(1.f, 256.f / (float)n) * fminf(1.f, 512.f / (float)n);
+    k.sens_lim = (R)(a.sens_tau * a.chi0[obj]);
+    k.ymax = (R)a.ymax[obj];
+    return k;
+}
+
+// Sum of the threads' compensated chi2 sums and OR of their near flags, valid
+// on thread 0 only (the one that stores the result).  One barrier.  FP32C
+// combines the (sum, -compensation) pairs as double-float numbers with
+// error-free additions on the FP32 pipe; thread 0 converts the total once.
+// NQ sums at once (SPG scores three spans twice).
+template <int NQ>
+__device__ inline void block_reduce0(const KSum<float> (&k)[NQ], bool near, double *red, int *ired,
+                                     double (&out)[NQ], bool &near0)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    df v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        v[q] = df{k[q].s, -k[q].c};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const df y{__shfl_xor_sync(0xffffffffu, v[q].hi, o),
+                       __shfl_xor_sync(0xffffffffu, v[q].lo, o)};
+            v[q] = acc_add(v[q], y);
+        }
+    }
+    const bool wn = __any_sync(0xffffffffu, near);
+    float2 *rf = (float2 *)red;   // 32 slots
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) rf[q * 16 + warp] = make_float2(v[q].hi, v[q].lo);
+        ired[warp] = wn ? 1 : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nr = 0;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            df t{0.f, 0.f};
+            for (int w = 0; w < nw; ++w) {
+                const float2 e = rf[q * 16 + w];
+                t = acc_add(t, df{e.x, e.y});
+            }
+            out[q] = (double)t.hi + (double)t.lo;
+        }
+        for (int w = 0; w < nw; ++w) nr |= ired[w];
+        near0 = nr != 0;
+    }
+}
+template <int NQ>
+__device__ inline void block_reduce0(const KSum<double> (&k)[NQ], bool near, double *red, int *ired,
+                                     double (&out)[NQ], bool &near0)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    double v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        v[q] = k[q].value();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    }
+    const bool wn = __any_sync(0xffffffffu, near);
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) red[q * 16 + warp] = v[q];
+        ired[warp] = wn ? 1 : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nr = 0;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += red[q * 16 + w];
+            out[q] = t;
+        }
+        for (int w = 0; w < nw; ++w) nr |= ired[w];
+        near0 = nr != 0;
+    }
+}
+template <typename R>
+__device__ inline FreqResult chi2_result(const KSum<R> &chi2, bool near, double *red, int *ired)
+{
+    const KSum<R> k[1] = {chi2};
+    double out[1] = {0.0};
+    bool n0 = false;
+    block_reduce0<1>(k, near, red, ired, out, n0);
+    return FreqResult{out[0], n0};
+}
+
 // Listing 1's fixed-span mode: one running-line smooth of y with span
 // a.span, no cross-validation, then chi2 (its own kernel variant).
 template <typename R, typename A>
-__device__ inline FreqResult fixed_span_pass(const PgramArgs &a, const Frame<R> &fr,
+__device__ inline FreqResult fixed_span_pass(const ObjK<R> &ok, const Frame<R> &fr,
                                              const Small<R, A> &sm, int n, int c0, int c1, R o,
                                              R vsmlsq, bool ties, R rf)
 {
-    const int hs = half_width(n, a.span);
+    const int hs = ok.hs;
     const R *vy[1] = {fr.Y};
     KSum<R> chi2;
     bool near = false;
@@ -1361,16 +1493,17 @@ __device__ inline FreqResult fixed_span_pass(const PgramArgs &a, const Frame<R> 
             if (j + 1 < c1) win_slide<R, 1>(w, fr, vy, j, hs, n, o);
         }
     }
-    near = __syncthreads_or(near) != 0;
-    return FreqResult{block_sum(chi2.value(), sm.red), near};
+    return chi2_result(chi2, near, sm.red, sm.ired);
 }
 
 // ---------------------------------------------------------------------------
 // one (object, frequency)
 // ---------------------------------------------------------------------------
+// The result is valid on thread 0 only.
 template <typename R, int VARIANT, bool LONG, typename A>
-__device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, int n, double f,
-                                        const Frame<R> &fr, const Small<R, A> &sm, bool reuse)
+__device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, int obj, int lead,
+                                        int n, double f, const Frame<R> &fr, const Small<R, A> &sm,
+                                        bool reuse)
 {
     const int tid = threadIdx.x, G = blockDim.x;
     const int64_t base = a.off[obj];
@@ -1459,11 +1592,9 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
     const int qi = n / 4 - 1, qj = 3 * (qi + 1) - 1;
     const R scale = fr.XW[qj].x - fr.XW[qi].x;
     const R vsmlsq = (R)1.0e-6 * scale * scale;
-    const int h0 = half_width(n, a.spans[0]);
-    const int h1 = half_width(n, a.spans[1]);
-    const int h2 = half_width(n, a.spans[2]);
-    const bool lim0 = h0 != h2, lim1 = h1 != h2;
-    const SpanK<R> K = span_consts<R>(a.spans, a.alpha);
+    const int h0 = ok.h0, h1 = ok.h1, h2 = ok.h2;
+    const bool lim0 = ok.lim0, lim1 = ok.lim1;
+    const SpanK<R> &K = ok.K;
 
     // ---- chunks: contiguous centre ranges that never split a run of ties ----
     {
@@ -1482,7 +1613,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
     const R rf = (R)a.refit_frac;
 
     if (VARIANT == VAR_FIXED)   // Listing 1's single smooth of y
-        return fixed_span_pass<R, A>(a, fr, sm, n, c0, c1, o, vsmlsq, ties, rf);
+        return fixed_span_pass<R, A>(ok, fr, sm, n, c0, c1, o, vsmlsq, ties, rf);
 
     if (VARIANT == VAR_SPG) {
         // Sec. 3, global generalized validation: three windows in one
@@ -1531,20 +1662,18 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
                 }
             }
         }
-        double G[3], X[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            G[k] = block_sum(gs[k].value(), sm.red);
-            X[k] = block_sum(xs[k].value(), sm.red);
-        }
+        const KSum<R> all[6] = {gs[0], gs[1], gs[2], xs[0], xs[1], xs[2]};
+        double tot[6] = {0, 0, 0, 0, 0, 0};
+        bool n0 = false;
+        block_reduce0<6>(all, near, sm.red, sm.ired, tot, n0);
+        // thread 0 picks the span (the result is read on thread 0 only)
         int kbest = 0;
         for (int k = 1; k < 3; ++k)
-            if (G[k] < G[kbest]) kbest = k;
+            if (tot[k] < tot[kbest]) kbest = k;
         if (sizeof(R) == 4)
             for (int k = 0; k < 3; ++k)
-                if (k != kbest && fabs(G[k] - G[kbest]) <= kNearSPG * fabs(G[kbest])) near = true;
-        near = __syncthreads_or(near) != 0;
-        return FreqResult{X[kbest], near};
+                if (k != kbest && fabs(tot[k] - tot[kbest]) <= kNearSPG * fabs(tot[kbest])) n0 = true;
+        return FreqResult{tot[3 + kbest], n0};
     }
 
     if (VARIANT == VAR_SP) {
@@ -1569,15 +1698,9 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
         const R gl2 = R(1) / (R(1) - R(2) / m2), gc2 = R(1) / (R(1) - R(1) / m2);
         const double *y64 = a.yc64 ? a.yc64 + base : nullptr;
         const double *w64 = a.wv64 ? a.wv64 + base : nullptr;
-        double vsm64 = 0.0;
-        if (sizeof(R) == 4 && y64) {
-            const double xi = (double)fr.key[qi] * 5.421010862427522e-20;
-            const double xq = (double)fr.key[qj] * 5.421010862427522e-20;
-            vsm64 = 1.0e-6 * (xq - xi) * (xq - xi);
-        }
         // a point whose bound E on its chi2 change exceeds this is refitted
-        const R sens_lim = (R)(a.sens_tau * a.chi0[obj]);
-        const R ymax = (R)a.ymax[obj];
+        const R sens_lim = ok.sens_lim;
+        const R ymax = ok.ymax;
         RunAvg<R, 1> ra;
         ra.reset(c0);
         auto emit = [&](int i, const R (&v)[1]) {
@@ -1653,7 +1776,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
                 const int je = __shfl_sync(0xffffffffu, j, src);
                 const int sl = __shfl_sync(0xffffffffu, (sl0 ? 1 : 0) | (sl1 ? 2 : 0) | (sl2 ? 4 : 0),
                                            src);
-                const double v = sp_settle_fp64<R>(fr, y64, w64, je, h0, h1, h2, n, vsm64, sl, lim0,
+                const double v = sp_settle_fp64<R>(fr, y64, w64, je, h0, h1, h2, n, qi, qj, sl, lim0,
                                                    lim1, a.spans, a.alpha);
                 if (lane == src) val[0] = (R)v;
             }
@@ -1666,8 +1789,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
                 }
             }
         }
-        near = __syncthreads_or(near) != 0;
-        return FreqResult{block_sum(chi2.value(), sm.red), near};
+        return chi2_result(chi2, near, sm.red, sm.ired);
     }
 
     // ===== SS, Listing 1 =====
@@ -1726,7 +1848,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
         constexpr bool DIFF = sizeof(R) == 4;
         constexpr int NB = DIFF ? 4 : 3;
         const R *vr[3] = {fr.C[1], fr.C[3], fr.C[5]};
-        const float margin = a.near_ss * fminf(1.f, 256.f / (float)n) * fminf(1.f, 512.f / (float)n);
+        const float margin = ok.margin;
         // resolves the -1 residuals of pass A while it sums them
         build_channel_prefix<R, NB, DIFF, true>(fr, sm, vr, c0, c1, o);
         __syncthreads();
@@ -1803,8 +1925,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, int obj, int lead, i
             }
         }
     }
-    near = __syncthreads_or(near) != 0;
-    return FreqResult{block_sum(chi2.value(), sm.red), near};
+    return chi2_result(chi2, near, sm.red, sm.ired);
 }
 
 // ---------------------------------------------------------------------------
@@ -1838,6 +1959,7 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
         const int m = SHARED && item.w > 1 ? item.w : 1;
         const int n = (int)(a.off[o + 1] - a.off[o]);
         Frame<R> fr = carve_frame<R>(big, n, VARIANT, SHARED);
+        ObjK<R> ok = obj_consts<R>(a, n, o);
         fr.per = PER;
         // a frame in global memory still counts its sort buckets in shared
         // memory: the counting pass is one atomic per point
@@ -1849,18 +1971,22 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
                 const int64_t at = (int64_t)obj * a.n_freq + q;
                 const bool bad = a.bad[obj] != 0;
                 if (a.recompute && (bad || a.near[at] == 0)) continue;   // block-uniform
-                double pw;
+                double pw = 0.0;
                 bool near = false;
                 if (bad) {
                     pw = __longlong_as_double(0x7ff8000000000000LL);
                 } else {
+                    if (SHARED && k > 0) ok = obj_consts<R>(a, n, obj);
                     const double fq = a.freq[(a.fbase ? a.fbase[o] : 0) + q];
-                    const FreqResult r =
-                        process_frequency<R, VARIANT, LONG>(a, obj, o, n, fq, fr, sm, SHARED && sorted);
+                    const FreqResult r = process_frequency<R, VARIANT, LONG>(a, ok, obj, o, n, fq, fr,
+                                                                             sm, SHARED && sorted);
                     sorted = true;
-                    const double c0 = a.chi0[obj];
-                    pw = (c0 > 0.0) ? 1.0 - r.chi2 / c0 : 0.0;
-                    near = r.near;
+                    // the result is valid on thread 0, the one that stores it
+                    if (threadIdx.x == 0) {
+                        const double c0 = a.chi0[obj];
+                        pw = (c0 > 0.0) ? 1.0 - r.chi2 / c0 : 0.0;
+                        near = r.near;
+                    }
                 }
                 if (threadIdx.x == 0) {
                     if (a.power_f32) ((float *)a.power)[at] = (float)pw;

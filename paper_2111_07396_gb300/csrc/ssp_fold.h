@@ -112,4 +112,57 @@ SSP_HD inline uint64_t fold_fixed64(double tt, double f)
     return frac >> (-up);
 }
 
+
+// The trial frequency's part of the fold, taken apart once per frequency.
+struct FoldFreq {
+    double f;
+    uint64_t mf;   // 53-bit significand with its leading bit
+    int ef;        // biased exponent; 0 (a subnormal f) takes the general path
+};
+
+SSP_HD inline FoldFreq fold_freq(double f)
+{
+    const uint64_t bf = dbl_bits(f);
+    FoldFreq r;
+    r.f = f;
+    r.ef = (int)((bf >> 52) & 0x7ff);
+    r.mf = (bf & 0xfffffffffffffull) | (1ull << 52);
+    return r;
+}
+
+// fold_fixed64 for a normal tt and a normal f with no data-dependent
+// branches on the common path: both significands carry their leading bit, so
+// the exact product lies in [2^104, 2^106) and the rounding point is one of
+// two fixed bit positions.  The 64-bit fixed-point fraction of m 2^q is then
+// (m 2^(q+64)) mod 2^64: the integer part shifts out.  Returns exactly what
+// fold_fixed64 returns (zero and subnormal operands go through it).
+SSP_HD inline uint64_t fold_fixed64_fast(double tt, const FoldFreq &F)
+{
+    const uint64_t bt = dbl_bits(tt);
+    const int et = (int)(bt >> 52);   // tt >= 0: the sign bit is clear
+    if (et == 0 || F.ef == 0) return bt == 0 ? 0 : fold_fixed64(tt, F.f);
+    const uint64_t mt = (bt & 0xfffffffffffffull) | (1ull << 52);
+    const uint64_t lo = mt * F.mf, hi = mulhi64(mt, F.mf);
+    const int top = (int)(hi >> 41);   // bit 105 of the product
+    const int sh = 52 + top;           // significant bits below the kept 53
+    int q = et + F.ef - 2150;          // product = (hi:lo) 2^q
+    if (q + sh + 53 <= -64) return 0;  // product below 2^-64
+    uint64_t m = top ? ((hi << 11) | (lo >> 53)) : ((hi << 12) | (lo >> 52));
+    const uint64_t g = top ? (1ull << 52) : (1ull << 51);
+    const bool guard = (lo & g) != 0, sticky = (lo & (g - 1)) != 0;
+    q += sh;
+    if (guard && (sticky || (m & 1))) {
+        ++m;
+        if (m == (1ull << 53)) {
+            m >>= 1;
+            ++q;
+        }
+    }
+    const int s = q + 64;
+    if (s >= 64) return 0;
+    if (s >= 0) return m << s;
+    if (s <= -64) return 0;
+    return m >> (-s);
+}
+
 }  // namespace ssp
