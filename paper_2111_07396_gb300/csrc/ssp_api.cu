@@ -43,11 +43,11 @@ cudaError_t pgram_launch_fp64_shared(int, bool, bool, int, int, size_t, const Pg
 cudaError_t pgram_occupancy_redo_shared(int, bool, bool, int, size_t, int *);
 cudaError_t pgram_launch_redo_shared(int, bool, bool, int, int, size_t, const PgramArgs &, cudaStream_t);
 size_t pgram_small_bytes_fp32(int, int);
-size_t pgram_frame_bytes_fp32(int, int, bool);
+size_t pgram_frame_bytes_fp32(int, int, bool, bool);
 size_t pgram_small_bytes_fp64(int, int);
-size_t pgram_frame_bytes_fp64(int, int, bool);
+size_t pgram_frame_bytes_fp64(int, int, bool, bool);
 size_t pgram_small_bytes_redo(int, int);
-size_t pgram_frame_bytes_redo(int, int, bool);
+size_t pgram_frame_bytes_redo(int, int, bool, bool);
 
 cudaError_t prep_launch(int p, const PrepArgs &a, int n, cudaStream_t s)
 {
@@ -97,11 +97,11 @@ size_t pgram_small_bytes(int p, int G, int variant)
          : p == kPrecRedo ? pgram_small_bytes_redo(G, variant)
                           : pgram_small_bytes_fp32(G, variant);
 }
-size_t pgram_frame_bytes(int p, int n, int variant, bool keep_perm)
+size_t pgram_frame_bytes(int p, int n, int variant, bool keep_perm, bool smo_out)
 {
-    return p == SSP_FP64 ? pgram_frame_bytes_fp64(n, variant, keep_perm)
-         : p == kPrecRedo ? pgram_frame_bytes_redo(n, variant, keep_perm)
-                          : pgram_frame_bytes_fp32(n, variant, keep_perm);
+    return p == SSP_FP64 ? pgram_frame_bytes_fp64(n, variant, keep_perm, smo_out)
+         : p == kPrecRedo ? pgram_frame_bytes_redo(n, variant, keep_perm, smo_out)
+                          : pgram_frame_bytes_fp32(n, variant, keep_perm, smo_out);
 }
 }  // namespace ssp
 
@@ -175,9 +175,10 @@ int check_shape(const int64_t *n_per_object, int64_t n_objects, int64_t n_freq, 
 // Objects are planned in length ranges; the objects of one range share a
 // launch.  Threads per CTA by default: about a dozen centres per thread
 // (SSP_GROUP_SCALE, a power of two, scales the rule for calibration).  FP32C
-// SS objects above 2048 points take 512 threads: their frame leaves room for
-// one CTA per SM, and 16 warps hide more latency than 8 (the FP64 kernel,
-// bound by its FP64 pipe, runs slower that way).  ssp_autotune
+// SS objects above 2048 points take 256 threads when pass A's smooths live
+// in the global slab (their frame then leaves room for two CTAs per SM), and
+// 512 otherwise (one CTA per SM: 16 warps hide more latency than 8; the FP64
+// kernel, bound by its FP64 pipe, runs slower that way).  ssp_autotune
 // replaces the rule per (precision, variant, range) with measured choices.
 constexpr int kRanges = 5;
 constexpr int kRangeMax[kRanges] = {384, 768, 1536, 2048, 65535};
@@ -190,7 +191,7 @@ int range_of(int n)
     return kRanges - 1;
 }
 
-int group_size_rule(int n, int variant, int precision)
+int group_size_rule(int n, int variant, int precision, bool smo_ok = true)
 {
     static const int scale = [] {
         const char *e = std::getenv("SSP_GROUP_SCALE");
@@ -201,7 +202,7 @@ int group_size_rule(int n, int variant, int precision)
     if (n <= 384) g = 32;
     else if (n <= 768) g = 64;
     else if (n <= 1536) g = 128;
-    else if (variant == SSP_SS && precision == SSP_FP32C && n > 2048) g = 512;
+    else if (variant == SSP_SS && precision == SSP_FP32C && n > 2048) g = smo_ok ? 256 : 512;
     else g = 256;
     if (scale > 1) g = std::min(512, g * scale);
     if (scale < 0) g = std::max(32, g / -scale);
@@ -216,22 +217,24 @@ int kernel_variant(ssp_variant v, const ssp_params &P)
     return v == SSP_SS ? VAR_SS : v == SSP_SP ? VAR_SP : VAR_SPG;
 }
 
-int group_size(int n, int variant, int precision)
+int group_size(int n, int variant, int precision, bool smo_ok = true)
 {
     const int t = g_tuned[precision == SSP_FP64 ? 0 : 1][variant][range_of(n)].load();
-    return t ? t : group_size_rule(n, variant, precision);
+    return t ? t : group_size_rule(n, variant, precision, smo_ok);
 }
 
 struct LaunchCfg {
     bool gmem = false;
     bool cnt_smem = false;   // gmem: the sort's bucket counts in shared memory
     bool lng = false;        // SS kernel that initialises windows out of line
-    size_t smem = 0, slab_bytes = 0;
+    bool smo_out = false;    // SS: pass A's smooths in the global slab
+    size_t smem = 0, slab_bytes = 0, smo_stride = 0;
     int grid = 0;
 };
 
 struct Bucket {
     int G = 32, n_max = 0;
+    int G_redo = 32;        // threads per CTA of the FP64 recompute launch
     bool shared = false;    // some item covers several objects with identical times
     LaunchCfg main, redo;   // redo: FP64 recompute of flagged FP32C frequencies
     std::vector<int> objects;
@@ -240,7 +243,7 @@ struct Bucket {
 
 struct Plan {
     std::vector<Bucket> buckets;
-    size_t items_total = 0, slab_total = 0;
+    size_t items_total = 0, slab_total = 0, smo_total = 0;
     bool redo = false;
 };
 
@@ -257,10 +260,18 @@ int device_limits(int *num_sms, size_t *max_smem)
 
 // frame placement and persistent grid of one kernel for one bucket
 int configure(int precision, int variant, bool per, bool shared, int G, int n_max, int sms,
-              size_t max_smem, LaunchCfg &c)
+              size_t max_smem, LaunchCfg &c, bool smo_ok = true)
 {
+    // FP32C SS objects of many points keep pass A's smooths in the global slab
+    // (coalesced), which shrinks their frame by 12 bytes a point.  Only the
+    // kernels built for long objects (LONG: periodic windows, shared or not)
+    // address the slab; the frame layout here and in the kernel must agree.
+    const bool long_kernel = variant == VAR_SS && precision == SSP_FP32C && n_max > kLongN &&
+                             (per || shared);
+    c.smo_out = smo_ok && long_kernel;
+    c.smo_stride = c.smo_out ? align16(smo_bytes(n_max, G, 4)) : 0;
     const size_t small = align16(pgram_small_bytes(precision, G, variant));
-    const size_t frame = align16(pgram_frame_bytes(precision, n_max, variant, shared));
+    const size_t frame = align16(pgram_frame_bytes(precision, n_max, variant, shared, c.smo_out));
     c.gmem = small + frame + 1024 > max_smem;
     // a single-sweep frame in global memory keeps its sort's bucket counts in
     // shared memory where they fit (C4 SP: 9% faster).  SS does not: its
@@ -287,7 +298,7 @@ int configure(int precision, int variant, bool per, bool shared, int G, int n_ma
 // group (host, or null): group[o] = number of objects o, o+1, ... that share
 // object o's times when o leads such a run, 0 for the run's other objects
 int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision, int variant,
-               bool per, Plan &plan, const int *group = nullptr)
+               bool per, Plan &plan, const int *group = nullptr, bool smo_ok = true)
 {
     int sms = 0;
     size_t max_smem = 0;
@@ -304,16 +315,29 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
                 if (group && group[o] > 1) b.shared = true;
             }
         if (b.objects.empty()) continue;
-        b.G = group_size(b.n_max, variant, precision);
+        // (the smooth slab exists only for periodic windows: see configure)
+        const bool slab_ok = smo_ok && (per || b.shared);
+        b.G = group_size(b.n_max, variant, precision, slab_ok);
+        if (b.G == 256 && slab_ok && variant == VAR_SS && precision == SSP_FP32C && b.n_max > 2048 &&
+            !g_tuned[1][variant][range_of(b.n_max)].load()) {
+            // 256 threads only where two CTAs of them fit an SM's shared memory
+            // with the smooths in the global slab; otherwise 512 (one CTA)
+            const size_t need = align16(pgram_small_bytes(precision, 256, variant)) +
+                                align16(pgram_frame_bytes(precision, b.n_max, variant, b.shared, true)) +
+                                1024;
+            if (2 * need > max_smem + 1024) b.G = 512;
+        }
         plan.buckets.push_back(std::move(b));
     }
     plan.items_total = 0;
     plan.slab_total = 0;
+    plan.smo_total = 0;
     for (Bucket &b : plan.buckets) {
-        rc = configure(precision, variant, per, b.shared, b.G, b.n_max, sms, max_smem, b.main);
+        rc = configure(precision, variant, per, b.shared, b.G, b.n_max, sms, max_smem, b.main, smo_ok);
         if (rc) return rc;
         if (plan.redo) {
-            rc = configure(kPrecRedo, variant, per, b.shared, b.G, b.n_max, sms, max_smem, b.redo);
+            b.G_redo = b.G;
+            rc = configure(kPrecRedo, variant, per, b.shared, b.G_redo, b.n_max, sms, max_smem, b.redo);
             if (rc) return rc;
         }
         const int resident = b.main.grid;
@@ -338,6 +362,7 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
         b.redo.grid = (int)std::min<int64_t>((int64_t)b.items.size(), b.redo.grid);
         plan.items_total += b.items.size();
         plan.slab_total += b.main.gmem ? b.main.slab_bytes * (size_t)b.main.grid : 0;
+        plan.smo_total += b.main.smo_stride * (size_t)b.main.grid;
         if (plan.redo && b.redo.gmem) plan.slab_total += b.redo.slab_bytes * (size_t)b.redo.grid;
     }
     return SSP_OK;
@@ -367,13 +392,14 @@ size_t workspace_bytes(const Plan &plan, int64_t n_obj, int64_t n_points, int64_
     b += align16(8 * (size_t)n_points);                     // tt
     b += align16(4 * (size_t)n_obj);                        // bad
     b += align16(rsize(precision) * (size_t)n_points) * 2;  // yc, wv
-    if (plan.redo) b += align16(8 * (size_t)n_points) * 2;  // FP64 copies
+    if (plan.redo) b += align16(8 * (size_t)n_points) * 4;  // FP64 copies, double-float pairs
     b += align16(8 * (size_t)n_obj);                        // chi0
     b += align16(8 * (size_t)n_obj);                        // ymax
     b += align16(sizeof(int4) * plan.items_total);
     b += align16(8 * plan.buckets.size() + 8);              // two counters per bucket
     if (plan.redo) b += align16((size_t)n_obj * (size_t)n_freq);  // near flags
     b += plan.slab_total;
+    b += plan.smo_total;
     return b;
 }
 
@@ -536,6 +562,8 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
     void *d_wv = take(rsize(prec) * (size_t)N);
     double *d_yc64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
     double *d_wv64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
+    float2 *d_ydf = plan.redo ? (float2 *)take(8 * (size_t)N) : nullptr;
+    float2 *d_wdf = plan.redo ? (float2 *)take(8 * (size_t)N) : nullptr;
     double *d_chi0 = (double *)take(8 * (size_t)n_obj);
     double *d_ymax = (double *)take(8 * (size_t)n_obj);
     int4 *d_items = (int4 *)take(sizeof(int4) * plan.items_total);
@@ -566,6 +594,8 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
         pa.wv = d_wv;
         pa.yc64 = d_yc64;
         pa.wv64 = d_wv64;
+        pa.ydf = d_ydf;
+        pa.wdf = d_wdf;
         pa.chi0 = d_chi0;
         pa.ymax = d_ymax;
         pa.bad = d_bad;
@@ -573,7 +603,7 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
         bool on = prof_begin(SSP_PHASE_PREP, s, mk);
         if ((e = prep_launch(prec, pa, (int)n_obj, s))) break;
         prof_end(on, mk, s);
-        size_t item_base = 0, slab_cur = 0;
+        size_t item_base = 0, slab_cur = 0, smo_cur = 0;
         for (size_t k = 0; k < plan.buckets.size(); ++k) {
             const Bucket &b = plan.buckets[k];
             PgramArgs ga{};
@@ -585,6 +615,8 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
             ga.ymax = d_ymax;
             ga.yc64 = d_yc64;
             ga.wv64 = d_wv64;
+            ga.ydf = d_ydf;
+            ga.wdf = d_wdf;
             ga.bad = d_bad;
             ga.freq = freq;
             ga.n_freq = n_freq;
@@ -596,6 +628,11 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
             for (int i = 0; i < 3; ++i) ga.spans[i] = P.spans[i];
             ga.alpha = P.alpha;
             ga.slab = b.main.gmem ? d_slab + slab_cur : nullptr;
+            ga.smo = b.main.smo_out ? d_slab + plan.slab_total + smo_cur : nullptr;
+            ga.smo_stride = b.main.smo_stride;
+            ga.smo_kmax = smo_rows(b.n_max, b.G);
+            ga.smo_nmax = b.n_max;
+            smo_cur += b.main.smo_stride * (size_t)b.main.grid;
             ga.slab_bytes = b.main.slab_bytes;
             ga.cnt_smem = b.main.cnt_smem ? 1 : 0;
             ga.near = d_near;
@@ -621,13 +658,14 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
                 ga.wv = d_wv64;
                 ga.item_counter = d_counters + 2 * k + 1;
                 ga.slab = b.redo.gmem ? d_slab + slab_cur : nullptr;
+                ga.smo = nullptr;
                 ga.slab_bytes = b.redo.slab_bytes;
                 ga.cnt_smem = b.redo.cnt_smem ? 1 : 0;
                 ga.recompute = 1;
                 slab_cur += b.redo.gmem ? b.redo.slab_bytes * (size_t)b.redo.grid : 0;
                 on = prof_begin(SSP_PHASE_REDO, s, mk);
-                if ((e = pgram_launch(kPrecRedo, kv, b.redo.gmem, b.redo.lng, per, b.shared, b.redo.grid, b.G,
-                                      b.redo.smem, ga, s)))
+                if ((e = pgram_launch(kPrecRedo, kv, b.redo.gmem, b.redo.lng, per, b.shared, b.redo.grid,
+                                      b.G_redo, b.redo.smem, ga, s)))
                     break;
                 prof_end(on, mk, s);
             }
@@ -690,7 +728,7 @@ int run_device_noalloc(const double *t, const double *y, const double *dy, const
     Plan plan;
     const int kv = kernel_variant(variant, P);
     const bool per = P.periodic != 0;
-    int rc = build_plan(npo, n_obj, n_freq, prec, kv, per, plan);
+    int rc = build_plan(npo, n_obj, n_freq, prec, kv, per, plan, nullptr, false);
     if (rc) return rc;
     for (const Bucket &b : plan.buckets)
         if (b.main.gmem || (plan.redo && b.redo.gmem))
@@ -723,6 +761,8 @@ int run_device_noalloc(const double *t, const double *y, const double *dy, const
     void *d_wv = take(rsize(prec) * (size_t)N);
     double *d_yc64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
     double *d_wv64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
+    float2 *d_ydf = plan.redo ? (float2 *)take(8 * (size_t)N) : nullptr;
+    float2 *d_wdf = plan.redo ? (float2 *)take(8 * (size_t)N) : nullptr;
     double *d_chi0 = (double *)take(8 * (size_t)n_obj);
     double *d_ymax = (double *)take(8 * (size_t)n_obj);
     int4 *d_items = (int4 *)take(sizeof(int4) * plan.items_total);
@@ -753,6 +793,8 @@ int run_device_noalloc(const double *t, const double *y, const double *dy, const
         pa.wv = d_wv;
         pa.yc64 = d_yc64;
         pa.wv64 = d_wv64;
+        pa.ydf = d_ydf;
+        pa.wdf = d_wdf;
         pa.chi0 = d_chi0;
         pa.ymax = d_ymax;
         pa.bad = d_bad;
@@ -769,6 +811,8 @@ int run_device_noalloc(const double *t, const double *y, const double *dy, const
             ga.ymax = d_ymax;
             ga.yc64 = d_yc64;
             ga.wv64 = d_wv64;
+            ga.ydf = d_ydf;
+            ga.wdf = d_wdf;
             ga.bad = d_bad;
             ga.freq = freq;
             ga.n_freq = n_freq;
@@ -795,7 +839,7 @@ int run_device_noalloc(const double *t, const double *y, const double *dy, const
                 ga.wv = d_wv64;
                 ga.item_counter = d_counters + 2 * k + 1;
                 ga.recompute = 1;
-                if ((e = pgram_launch(kPrecRedo, kv, false, b.redo.lng, per, false, b.redo.grid, b.G, b.redo.smem,
+                if ((e = pgram_launch(kPrecRedo, kv, false, b.redo.lng, per, false, b.redo.grid, b.G_redo, b.redo.smem,
                                       ga, s)))
                     break;
             }

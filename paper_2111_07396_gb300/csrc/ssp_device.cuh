@@ -53,8 +53,9 @@ constexpr int kBucketRankMax = 64;   // larger buckets switch to the bitonic sor
 // generalized-validation residuals are closer than kNearSP * eps_fp32 times
 // the magnitude scale (the larger of the point's and the object's largest
 // centred magnitude), and the other choice could move the power by more than
-// kSensTau, the warp refits the three span windows in binary64 from the exact
-// phases and binary64 inputs and takes the choice from those.
+// kSensTau, the warp refits the three span windows beyond FP32 precision
+// (double-float sums of exact products) from the exact phases and the inputs
+// split into double-float pairs, and takes the choice from those in binary64.
 constexpr float kNearSS = 1e-6f;
 constexpr float kNearSP = 64.f;
 constexpr float kNearLev = 1e-4f;
@@ -68,8 +69,8 @@ constexpr int kLongN = 1536;
 // SP: a point whose fit could move the power by more than kSensTau through
 // the FP32 error of its residuals (bass enhancement divides by the smallest;
 // each residual is taken to err by its slope times the rounding of X plus
-// kSensUlps ulps of its magnitude scale) is settled by the warp's binary64
-// refit as well
+// kSensUlps ulps of its magnitude scale) is settled by the warp's refit as
+// well
 constexpr double kSensTau = 1e-6;
 constexpr float kSensUlps = 2.f;
 
@@ -81,6 +82,7 @@ struct PgramArgs {
     const double *chi0;     // [n_obj]
     const double *ymax;     // [n_obj] largest centred magnitude
     const double *yc64, *wv64;  // [N] binary64 inputs (FP32C: exact SP refits)
+    const float2 *ydf, *wdf;    // [N] the same as double-float pairs (hi, lo) (FP32C)
     const int *bad;         // [n_obj] nonzero: invalid input, NaN output
     const double *freq;     // [n_freq]
     int64_t n_freq;
@@ -104,7 +106,23 @@ struct PgramArgs {
     float refit_frac;       // refit windows whose spread fell below this part of hiB
     float sens_ulps;        // SP sensitivity: rounding of a residual, in ulps of its scale
     double sens_tau;        // SP sensitivity: power budget per point
+    // SS: the three smooths of pass A, read back only at their own centre in
+    // pass C, live in a per-CTA global slab instead of the frame (null: in
+    // the frame).  Layout per CTA: [column][k][thread] for the k-th centre of
+    // a thread's chunk while k < smo_kmax (a warp's accesses are adjacent),
+    // then [column][point] for the centres of longer chunks.
+    void *smo;
+    size_t smo_stride;      // bytes per CTA
+    int smo_kmax, smo_nmax;
 };
+
+// rows of the smooth slab's per-thread part: twice the mean chunk length
+// plus slack (chunks grow past the mean only over runs of tied phases)
+__host__ __device__ inline int smo_rows(int n, int G) { return 2 * ((n + G - 1) / G) + 4; }
+__host__ __device__ inline size_t smo_bytes(int n, int G, size_t rsize)
+{
+    return 3 * ((size_t)smo_rows(n, G) * (size_t)G + (size_t)n) * rsize;
+}
 
 // ---------------------------------------------------------------------------
 // frame layout (per CTA, sized for the largest n of a launch)
@@ -204,23 +222,28 @@ __host__ __device__ inline size_t tie_offset(int n, int ncols)
     return cols > s ? cols : s;
 }
 
-// columns a variant keeps: SS uses XW (two columns), Y and C0..C6; SP only XW, Y
-__host__ __device__ inline int frame_cols(int variant) { return variant == VAR_SS ? 10 : 3; }
+// columns a variant keeps: SS uses XW (two columns), Y and C0..C6 (C1, C3, C5,
+// C6 only when the smooths C0, C2, C4 live in the global slab); SP only XW, Y
+__host__ __device__ inline int frame_cols(int variant, bool smo_out = false)
+{
+    return variant == VAR_SS ? (smo_out ? 7 : 10) : 3;
+}
 
 // keep_perm: objects with identical times share one sort (their frame keeps
 // perm for every member's gather); an SS frame then holds perm past the tie
 // bitmask, clear of the smoother columns that overlay the sort region
 template <typename R>
-__host__ __device__ inline size_t frame_bytes(int n, int variant, bool keep_perm = false)
+__host__ __device__ inline size_t frame_bytes(int n, int variant, bool keep_perm = false,
+                                              bool smo_out = false)
 {
-    size_t b = tie_offset<R>(n, frame_cols(variant)) + align16(4 * tie_words(n));
+    size_t b = tie_offset<R>(n, frame_cols(variant, smo_out)) + align16(4 * tie_words(n));
     if (keep_perm && variant == VAR_SS) b += align16(2 * (size_t)pow2_at_least(n));
     return b;
 }
 
 template <typename R>
 __device__ inline Frame<R> carve_frame(unsigned char *base, int n, int variant,
-                                       bool keep_perm = false)
+                                       bool keep_perm = false, bool smo_out = false)
 {
     Frame<R> f;
     const size_t col = align16(sizeof(R) * (size_t)n), xwy = xwy_bytes<R>(n);
@@ -231,15 +254,21 @@ __device__ inline Frame<R> carve_frame(unsigned char *base, int n, int variant,
     f.sk = (uint64_t *)base;   // 8n bytes <= 2 a4
     f.slot = (uint16_t *)(base + 2 * a4);
     f.tmp = (uint16_t *)(base + 2 * a4 + a2);
-    for (int k = 0; k < 7; ++k) f.C[k] = (R *)(base + xwy + k * col);
+    if (smo_out && variant == VAR_SS) {
+        // C1, C3, C5, C6 in the frame; the smooths C0, C2, C4 in the slab
+        const int slot[7] = {-1, 0, -1, 1, -1, 2, 3};
+        for (int k = 0; k < 7; ++k) f.C[k] = slot[k] < 0 ? nullptr : (R *)(base + xwy + slot[k] * col);
+    } else {
+        for (int k = 0; k < 7; ++k) f.C[k] = (R *)(base + xwy + k * col);
+    }
     unsigned char *s = base + xwy;
     f.key = (uint64_t *)s;     // 8n bytes <= 2 a4
     f.perm = (uint16_t *)(s + 2 * a4);
     f.cnt = (uint32_t *)(s + 2 * a4 + ap);
     f.ph = (double *)(s + 2 * a4 + ap + align16(4 * (size_t)bucket_count(n)));
-    f.tie = (uint32_t *)(base + tie_offset<R>(n, frame_cols(variant)));
+    f.tie = (uint32_t *)(base + tie_offset<R>(n, frame_cols(variant, smo_out)));
     if (keep_perm && variant == VAR_SS)
-        f.perm = (uint16_t *)(base + tie_offset<R>(n, frame_cols(variant)) +
+        f.perm = (uint16_t *)(base + tie_offset<R>(n, frame_cols(variant, smo_out)) +
                               align16(4 * tie_words(n)));
     f.per = 1;
     return f;
@@ -296,6 +325,16 @@ __device__ inline xacc<T> acc_shfl_up(xacc<T> x, int k)
 {
     return xacc<T>{__shfl_up_sync(0xffffffffu, x.hi, k), __shfl_up_sync(0xffffffffu, x.lo, k)};
 }
+template <typename T>
+__device__ inline xacc<T> acc_shfl_xor(xacc<T> x, int k)
+{
+    return xacc<T>{__shfl_xor_sync(0xffffffffu, x.hi, k), __shfl_xor_sync(0xffffffffu, x.lo, k)};
+}
+template <typename T>
+__device__ inline xacc<T> acc_shfl_idx(xacc<T> x, int k)
+{
+    return xacc<T>{__shfl_sync(0xffffffffu, x.hi, k), __shfl_sync(0xffffffffu, x.lo, k)};
+}
 
 // plain accumulator (the FP64 recompute of flagged FP32C frequencies, whose
 // results only have to meet the FP32C tolerance)
@@ -304,6 +343,8 @@ __device__ inline double acc_neg(double x) { return -x; }
 __device__ inline double acc_mul(double x, double b) { return x * b; }
 __device__ inline double acc_to(double x) { return x; }
 __device__ inline double acc_shfl_up(double x, int k) { return __shfl_up_sync(0xffffffffu, x, k); }
+__device__ inline double acc_shfl_xor(double x, int k) { return __shfl_xor_sync(0xffffffffu, x, k); }
+__device__ inline double acc_shfl_idx(double x, int k) { return __shfl_sync(0xffffffffu, x, k); }
 
 // smallest window B / total weight whose prefix-based sums keep the accuracy
 // stated in win_init
@@ -677,10 +718,62 @@ __device__ inline void win_add(Win<R, NCH> &s, const Frame<R> &fr, const R *cons
 
 // Exclusive block-wide scan of Q accumulator values per thread (one entry per
 // chunk): out[q][t] = sum over threads < t, out[q][G] = total.  Warps scan
-// with shuffles; warp 0 then scans the warp totals, so no thread adds more
-// than log2(warps) of them.  The caller synchronises before reading out.
+// with shuffles and publish their totals; after one barrier every warp sums
+// the totals of the warps before it itself (a shuffle reduction over at most
+// 16 lanes), so no warp waits on a serial second-level scan.  The caller
+// synchronises before reading out, and that barrier also orders this scan's
+// reads of scratch before the next scan's writes.
 template <typename A, int Q>
 __device__ void block_scan_store(A (&v)[Q], A *const (&out)[Q], A *scratch)
+{
+    typedef typename R_of<A>::type T;
+    const int G = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = G >> 5;
+#pragma unroll
+    for (int k = 1; k < 32; k <<= 1) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const A y = acc_shfl_up(v[q], k);
+            if (lane >= k) v[q] = acc_add(v[q], y);
+        }
+    }
+    A ex[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        ex[q] = acc_shfl_up(v[q], 1);
+        if (lane == 0) ex[q] = acc_from<A>(T(0));
+    }
+    if (nw == 1) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            out[q][tid] = ex[q];
+            if (lane == 31) out[q][G] = v[q];
+        }
+        return;
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) scratch[warp * 8 + q] = v[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        // offset of this warp: the totals of warps 0 .. warp-1, summed over
+        // lanes 0 .. nw-1 (nw is a power of two, so the butterflies below
+        // never mix in lanes >= nw)
+        A b = lane < warp ? scratch[lane * 8 + q] : acc_from<A>(T(0));
+        for (int k = 1; k < nw; k <<= 1) b = acc_add(b, acc_shfl_xor(b, k));
+        b = acc_shfl_idx(b, 0);
+        out[q][tid] = acc_add(b, ex[q]);
+        if (tid == G - 1) out[q][G] = acc_add(b, v[q]);
+    }
+}
+
+// The same scan with warp 0 scanning the warp totals between two barriers:
+// more waiting, but fewer registers live across the barriers, which the SS
+// kernels for short objects (few warps per CTA) need to keep their occupancy.
+template <typename A, int Q>
+__device__ void block_scan_store_serial(A (&v)[Q], A *const (&out)[Q], A *scratch)
 {
     typedef typename R_of<A>::type T;
     const int G = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -734,7 +827,7 @@ __device__ void block_scan_store(A (&v)[Q], A *const (&out)[Q], A *scratch)
 
 // x-moment prefixes of the chunks together with the prefixes of one channel
 // (sum w v, sum w x v), all about 0
-template <typename R, typename A>
+template <typename R, bool SERIAL = false, typename A>
 __device__ void build_xy_prefix(const Frame<R> &fr, const Small<R, A> &sm, const R *vy, int c0,
                                 int c1, R o)
 {
@@ -758,7 +851,8 @@ __device__ void build_xy_prefix(const Frame<R> &fr, const Small<R, A> &sm, const
     v[3] = acc_from<A>(sc);
     v[4] = acc_add(acc_from<A>(sd), acc_mul(acc_from<A>(sc), o));
     A *const out[5] = {sm.px, sm.px + L, sm.px + 2 * L, sm.pc, sm.pc + L};
-    block_scan_store<A, 5>(v, out, sm.scan);
+    if (SERIAL) block_scan_store_serial<A, 5>(v, out, sm.scan);
+    else block_scan_store<A, 5>(v, out, sm.scan);
 }
 
 // channel prefixes of the chunks (each later pass).  With FIX, a stored
@@ -767,7 +861,7 @@ __device__ void build_xy_prefix(const Frame<R> &fr, const Small<R, A> &sm, const
 // does; a value read from a neighbouring chunk while its owner resolves it is
 // either still negative (the walk goes on) or already the value the walk
 // would find.
-template <typename R, int NCH, bool DIFF = false, bool FIX = false, typename A>
+template <typename R, int NCH, bool DIFF = false, bool FIX = false, bool SERIAL = false, typename A>
 __device__ void build_channel_prefix(const Frame<R> &fr, const Small<R, A> &sm, const R *const *vv,
                                      int c0, int c1, R o)
 {
@@ -808,7 +902,8 @@ __device__ void build_channel_prefix(const Frame<R> &fr, const Small<R, A> &sm, 
     A *out[2 * NCH];
 #pragma unroll
     for (int q = 0; q < 2 * NCH; ++q) out[q] = sm.pc + q * L;
-    block_scan_store<A, 2 * NCH>(v, out, sm.scan);
+    if (SERIAL) block_scan_store_serial<A, 2 * NCH>(v, out, sm.scan);
+    else block_scan_store<A, 2 * NCH>(v, out, sm.scan);
 }
 
 // Chunk u starts at cs[u] = floor(u n / G), moved forward past a run of ties
@@ -1265,31 +1360,73 @@ __device__ inline void run_push(RunAvg<R, K> &ra, const Frame<R> &fr, int j, boo
 }
 
 
-// Settles one contested SP centre je in binary64: the line fits of its three
-// span windows from exact phases (the sorted 64-bit fixed-point keys) and
-// binary64 magnitudes and weights read through perm, then the span choice and
-// interpolation.  The windows share their centre and nest (h0 <= h1 <= h2,
-// periodic or clamped), so each point is loaded and summed once: into the
-// tweeter window, or the ring the midrange window adds around it, or the
-// woofer's ring around that (each ring's two segments in one walk); the wider
-// windows' sums are running totals.  sl: bit k set when span k's fit kept its
-// slope, which picks the validation factor as in the FP32 choice.
-// The code runs rarely, from a cold instruction cache, so it is out of line and
-// written once per step (only the walk is unrolled).  All lanes of the warp call it
-// together with the same centre; every lane returns the smooth.
+// Error-free pieces of the SP settle.  u22f: an integer below 2^23 as a float,
+// exactly, by way of its bit pattern (no conversion instruction).
+__device__ inline float u22f(uint32_t m) { return __int_as_float(0x4b000000 | m) - 8388608.0f; }
+// (kp - kj) 2^-64 + sh as a double-float, exact to about 2^-48 relative: the
+// 64-bit difference of two fixed-point phases is split into three pieces that
+// floats hold exactly and summed with an error-free addition.
+__device__ inline df key_diff_df(uint64_t kp, uint64_t kj, int sh)
+{
+    const bool ge = kp >= kj;
+    const uint64_t m = ge ? kp - kj : kj - kp;
+    const float f2 = u22f((uint32_t)(m >> 44)) * 0x1p-20f;
+    const float f1 = u22f((uint32_t)(m >> 22) & 0x3fffffu) * 0x1p-42f;
+    const float f0 = u22f((uint32_t)m & 0x3fffffu) * 0x1p-64f;
+    df v = x_two_sum(f2, f1);
+    v = x_fast(v.hi, v.lo + f0);
+    if (!ge) v = df{-v.hi, -v.lo};
+    if (sh) v = acc_add(df{(float)sh, 0.f}, v);
+    return v;
+}
+// product of two double-floats, rounded once to a double-float (FMA-exact
+// leading product plus the cross terms)
+__device__ inline df df_mul(df a, df b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return x_fast(p, e);
+}
+// running sum: the leading parts add error-free, the low parts and the
+// errors collect in lo (renormalised once at the end)
+__device__ inline void df_acc(df &s, df x)
+{
+    const df t = x_two_sum(s.hi, x.hi);
+    s.hi = t.hi;
+    s.lo += t.lo + x.lo;
+}
+__device__ inline double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
+
+// Settles one contested SP centre je beyond FP32 precision: the line fits of
+// its three span windows from the exact phases (the sorted 64-bit
+// fixed-point keys) and the inputs as double-float pairs read through perm,
+// then the span choice and interpolation in binary64.  The window sums run on
+// the FP32 pipe as double-float sums of error-free products (about 2^-44
+// relative, against binary64's 2^-53; the FP64 pipe issues at 1/64 of the
+// FP32 rate on this chip, which made a binary64 walk over a woofer window the
+// largest wait of the SP kernel).  The windows share their centre and nest
+// (h0 <= h1 <= h2, periodic or clamped), so each point is loaded and summed
+// once: into the tweeter window, or the ring the midrange window adds around
+// it, or the woofer's ring around that (each ring's two segments in one walk);
+// the wider windows' sums are running totals.  sl: bit k set when span k's fit
+// kept its slope, which picks the validation factor as in the FP32 choice.
+// The code runs rarely, from a cold instruction cache, so it is out of line
+// and written once per step (only the walk is unrolled).  All lanes of the
+// warp call it together with the same centre; every lane returns the smooth.
 template <typename R>
-__device__ __noinline__ double sp_settle_fp64(const Frame<R> fr, const double *y64, const double *w64,
-                                              int je, int h0, int h1, int h2, int n, int qi, int qj,
-                                              int sl, bool lim0, bool lim1, const double *spans,
-                                              double alpha)
+__device__ __noinline__ double sp_settle(const Frame<R> fr, const float2 *ydf, const float2 *wdf,
+                                         int je, int h0, int h1, int h2, int n, int qi, int qj,
+                                         int sl, bool lim0, bool lim1, const double *spans,
+                                         double alpha)
 {
     const uint64_t *key = fr.key;
     // Listing 1's vsmlsq from the exact phases at the scale indices qi, qj
-    const double xqi = (double)key[qi] * 5.421010862427522e-20;
-    const double xqj = (double)key[qj] * 5.421010862427522e-20;
-    const double vsmlsq64 = 1.0e-6 * (xqj - xqi) * (xqj - xqi);
+    const double sq = df_to_double(key_diff_df(key[qj], key[qi], 0));
+    const double vsmlsq64 = 1.0e-6 * sq * sq;
     const uint16_t *perm = fr.perm;
-    const double xj = (double)key[je] * 5.421010862427522e-20;
+    const uint64_t kj = key[je];
     const int lo[3] = {win_lo(fr, je, h0, n), win_lo(fr, je, h1, n), win_lo(fr, je, h2, n)};
     const int hw[3] = {h0, h1, h2};
     double sw = 0.0, sa = 0.0, sb = 0.0, sc = 0.0, sd = 0.0, fit[3];
@@ -1299,40 +1436,41 @@ __device__ __noinline__ double sp_settle_fp64(const Frame<R> fr, const double *y
         // slots [ea, ea + na) and [eb, eb + nb): window 0, or ring k
         const int ea = lo[k], na = k ? lo[k - 1] - lo[k] : 2 * hw[0] + 1;
         const int eb = k ? lo[k - 1] + 2 * hw[k - 1] + 1 : 0, nb = k ? hi - (eb - 1) : 0;
-        double aw = 0.0, aa = 0.0, ab = 0.0, ac = 0.0, ad = 0.0;
-#pragma unroll 4   // a few loads in flight per lane
+        df aw{0.f, 0.f}, aa = aw, ab = aw, ac = aw, ad = aw;
+#pragma unroll 2
         for (int v = (int)(threadIdx.x & 31); v < na + nb; v += 32) {
             const int e = v < na ? ea + v : eb + (v - na);
             int sh;
             const int p = slot_point(e, n, sh);
             const uint32_t i = perm[p];
-            const double x = (double)key[p] * 5.421010862427522e-20 + sh;
-            const double w = w64[i], y = y64[i], dx = x - xj;
-            aw += w;
-            aa += w * dx;
-            ab += w * dx * dx;
-            ac += w * y;
-            ad += w * dx * y;
+            const df dx = key_diff_df(key[p], kj, sh);
+            const float2 w2 = wdf[i], y2 = ydf[i];
+            const df w{w2.x, w2.y}, y{y2.x, y2.y};
+            const df wdx = df_mul(w, dx);
+            df_acc(aw, w);
+            df_acc(aa, wdx);
+            df_acc(ab, df_mul(wdx, dx));
+            df_acc(ac, df_mul(w, y));
+            df_acc(ad, df_mul(wdx, y));
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            aw += __shfl_xor_sync(0xffffffffu, aw, o);
-            aa += __shfl_xor_sync(0xffffffffu, aa, o);
-            ab += __shfl_xor_sync(0xffffffffu, ab, o);
-            ac += __shfl_xor_sync(0xffffffffu, ac, o);
-            ad += __shfl_xor_sync(0xffffffffu, ad, o);
+        df q[5] = {aw, aa, ab, ac, ad};
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            q[m] = x_two_sum(q[m].hi, q[m].lo);
+            for (int o = 16; o > 0; o >>= 1) q[m] = acc_add(q[m], acc_shfl_xor(q[m], o));
         }
-        sw += aw;
-        sa += aa;
-        sb += ab;
-        sc += ac;
-        sd += ad;
+        sw += df_to_double(q[0]);
+        sa += df_to_double(q[1]);
+        sb += df_to_double(q[2]);
+        sc += df_to_double(q[3]);
+        sd += df_to_double(q[4]);
         const double xb = sa / sw;   // xbar - x_j
         const double sxx = sb - xb * sa;
         const double sxv = sd - xb * sc;
         const double b = sxx > vsmlsq64 ? sxv / sxx : 0.0;
         fit[k] = sc / sw + b * (0.0 - xb);
     }
-    const double ye = y64[perm[je]];
+    const double ye = df_to_double(df{ydf[perm[je]].x, ydf[perm[je]].y});
     double e[3];
 #pragma unroll 1
     for (int k = 0; k < 3; ++k) {
@@ -1343,6 +1481,25 @@ __device__ __noinline__ double sp_settle_fp64(const Frame<R> fr, const double *y
     const double sp = choose_span<double>(K64, e[0], e[1], e[2], e[2], K64.s2, lim0, lim1);
     return interpolate_span<double>(K64, sp, fit[0], fit[1], fit[2]);
 }
+
+// Where pass A leaves the three smooths for pass C: the frame's columns C0,
+// C2, C4, or this CTA's part of the global slab (coalesced across a warp:
+// every thread of a warp is at the same k of its chunk at the same time).
+// SLAB false: always the frame columns (kernels for objects too short to use
+// the slab carry no slab addressing).
+template <typename R, bool SLAB>
+struct SmoCols {
+    R *slab;        // null: frame columns
+    R *col[3];      // frame columns C0, C2, C4
+    int kmax, G, nmax, tid, c0;
+    __device__ inline R *at(int c, int i) const
+    {
+        if (!SLAB || !slab) return col[c] + i;
+        const int k = i - c0;
+        return k < kmax ? slab + ((size_t)(c * kmax + k) * G + tid)
+                        : slab + (size_t)3 * kmax * G + (size_t)c * nmax + i;
+    }
+};
 
 struct FreqResult {
     double chi2;
@@ -1696,8 +1853,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
         const R gl0 = R(1) / (R(1) - R(2) / m0), gc0 = R(1) / (R(1) - R(1) / m0);
         const R gl1 = R(1) / (R(1) - R(2) / m1), gc1 = R(1) / (R(1) - R(1) / m1);
         const R gl2 = R(1) / (R(1) - R(2) / m2), gc2 = R(1) / (R(1) - R(1) / m2);
-        const double *y64 = a.yc64 ? a.yc64 + base : nullptr;
-        const double *w64 = a.wv64 ? a.wv64 + base : nullptr;
+        const float2 *y64 = a.ydf ? a.ydf + base : nullptr;
+        const float2 *w64 = a.wdf ? a.wdf + base : nullptr;
         // a point whose bound E on its chi2 change exceeds this is refitted
         const R sens_lim = ok.sens_lim;
         const R ymax = ok.ymax;
@@ -1776,8 +1933,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
                 const int je = __shfl_sync(0xffffffffu, j, src);
                 const int sl = __shfl_sync(0xffffffffu, (sl0 ? 1 : 0) | (sl1 ? 2 : 0) | (sl2 ? 4 : 0),
                                            src);
-                const double v = sp_settle_fp64<R>(fr, y64, w64, je, h0, h1, h2, n, qi, qj, sl, lim0,
-                                                   lim1, a.spans, a.alpha);
+                const double v = sp_settle<R>(fr, y64, w64, je, h0, h1, h2, n, qi, qj, sl, lim0, lim1,
+                                              a.spans, a.alpha);
                 if (lane == src) val[0] = (R)v;
             }
             if (act) {
@@ -1793,12 +1950,23 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
     }
 
     // ===== SS, Listing 1 =====
+    SmoCols<R, LONG> smo;
+    smo.slab = (LONG && a.smo) ? (R *)((unsigned char *)a.smo + (size_t)blockIdx.x * a.smo_stride)
+                               : nullptr;
+    smo.col[0] = fr.C[0];
+    smo.col[1] = fr.C[2];
+    smo.col[2] = fr.C[4];
+    smo.kmax = a.smo_kmax;
+    smo.G = G;
+    smo.nmax = a.smo_nmax;
+    smo.tid = tid;
+    smo.c0 = c0;
     // pass A: the three spans on y with cross-validation.  C0/C2/C4 = smooths
     // (tweeter/midrange/woofer), C1/C3/C5 = CV residuals (-1 marks a centre
     // whose leverage reached 1; resolved below).
     {
         const R *vy[1] = {fr.Y};
-        build_xy_prefix(fr, sm, fr.Y, c0, c1, o);
+        build_xy_prefix<R, !LONG>(fr, sm, fr.Y, c0, c1, o);
         __syncthreads();
         if (c0 < c1) {
             Win<R, 1> w0, w1, w2;
@@ -1808,9 +1976,9 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
             RunAvg<R, 3> ra;
             ra.reset(c0);
             auto emit = [&](int i, const R (&v)[3]) {
-                fr.C[0][i] = v[0];
-                fr.C[2][i] = v[1];
-                fr.C[4][i] = v[2];
+                *smo.at(0, i) = v[0];
+                *smo.at(1, i) = v[1];
+                *smo.at(2, i) = v[2];
             };
             for (int j = c0; j < c1; ++j) {
                 Fit<R, 1> f0, f1, f2;
@@ -1850,7 +2018,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
         const R *vr[3] = {fr.C[1], fr.C[3], fr.C[5]};
         const float margin = ok.margin;
         // resolves the -1 residuals of pass A while it sums them
-        build_channel_prefix<R, NB, DIFF, true>(fr, sm, vr, c0, c1, o);
+        build_channel_prefix<R, NB, DIFF, true, !LONG>(fr, sm, vr, c0, c1, o);
         __syncthreads();
         if (c0 < c1) {
             Win<R, NB> w1;
@@ -1881,7 +2049,20 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
     // pass C: midrange smooth of the chosen spans, clamp and interpolate -> C1
     {
         const R *vs[1] = {fr.C[6]};
-        build_channel_prefix<R, 1>(fr, sm, vs, c0, c1, o);
+        // LONG (smooths in the global slab, where they come from L2): pass A's
+        // smooths at the next two centres are loaded ahead of their use, the
+        // first two before the prefix scan, then each two centres before it
+        // is interpolated
+        R q0[3] = {R(0), R(0), R(0)}, q1[3] = {R(0), R(0), R(0)};
+        if (LONG && c0 < c1) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) q0[c] = *smo.at(c, c0);
+            if (c0 + 1 < c1) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) q1[c] = *smo.at(c, c0 + 1);
+            }
+        }
+        build_channel_prefix<R, 1, false, false, !LONG>(fr, sm, vs, c0, c1, o);
         __syncthreads();
         if (c0 < c1) {
             Win<R, 1> w1;
@@ -1889,13 +2070,25 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
             RunAvg<R, 1> ra;
             ra.reset(c0);
             auto emit = [&](int i, const R (&v)[1]) {
-                fr.C[1][i] = interpolate_span<R>(K, v[0], fr.C[0][i], fr.C[2][i], fr.C[4][i]);
+                fr.C[1][i] = interpolate_span<R>(K, v[0], *smo.at(0, i), *smo.at(1, i), *smo.at(2, i));
             };
             for (int j = c0; j < c1; ++j) {
                 Fit<R, 1> f1;
                 win_fit_checked<R, 1>(f1, w1, fr, vs, j, h1, n, o, vsmlsq, near, rf);
-                const R val[1] = {f1.s[0]};
-                run_push<R, 1>(ra, fr, j, ties, val, emit);
+                if (LONG && !ties) {
+                    fr.C[1][j] = interpolate_span<R>(K, f1.s[0], q0[0], q0[1], q0[2]);
+                } else {
+                    const R val[1] = {f1.s[0]};
+                    run_push<R, 1>(ra, fr, j, ties, val, emit);
+                }
+                if (LONG) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) q0[c] = q1[c];
+                    if (j + 2 < c1) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) q1[c] = *smo.at(c, j + 2);
+                    }
+                }
                 if (j + 1 < c1) win_slide<R, 1>(w1, fr, vs, j, h1, n, o);
             }
         }
@@ -1905,7 +2098,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
     // pass D: final tweeter smooth and chi2
     {
         const R *vv[1] = {fr.C[1]};
-        build_channel_prefix<R, 1>(fr, sm, vv, c0, c1, o);
+        build_channel_prefix<R, 1, false, false, !LONG>(fr, sm, vv, c0, c1, o);
         __syncthreads();
         if (c0 < c1) {
             Win<R, 1> w0;
@@ -1958,7 +2151,8 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
         // frequency's fold and sort
         const int m = SHARED && item.w > 1 ? item.w : 1;
         const int n = (int)(a.off[o + 1] - a.off[o]);
-        Frame<R> fr = carve_frame<R>(big, n, VARIANT, SHARED);
+        // only the kernels for long objects address the smooth slab
+        Frame<R> fr = carve_frame<R>(big, n, VARIANT, SHARED, LONG && a.smo != nullptr);
         ObjK<R> ok = obj_consts<R>(a, n, o);
         fr.per = PER;
         // a frame in global memory still counts its sort buckets in shared

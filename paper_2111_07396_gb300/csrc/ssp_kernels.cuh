@@ -81,6 +81,11 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepArgs a)
             a.yc64[base + i] = d;
             a.wv64[base + i] = w;
         }
+        if (a.ydf) {
+            const float dh = (float)d, wh = (float)w;
+            a.ydf[base + i] = make_float2(dh, (float)(d - (double)dh));
+            a.wdf[base + i] = make_float2(wh, (float)(w - (double)wh));
+        }
     }
     c0 = warp_sum(c0);
     for (int off = 16; off > 0; off >>= 1) ym = fmax(ym, __shfl_xor_sync(0xffffffffu, ym, off));
@@ -293,8 +298,8 @@ __global__ void __launch_bounds__(256) peaks_kernel(PeaksArgs a)
     {                                                                                         \
         return small_bytes<typename AccSel<R, PLAIN>::T>(G, variant);                         \
     }                                                                                         \
-    size_t pgram_frame_bytes_##PREC(int n, int variant, bool keep_perm)                       \
+    size_t pgram_frame_bytes_##PREC(int n, int variant, bool keep_perm, bool smo_out)         \
     {                                                                                         \
-        return frame_bytes<R>(n, variant, keep_perm);                                         \
+        return frame_bytes<R>(n, variant, keep_perm, smo_out);                                \
     }                                                                                         \
     }

@@ -15,6 +15,7 @@ struct PrepArgs {
     double *tt;                // [N] t - min t, binary64 (both paths)
     void *yc, *wv;             // [N] R: centred magnitudes, weights
     double *yc64, *wv64;       // [N] FP64 copies for the FP32C recompute (or null)
+    float2 *ydf, *wdf;         // [N] FP32C: the same as double-float pairs, for the SP settle
     double *chi0;              // [n_obj]
     double *ymax;              // [n_obj] largest |y - ybar_w|
     int *bad;                  // [n_obj]
@@ -57,6 +58,6 @@ cudaError_t pgram_launch(int precision, int variant, bool gmem, bool lng, bool p
                          int grid, int G, size_t smem, const PgramArgs &a, cudaStream_t s);
 
 size_t pgram_small_bytes(int precision, int G, int variant);
-size_t pgram_frame_bytes(int precision, int n, int variant, bool keep_perm);
+size_t pgram_frame_bytes(int precision, int n, int variant, bool keep_perm, bool smo_out = false);
 
 }  // namespace ssp
