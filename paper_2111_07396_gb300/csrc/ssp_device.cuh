@@ -1412,6 +1412,12 @@ __device__ inline double df_to_double(df x) { return (double)x.hi + (double)x.lo
 // it, or the woofer's ring around that (each ring's two segments in one walk);
 // the wider windows' sums are running totals.  sl: bit k set when span k's fit
 // kept its slope, which picks the validation factor as in the FP32 choice.
+// Bit 3 of sl asks for the woofer window too.  Without it (a near-tie whose
+// smaller residual lies more than 1e-4 relative below the woofer's) the
+// woofer's FP32 fit s2f and residual g2f stand in: the span then depends on
+// them only continuously (bass enhancement, interpolation), so their FP32
+// error moves the smooth by about 1e-6 of the fits' spread, and the woofer's
+// ring, the longest walk, is skipped.
 // The code runs rarely, from a cold instruction cache, so it is out of line
 // and written once per step (only the walk is unrolled).  All lanes of the
 // warp call it together with the same centre; every lane returns the smooth.
@@ -1419,8 +1425,10 @@ template <typename R>
 __device__ __noinline__ double sp_settle(const Frame<R> fr, const float2 *ydf, const float2 *wdf,
                                          int je, int h0, int h1, int h2, int n, int qi, int qj,
                                          int sl, bool lim0, bool lim1, const double *spans,
-                                         double alpha)
+                                         double alpha, float s2f, float g2f)
 {
+    // bit 3 of sl: refit the woofer window as well, else take its FP32 fit
+    const int nk = (sl & 8) ? 3 : 2;
     const uint64_t *key = fr.key;
     // Listing 1's vsmlsq from the exact phases at the scale indices qi, qj
     const double sq = df_to_double(key_diff_df(key[qj], key[qi], 0));
@@ -1430,8 +1438,9 @@ __device__ __noinline__ double sp_settle(const Frame<R> fr, const float2 *ydf, c
     const int lo[3] = {win_lo(fr, je, h0, n), win_lo(fr, je, h1, n), win_lo(fr, je, h2, n)};
     const int hw[3] = {h0, h1, h2};
     double sw = 0.0, sa = 0.0, sb = 0.0, sc = 0.0, sd = 0.0, fit[3];
+    fit[2] = (double)s2f;
 #pragma unroll 1
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < nk; ++k) {
         const int hi = lo[k] + 2 * hw[k];
         // slots [ea, ea + na) and [eb, eb + nb): window 0, or ring k
         const int ea = lo[k], na = k ? lo[k - 1] - lo[k] : 2 * hw[0] + 1;
@@ -1472,8 +1481,9 @@ __device__ __noinline__ double sp_settle(const Frame<R> fr, const float2 *ydf, c
     }
     const double ye = df_to_double(df{ydf[perm[je]].x, ydf[perm[je]].y});
     double e[3];
+    e[2] = (double)g2f;
 #pragma unroll 1
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < nk; ++k) {
         const double d = 1.0 - (((sl >> k) & 1) ? 2.0 : 1.0) / (double)(2 * hw[k] + 1);
         e[k] = fabs(ye - fit[k]) / d;
     }
@@ -1871,6 +1881,11 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
             bool contested = false;
             R s0 = R(0), s1 = R(0), s2 = R(0), g2 = R(0);
             bool sl0 = false, sl1 = false, sl2 = false;
+            // the settle refits the woofer window too unless its FP32 fit is
+            // enough: a near-tie settle whose minimum lies clearly below the
+            // woofer's residual (bass enhancement and interpolation depend on
+            // the woofer's fit continuously there)
+            bool need2 = true;
             if (act) {
                 Fit<R, 1> f0, f1, f2;
                 win_fit_checked<R, 1>(f0, w0, fr, vy, j, h0, n, o, vsmlsq, near, rf);
@@ -1902,6 +1917,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
                         const R rs = fmax(fmax(s0, s1), s2) - fmin(fmin(s0, s1), s2);
                         const bool in_run = ties && (tie_next(fr, j) || (j > 0 && tie_next(fr, j - 1)));
                         contested = in_run || fr.XW[j].y * rs * (R(2) * fabs(yj - val[0]) + rs) > sens_lim;
+                        need2 = !(g2 - fmin(g0, g1) > (R)1e-4 * g2);
                     }
                     // bound on the power change from the FP32 error of the
                     // residuals through bass enhancement and interpolation:
@@ -1922,7 +1938,10 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
                                                            : fabs(s2 - s1) * K.inv21;
                         const R E = R(2) * fr.XW[j].y * fabs(yj - val[0]) *
                                     ((K.s2 - sk) * dvds * tmp * (ge / gm + we / g2));
-                        if (E > sens_lim) contested = true;
+                        if (E > sens_lim) {
+                            contested = true;
+                            need2 = true;
+                        }
                     }
                 }
             }
@@ -1931,10 +1950,12 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
                 const int src = __ffs(todo) - 1;
                 todo &= todo - 1;
                 const int je = __shfl_sync(0xffffffffu, j, src);
-                const int sl = __shfl_sync(0xffffffffu, (sl0 ? 1 : 0) | (sl1 ? 2 : 0) | (sl2 ? 4 : 0),
-                                           src);
+                const int sl = __shfl_sync(0xffffffffu, (sl0 ? 1 : 0) | (sl1 ? 2 : 0) | (sl2 ? 4 : 0) |
+                                                            (need2 ? 8 : 0), src);
+                const float s2f = __shfl_sync(0xffffffffu, (float)s2, src);
+                const float g2f = __shfl_sync(0xffffffffu, (float)g2, src);
                 const double v = sp_settle<R>(fr, y64, w64, je, h0, h1, h2, n, qi, qj, sl, lim0, lim1,
-                                              a.spans, a.alpha);
+                                              a.spans, a.alpha, s2f, g2f);
                 if (lane == src) val[0] = (R)v;
             }
             if (act) {
