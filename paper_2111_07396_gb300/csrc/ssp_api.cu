@@ -327,6 +327,9 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
                                 1024;
             if (2 * need > max_smem + 1024) b.G = 512;
         }
+        // the kernels split chunks and scans by shifts: a power of two, 32..512
+        if (b.G < 32 || b.G > 512 || (b.G & (b.G - 1)) != 0)
+            return fail(SSP_ERR_ARG, "threads per CTA must be a power of two in 32..512, not %d", b.G);
         plan.buckets.push_back(std::move(b));
     }
     plan.items_total = 0;

@@ -367,6 +367,31 @@ template <> struct AccFrom<double> {
 template <typename A>
 __device__ inline A acc_from(typename R_of<A>::type a) { return AccFrom<A>::get(a); }
 
+// Exact floor(a / n) for 0 <= a < 2^26 and 1 <= n <= 65535 by one 64-bit
+// multiply and a shift (Granlund-Montgomery): with L = ceil(log2 n), s = 26 + L
+// and m = floor(2^s / n) + 1, a m / 2^s exceeds a / n by less than
+// a / 2^s < 2^-L <= 1/n, which never reaches the next integer.  The GPU has no
+// integer divider: a plain division compiles to float reciprocals and
+// conversions, and conversions issue on the FP64 pipe, at 1/64 of the FP32
+// rate on this chip.
+struct DivN {
+    uint32_t m;
+    int s;
+};
+__host__ __device__ inline DivN divn_make(int n)
+{
+    int L = 0;
+    while ((1 << L) < n) ++L;
+    DivN d;
+    d.s = 26 + L;
+    d.m = (uint32_t)((1ull << d.s) / (uint64_t)n) + 1u;
+    return d;
+}
+__host__ __device__ inline int divn(uint32_t a, DivN d)
+{
+    return (int)(((uint64_t)a * d.m) >> d.s);
+}
+
 // per-frequency chunk table, window prefixes and reduction scratch (always
 // shared memory).  px: exclusive prefixes over chunks of the raw moments
 // sum w, sum w x, sum w x^2 (x about 0); pc: per channel sum w v and
@@ -380,6 +405,7 @@ struct Small {
     double *red;   // [96] reduction scratch
     int *ired;     // [32]
     int *flags;    // [4]
+    DivN dn;       // division by the item's n (chunk lookups)
 };
 
 // channels a variant smooths at once: SS pass B smooths three residual
@@ -438,7 +464,7 @@ __device__ inline double block_sum(double v, double *red)
 __device__ inline int block_exclusive_scan(uint32_t *cnt, int nb, int *ired)
 {
     const int G = blockDim.x, tid = threadIdx.x;
-    const int per = (nb + G - 1) / G;
+    const int per = nb > G ? nb >> (__ffs(G) - 1) : 1;   // nb and G are powers of two
     const int a = min(nb, tid * per), len = min(nb, a + per) - a;
     // Blocks of 16 or more counts: each thread walks its block starting at
     // offset sk, so that the lanes of a warp, whose blocks lie per words
@@ -504,6 +530,18 @@ __device__ inline int block_exclusive_scan(uint32_t *cnt, int nb, int *ired)
     }
     __syncthreads();
     return gmax;
+}
+
+// The phase k 2^-64 of a 64-bit fixed-point key, truncated to float (round
+// toward zero), built from the key's bits: the exponent from the position of
+// its leading one, the significand from the 23 bits below it.  (An integer to
+// float conversion instruction would issue on the FP64 pipe.)
+__device__ inline float key_to_float_rz(uint64_t k)
+{
+    if (k == 0) return 0.f;
+    const int e = 63 - __clzll((long long)k);   // leading one: value in [2^(e-64), 2^(e-63))
+    const uint32_t mant = (uint32_t)((e >= 23 ? k >> (e - 23) : k << (23 - e)) & 0x7fffffu);
+    return __int_as_float(((e + 63) << 23) | (int)mant);   // exponent field (e - 64) + 127
 }
 
 // ---------------------------------------------------------------------------
@@ -910,16 +948,16 @@ __device__ void build_channel_prefix(const Frame<R> &fr, const Small<R, A> &sm, 
 // it would split, so cs[u] >= floor(u n / G): the arithmetic guess below is
 // never too low, and the correction walks down over tie-emptied chunks only.
 // First chunk starting at or after p (0 <= p <= n):
-__device__ inline int chunk_lower(const int *cs, int G, int n, int p)
+__device__ inline int chunk_lower(const int *cs, int G, int n, DivN dn, int p)
 {
-    int u = (int)(((unsigned)(p * G) + (unsigned)(n - 1)) / (unsigned)n);   // ceil(p G / n): cs[u] >= p
+    int u = divn((unsigned)(p * G) + (unsigned)(n - 1), dn);   // ceil(p G / n): cs[u] >= p
     while (u > 0 && cs[u - 1] >= p) --u;
     return u;
 }
 // Last chunk boundary at or before q (0 <= q <= n):
-__device__ inline int chunk_upper(const int *cs, int G, int n, int q)
+__device__ inline int chunk_upper(const int *cs, int G, int n, DivN dn, int q)
 {
-    int u = (int)(((unsigned)((q + 1) * G) + (unsigned)(n - 1)) / (unsigned)n) - 1;   // floor(u n / G) <= q
+    int u = divn((unsigned)((q + 1) * G) + (unsigned)(n - 1), dn) - 1;   // floor(u n / G) <= q
     if (u > G) u = G;
     while (cs[u] > q) --u;
     return u;
@@ -971,8 +1009,8 @@ __device__ inline void win_init_body(Win<R, NCH> &s, const Frame<R> &fr, const S
         if (seg < 0) { pa = ea + n; pb = n - 1; if (ea >= 0) continue; }
         else if (seg == 0) { pa = ea < 0 ? 0 : ea; pb = eb >= n ? n - 1 : eb; }
         else { pa = 0; pb = eb - n; if (eb < n) continue; }
-        int ua = chunk_lower(sm.cs, G, n, pa);
-        int ub = chunk_upper(sm.cs, G, n, pb + 1);
+        int ua = chunk_lower(sm.cs, G, n, sm.dn, pa);
+        int ub = chunk_upper(sm.cs, G, n, sm.dn, pb + 1);
         // points walked one by one: [la, la + nl) with sign sl, then
         // [pr + nl, pr + nt) with sign sr
         int nl = pb - pa + 1, nt = nl, pr = pa, la = pa;
@@ -998,7 +1036,7 @@ __device__ inline void win_init_body(Win<R, NCH> &s, const Frame<R> &fr, const S
             }
             if (seg != 0) {
                 // x -> x + seg: s2 += 2 seg s1 + W, s1 += seg W, D += seg C
-                const R sg = (R)seg;
+                const R sg = seg < 0 ? R(-1) : R(1);
                 s2 = acc_add(s2, acc_add(acc_mul(s1, R(2) * sg), w));
                 s1 = acc_add(s1, acc_mul(w, sg));
 #pragma unroll
@@ -1021,7 +1059,8 @@ __device__ inline void win_init_body(Win<R, NCH> &s, const Frame<R> &fr, const S
             pr = ra - nl;
         }
         for (int k = 0; k < nt; ++k)
-            win_add_slot<R, NCH, DIFF>(s, fr, v, k < nl ? la + k : pr + k, (R)seg, o,
+            win_add_slot<R, NCH, DIFF>(s, fr, v, k < nl ? la + k : pr + k,
+                                       seg == 0 ? R(0) : (seg < 0 ? R(-1) : R(1)), o,
                                        k < nl ? sl : sr);
     }
     // about o: A = S1 - o W, B = S2 - 2 o S1 + o^2 W, D = D - o C
@@ -1068,7 +1107,7 @@ struct Chans {
 template <typename R, int NCH, bool DIFF, typename A>
 __device__ __noinline__ Win<R, NCH> win_init_ool(const typename Vec2<R>::T *XW, int per,
                                                  const Chans<R, NCH> cv, int *cs, A *px, A *pc,
-                                                 int c, int h, int n, R o)
+                                                 DivN dn, int c, int h, int n, R o)
 {
     Frame<R> fr{};
     fr.XW = const_cast<typename Vec2<R>::T *>(XW);
@@ -1077,6 +1116,7 @@ __device__ __noinline__ Win<R, NCH> win_init_ool(const typename Vec2<R>::T *XW, 
     sm.cs = cs;
     sm.px = px;
     sm.pc = pc;
+    sm.dn = dn;
     const R *v[NCH];
 #pragma unroll
     for (int ch = 0; ch < NCH; ++ch) v[ch] = cv.p[ch];
@@ -1092,7 +1132,7 @@ __device__ inline void win_init(Win<R, NCH> &s, const Frame<R> &fr, const Small<
         Chans<R, NCH> cv;
 #pragma unroll
         for (int ch = 0; ch < NCH; ++ch) cv.p[ch] = (DIFF && ch == NCH - 1) ? nullptr : v[ch];
-        s = win_init_ool<R, NCH, DIFF, A>(fr.XW, fr.per, cv, sm.cs, sm.px, sm.pc, c, h, n, o);
+        s = win_init_ool<R, NCH, DIFF, A>(fr.XW, fr.per, cv, sm.cs, sm.px, sm.pc, sm.dn, c, h, n, o);
     } else {
         win_init_body<R, NCH, DIFF>(s, fr, sm, v, c, h, n, o);
     }
@@ -1525,6 +1565,9 @@ struct ObjK {
     int h0, h1, h2, hs;   // half widths of the three spans, and of the fixed span
     bool lim0, lim1;      // the tweeter's / midrange's window differs from the woofer's
     SpanK<R> K;
+    // generalized-validation factors 1 / (1 - nu/m) of the three windows (m
+    // points) for a line (nu = 2) and a constant (nu = 1)
+    R gl0, gc0, gl1, gc1, gl2, gc2;
     float margin;         // SS: tweeter-vs-midrange margin
     R sens_lim, ymax;     // SP: chi2 budget per point, largest centred magnitude
 };
@@ -1538,6 +1581,13 @@ __device__ inline ObjK<R> obj_consts(const PgramArgs &a, int n, int obj)
     k.hs = a.span > 0.0 ? half_width(n, a.span) : 0;
     k.lim0 = k.h0 != k.h2;
     k.lim1 = k.h1 != k.h2;
+    const R m0 = (R)(2 * k.h0 + 1), m1 = (R)(2 * k.h1 + 1), m2 = (R)(2 * k.h2 + 1);
+    k.gl0 = R(1) / (R(1) - R(2) / m0);
+    k.gc0 = R(1) / (R(1) - R(1) / m0);
+    k.gl1 = R(1) / (R(1) - R(2) / m1);
+    k.gc1 = R(1) / (R(1) - R(1) / m1);
+    k.gl2 = R(1) / (R(1) - R(2) / m2);
+    k.gc2 = R(1) / (R(1) - R(1) / m2);
     k.K = span_consts<R>(a.spans, a.alpha);
     k.margin = a.near_ss * fminf(1.f, 256.f / (float)n) * fminf(1.f, 512.f / (float)n);
     k.sens_lim = (R)(a.sens_tau * a.chi0[obj]);
@@ -1712,11 +1762,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
                 // X = the phase truncated to float.  From 2^-8 up, the top
                 // word alone holds the float's 24 bits (its own truncation is
                 // the same); only tiny phases need the 64-bit conversion.
-                if (kh >= (1u << 24)) {
-                    x = (R)(__uint2float_rz(kh) * 2.3283064365386963e-10f);   // * 2^-32
-                } else {
-                    x = (R)(__ull2float_rz(kj) * 5.421010862427522e-20f);    // * 2^-64
-                }
+                x = (R)key_to_float_rz(kj);
             }
             fr.XW[j] = vec2<R>(x, wv[i]);
             fr.Y[j] = yc[i];
@@ -1765,7 +1811,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
 
     // ---- chunks: contiguous centre ranges that never split a run of ties ----
     {
-        int c = (int)((unsigned)(tid * n) / (unsigned)G);   // n G < 2^31
+        int c = (int)((unsigned)(tid * n) >> (__ffs(G) - 1));   // floor(tid n / G), G a power of two
         if (ties)
             while (c > 0 && c < n && tie_next(fr, c - 1)) ++c;
         sm.cs[tid] = c;
@@ -1795,10 +1841,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
             win_init<R, 1>(w0, fr, sm, vy, c0, h0, n, o);
             win_init<R, 1>(w1, fr, sm, vy, c0, h1, n, o);
             win_init<R, 1>(w2, fr, sm, vy, c0, h2, n, o);
-            const R m0 = (R)(2 * h0 + 1), m1 = (R)(2 * h1 + 1), m2 = (R)(2 * h2 + 1);
-            const R gl0 = R(1) / (R(1) - R(2) / m0), gc0 = R(1) / (R(1) - R(1) / m0);
-            const R gl1 = R(1) / (R(1) - R(2) / m1), gc1 = R(1) / (R(1) - R(1) / m1);
-            const R gl2 = R(1) / (R(1) - R(2) / m2), gc2 = R(1) / (R(1) - R(1) / m2);
+            const R gl0 = ok.gl0, gc0 = ok.gc0, gl1 = ok.gl1, gc1 = ok.gc1, gl2 = ok.gl2, gc2 = ok.gc2;
             RunAvg<R, 3> ra;
             ra.reset(c0);
             auto emit = [&](int i, const R (&v)[3]) {
@@ -1858,11 +1901,8 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
             win_init<R, 1>(w1, fr, sm, vy, c0, h1, n, o);
             win_init<R, 1>(w2, fr, sm, vy, c0, h2, n, o);
         }
-        const R m0 = (R)(2 * h0 + 1), m1 = (R)(2 * h1 + 1), m2 = (R)(2 * h2 + 1);
         // 1 / (1 - nu/m) for a line (nu = 2) and a constant (nu = 1)
-        const R gl0 = R(1) / (R(1) - R(2) / m0), gc0 = R(1) / (R(1) - R(1) / m0);
-        const R gl1 = R(1) / (R(1) - R(2) / m1), gc1 = R(1) / (R(1) - R(1) / m1);
-        const R gl2 = R(1) / (R(1) - R(2) / m2), gc2 = R(1) / (R(1) - R(1) / m2);
+        const R gl0 = ok.gl0, gc0 = ok.gc0, gl1 = ok.gl1, gc1 = ok.gc1, gl2 = ok.gl2, gc2 = ok.gc2;
         const float2 *y64 = a.ydf ? a.ydf + base : nullptr;
         const float2 *w64 = a.wdf ? a.wdf + base : nullptr;
         // a point whose bound E on its chi2 change exceeds this is refitted
@@ -2174,6 +2214,7 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
         const int n = (int)(a.off[o + 1] - a.off[o]);
         // only the kernels for long objects address the smooth slab
         Frame<R> fr = carve_frame<R>(big, n, VARIANT, SHARED, LONG && a.smo != nullptr);
+        sm.dn = divn_make(n);
         ObjK<R> ok = obj_consts<R>(a, n, o);
         fr.per = PER;
         // a frame in global memory still counts its sort buckets in shared
