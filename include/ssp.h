@@ -57,8 +57,9 @@ typedef enum {
  * SSP_FP32C re-takes in binary64 the decisions that FP32 rounding could flip.
  * Its margins have defaults chosen for the 2e-4 tolerance; each can be
  * overridden, for testing and tuning only, by an environment variable read at
- * every launch (a value of 1e6 or more, or an empty one, keeps the default; a
- * negative margin disables its test):
+ * every launch, and only while SSP_TESTING=1 is set too (a value of 1e6 or
+ * more, or an empty one, keeps the default; a negative margin disables its
+ * test):
  *   SSP_NEAR_SS     SS tweeter-vs-midrange margin for n <= 256 (default 1e-6,
  *                   relative; scaled down for larger n).  Flags the frequency
  *                   for the binary64 recompute.
@@ -81,7 +82,7 @@ typedef enum {
     SSP_ERR_ARG = -1,         /* invalid argument or input value */
     SSP_ERR_NOMEM = -2,       /* device memory budget exceeded */
     SSP_ERR_CUDA = -3,        /* a CUDA call failed */
-    SSP_ERR_TIMEOUT = -4,     /* a bounded wait expired */
+    SSP_ERR_TIMEOUT = -4,     /* a bounded wait expired (serving: stall_ms) */
     SSP_ERR_UNSUPPORTED = -5, /* valid request this build cannot run */
     SSP_ERR_BUSY = -6,        /* serving: too many requests in flight */
     SSP_PENDING = 1           /* serving: the request has not finished yet */
@@ -123,8 +124,8 @@ void ssp_default_params(ssp_params *p);
  * batches sized to hbm_fraction of free device memory (Eq. 1's role).
  * Errors: SSP_ERR_ARG (any rule above, n_objects < 1, n_freq < 1, bad
  * params), SSP_ERR_NOMEM (one object's minimum batch does not fit),
- * SSP_ERR_UNSUPPORTED (periodic = 0; FP32C with a weight outside the float
- * range), SSP_ERR_CUDA.
+ * SSP_ERR_UNSUPPORTED (FP32C with a weight outside the float range),
+ * SSP_ERR_CUDA.
  */
 int ssp_periodogram(const double *t, const double *y, const double *dy,
                     const int64_t *n_per_object, int64_t n_objects,
@@ -162,9 +163,10 @@ int ssp_fold_fixed(const double *tt, int64_t n, double f, uint64_t *out);
 /*
  * ssp_periodogram_device without any device allocation.  (The paper has no
  * counterpart; this entry point exists for callers that cannot call
- * cudaMalloc: code running while a stream is being captured into a CUDA
- * graph, programs whose device memory is owned by another allocator or
- * capped by a memory pool, and hosts that forbid allocation after start-up.)
+ * cudaMalloc: programs whose device memory is owned by another allocator or
+ * capped by a memory pool, which would see the library's own allocations
+ * fail or overrun their budget, and services that forbid allocation after
+ * start-up because an allocation can block or fail at an arbitrary time.)
  * Arguments and results are those of ssp_periodogram_device; inputs and
  * outputs are still the caller's device buffers, and n_per_object is a host
  * array.  Temporary storage is a fixed 8 MiB array in device memory that
@@ -205,6 +207,9 @@ typedef struct {
                                launch at once */
     int64_t max_in_flight;  /* requests submitted and not yet collected by
                                ssp_server_poll; <= 0: 1 << 20 */
+    double stall_ms;        /* bounded wait for a batch on the GPU: a batch not
+                               finished this long after it was launched ends
+                               its requests with SSP_ERR_TIMEOUT; <= 0: 60000 */
 } ssp_server_config;
 
 /*
@@ -238,9 +243,10 @@ int ssp_server_next(ssp_server *s, int wait_ms, int64_t *out_ticket);
  * values, double for SSP_FP64 and float for SSP_FP32C) and
  * *out_best_period hold the results, *out_latency_ms (if not NULL) the time
  * from submission to completion, and the ticket is retired.  SSP_PENDING: not
- * finished yet.  The request's own error status (e.g. SSP_ERR_NOMEM) if its
- * batch failed; the ticket is retired.  SSP_ERR_ARG: unknown or retired
- * ticket.
+ * finished yet.  The request's own error status (e.g. SSP_ERR_NOMEM, or
+ * SSP_ERR_TIMEOUT when its batch outlived stall_ms) if its batch failed; the
+ * ticket is retired and the server keeps serving.  SSP_ERR_ARG: unknown or
+ * retired ticket.
  */
 int ssp_server_poll(ssp_server *s, int64_t ticket, int wait_ms, void *out_power,
                     double *out_best_period, double *out_latency_ms);
@@ -300,6 +306,22 @@ int ssp_search_refine(const double *t, const double *y, const double *dy,
                       int64_t n_coarse, ssp_variant coarse_variant, ssp_variant fine_variant,
                       int n_peaks, int n_fine, const ssp_params *params, double *out_best_period,
                       double *out_best_power);
+
+/*
+ * Testing only (the paper has no counterpart): host-side fault injection, so
+ * that tests reach the failure paths without faulting a GPU.  Honoured only
+ * while SSP_TESTING=1 is set in the environment (else SSP_ERR_UNSUPPORTED).
+ *   SSP_FAULT_ALLOC  the library's next `count` device allocations fail as
+ *                    if the device were out of memory: the entry point (or
+ *                    the served request) returns SSP_ERR_NOMEM and nothing
+ *                    is left allocated or enqueued;
+ *   SSP_FAULT_STALL  the serving worker treats its next `count` batches as
+ *                    not finished within stall_ms: their requests end with
+ *                    SSP_ERR_TIMEOUT (the batches themselves complete).
+ * count 0 clears the kind.  Errors: SSP_ERR_ARG (unknown kind, count < 0).
+ */
+enum { SSP_FAULT_ALLOC = 1, SSP_FAULT_STALL = 2 };
+int ssp_test_fault(int kind, int count);
 
 /* Static text for a status code. */
 const char *ssp_status_string(int status);

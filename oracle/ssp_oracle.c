@@ -181,6 +181,28 @@ static double window_fit(int n, const double *x, const double *v, const double *
     return vm + a * dxj;
 }
 
+/* Whether every point of j's window other than j has one abscissa: then the
+ * leave-one-out line through them does not exist (it has no slope to reach
+ * x_j), and with the slope in use j's leverage w_j h_j is exactly 1. */
+static int others_share_abscissa(int n, const double *x, int ibw, int periodic, int j)
+{
+    int lo = window_lo(n, ibw, periodic, j);
+    int first = 1;
+    double x0 = 0.0;
+    for (int e = lo; e <= lo + 2 * ibw; e++) {
+        if (e == j) continue;   /* the centre's own slot */
+        double xe;
+        slot_point(n, e, x, &xe);
+        if (first) {
+            x0 = xe;
+            first = 0;
+        } else if (xe != x0) {
+            return 0;
+        }
+    }
+    return 1;
+}
+
 void ssp_oracle_runline_raw(int n, const double *x, const double *v, const double *w,
                             double span, int iper, double vsmlsq, double *smo,
                             double *acvr)
@@ -188,17 +210,22 @@ void ssp_oracle_runline_raw(int n, const double *x, const double *v, const doubl
     int periodic = (abs(iper) == 2);
     int ibw = ssp_oracle_half_width(n, span);
     for (int j = 0; j < n; j++) {
-        double h;
-        smo[j] = window_fit(n, x, v, w, ibw, periodic, j, vsmlsq, &h, NULL);
+        double h, sxx;
+        smo[j] = window_fit(n, x, v, w, ibw, periodic, j, vsmlsq, &h, &sxx);
         if (iper > 0) {
             /* cross-validated residual: exact leave-one-out residual of a
-             * linear smoother; when the leverage reaches 1 the previous
-             * point's value is kept (0 for the first point).  Leverage 1
-             * is exact for some windows (a point alone at one end of a
-             * clamped window, the rest tied), where 1 - w h is rounding
-             * noise of either sign: within 1e-10 of 1 counts as reached. */
+             * linear smoother, |v_j - s_j| / (1 - w_j h_j).  When j's
+             * leverage reaches 1 the previous point's value is kept (0 for
+             * the first point).  Leverage 1 is decided exactly, not from the
+             * computed 1 - w h: it is 1 when the slope is in use and every
+             * other point of the window shares one abscissa (a point alone at
+             * one end of a clamped window, the rest tied), where 1 - w h is
+             * rounding noise of either sign whose size grows as the lone
+             * point nears the others.  A 1 - w h that rounds to 0 or below
+             * (weights apart by more than 1/u) is taken as 1 as well. */
             double den = 1.0 - w[j] * h;
-            if (den > 1.0e-10) acvr[j] = fabs(v[j] - smo[j]) / den;
+            int lev1 = (sxx > vsmlsq) && others_share_abscissa(n, x, ibw, periodic, j);
+            if (den > 0.0 && !lev1) acvr[j] = fabs(v[j] - smo[j]) / den;
             else acvr[j] = (j > 0) ? acvr[j - 1] : 0.0;
         }
     }

@@ -107,6 +107,36 @@ size_t pgram_frame_bytes(int p, int n, int variant, bool keep_perm, bool smo_out
 
 using namespace ssp;
 
+namespace ssp_internal {
+std::atomic<int> g_fault_alloc{0}, g_fault_stall{0};
+
+bool testing()
+{
+    const char *e = std::getenv("SSP_TESTING");
+    return e && std::strcmp(e, "1") == 0;
+}
+
+// one countdown step of an injected fault: true while the count lasts
+static bool take_fault(std::atomic<int> &c)
+{
+    int v = c.load();
+    while (v > 0)
+        if (c.compare_exchange_weak(v, v - 1)) return true;
+    return false;
+}
+
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s)
+{
+    if (take_fault(g_fault_alloc)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;   // as the allocator reports it; nothing was allocated
+    }
+    return cudaMallocAsync(p, bytes, s);
+}
+
+bool stall_injected() { return take_fault(g_fault_stall); }
+}  // namespace ssp_internal
+
 namespace {
 
 thread_local std::string g_err;
@@ -174,7 +204,8 @@ int check_shape(const int64_t *n_per_object, int64_t n_objects, int64_t n_freq, 
 
 // Objects are planned in length ranges; the objects of one range share a
 // launch.  Threads per CTA by default: about a dozen centres per thread
-// (SSP_GROUP_SCALE, a power of two, scales the rule for calibration).  FP32C
+// (SSP_GROUP_SCALE, a power of two, scales the rule for calibration under
+// SSP_TESTING=1; read once per process).  FP32C
 // SS objects above 2048 points take 256 threads when pass A's smooths live
 // in the global slab (their frame then leaves room for two CTAs per SM), and
 // 512 otherwise (one CTA per SM: 16 warps hide more latency than 8; the FP64
@@ -194,7 +225,7 @@ int range_of(int n)
 int group_size_rule(int n, int variant, int precision, bool smo_ok = true)
 {
     static const int scale = [] {
-        const char *e = std::getenv("SSP_GROUP_SCALE");
+        const char *e = ssp_internal::testing() ? std::getenv("SSP_GROUP_SCALE") : nullptr;
         const int v = e ? std::atoi(e) : 0;
         return (v == 2 || v == 4 || v == -2 || v == -4) ? v : 1;
     }();
@@ -375,9 +406,11 @@ size_t rsize(int precision) { return precision == SSP_FP64 ? 8 : 4; }
 
 // FP32C margins, overridable for testing and tuning by SSP_NEAR_SS,
 // SSP_NEAR_SP, SSP_SENS_TAU, SSP_SENS_ULPS and SSP_REFIT_FRAC (a value of 1e6
-// or more keeps the default; a negative margin disables its test)
+// or more keeps the default; a negative margin disables its test), honoured
+// only while SSP_TESTING=1: a stray variable cannot change the numerics
 float near_margin(const char *env, float dflt)
 {
+    if (!ssp_internal::testing()) return dflt;
     const char *e = std::getenv(env);
     if (e && *e) {
         const double v = std::atof(e);
@@ -547,7 +580,7 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
     const int64_t N = off[n_obj];
     const size_t ws = workspace_bytes(plan, n_obj, N, n_freq, prec);
     unsigned char *base = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&base, ws, s);
+    cudaError_t e = ssp_internal::dev_alloc((void **)&base, ws, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(SSP_ERR_NOMEM, "workspace of %zu bytes: %s", ws, cudaGetErrorString(e));
@@ -932,6 +965,18 @@ const char *ssp_last_error(void) { return g_err.c_str(); }
 
 const char *ssp_version(void) { return "ssp 0.1 sm_103a"; }
 
+int ssp_test_fault(int kind, int count)
+{
+    g_err.clear();
+    if (!ssp_internal::testing())
+        return fail(SSP_ERR_UNSUPPORTED, "fault injection needs SSP_TESTING=1 in the environment");
+    if (count < 0) return fail(SSP_ERR_ARG, "count must be >= 0");
+    if (kind == SSP_FAULT_ALLOC) ssp_internal::g_fault_alloc.store(count);
+    else if (kind == SSP_FAULT_STALL) ssp_internal::g_fault_stall.store(count);
+    else return fail(SSP_ERR_ARG, "unknown fault kind %d", kind);
+    return SSP_OK;
+}
+
 int ssp_fold_fixed(const double *tt, int64_t n, double f, uint64_t *out)
 {
     g_err.clear();
@@ -1057,10 +1102,15 @@ int ssp_periodogram(const double *t, const double *y, const double *dy,
     // batch objects so that inputs, outputs and working storage fit the budget
     int status = SSP_OK;
     double *d_freq = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&d_freq, 8 * (size_t)n_freq, s);
+    cudaError_t e = ssp_internal::dev_alloc((void **)&d_freq, 8 * (size_t)n_freq, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_freq, freq_grid, 8 * (size_t)n_freq, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) status = cuda_fail(e, "frequency grid");
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        status = fail(SSP_ERR_NOMEM, "frequency grid of %lld values", (long long)n_freq);
+    } else if (e != cudaSuccess) {
+        status = cuda_fail(e, "frequency grid");
+    }
     int64_t o0 = 0, p0 = 0;
     while (status == SSP_OK && o0 < n_objects) {
         // grow the batch while its estimate fits
@@ -1077,7 +1127,7 @@ int ssp_periodogram(const double *t, const double *y, const double *dy,
         const int64_t nb = o1 - o0;
         unsigned char *blk = nullptr;
         const size_t in_b = 8 * (size_t)pts, pw_b = rs * (size_t)nb * (size_t)n_freq;
-        e = cudaMallocAsync((void **)&blk, 3 * align16(in_b) + align16(pw_b) + align16(8 * nb), s);
+        e = ssp_internal::dev_alloc((void **)&blk, 3 * align16(in_b) + align16(pw_b) + align16(8 * nb), s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             status = fail(SSP_ERR_NOMEM, "batch of %lld objects does not fit", (long long)nb);
@@ -1227,7 +1277,7 @@ int ssp_autotune(const double *t, const double *y, const double *dy, const int64
         unsigned char *blk = nullptr;
         const size_t a = align16(8 * (size_t)pts), bf = align16(8 * (size_t)F),
                      bp = align16(rs * (size_t)nob * (size_t)F), bb = align16(8 * (size_t)nob);
-        cudaError_t e = cudaMallocAsync((void **)&blk, 3 * a + bf + bp + bb, s);
+        cudaError_t e = ssp_internal::dev_alloc((void **)&blk, 3 * a + bf + bp + bb, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             status = fail(SSP_ERR_NOMEM, "autotune sample does not fit");
@@ -1339,7 +1389,7 @@ int ssp_search_refine(const double *t, const double *y, const double *dy,
     const double budget = P.hbm_fraction * (double)free_b - kSlabReserve;
     int status = SSP_OK;
     double *d_coarse = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&d_coarse, 8 * (size_t)n_coarse, s);
+    cudaError_t e = ssp_internal::dev_alloc((void **)&d_coarse, 8 * (size_t)n_coarse, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_coarse, coarse_grid, 8 * (size_t)n_coarse, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) status = cuda_fail(e, "coarse grid");
@@ -1361,7 +1411,7 @@ int ssp_search_refine(const double *t, const double *y, const double *dy,
         const size_t fp_b = align16(rs * (size_t)(nb * nf)), fg_b = align16(8 * (size_t)(nb * nf));
         const size_t ob_b = align16(8 * (size_t)nb);
         unsigned char *blk = nullptr;
-        e = cudaMallocAsync((void **)&blk, 3 * in_b + cp_b + fp_b + fg_b + 4 * ob_b, s);
+        e = ssp_internal::dev_alloc((void **)&blk, 3 * in_b + cp_b + fp_b + fg_b + 4 * ob_b, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             status = fail(SSP_ERR_NOMEM, "batch of %lld objects does not fit", (long long)nb);

@@ -1255,6 +1255,18 @@ __device__ inline void win_slide(Win<R, NCH> &s, const Frame<R> &fr, const R *co
     win_add<R, NCH, DIFF>(s, fr, v, j + h + 1, n, o, R(1));
 }
 
+// Binary64 kernels: the fit of the window of centre j recomputed in two
+// passes (weighted means, then centred sums), and 1 - w_j h_j from it.
+template <typename R>
+__device__ inline void cv_refit(Fit<R, 1> &f, R &d, const Frame<R> &fr, const R *const *v, int j,
+                                int h, int n, R vsmlsq, R wj)
+{
+    Chans<R, 1> cv;
+    cv.p[0] = v[0];
+    f = win_refit_fp64<R, 1, false>(fr.XW, fr.per, cv, j, h, n, (double)vsmlsq);
+    d = R(1) - wj * (f.rW + f.dxj * f.dxj * f.rS);
+}
+
 // ---------------------------------------------------------------------------
 // Listing 1 pieces shared by SS and SP
 // ---------------------------------------------------------------------------
@@ -1373,6 +1385,26 @@ template <typename R>
 __device__ inline bool tie_next(const Frame<R> &fr, int j)
 {
     return (fr.tie[j >> 5] >> (j & 31)) & 1u;
+}
+
+// Whether the window (half width h) of centre j holds j alone beside points
+// that all share one abscissa: then the leave-one-out line does not exist and,
+// with the slope in use, j's leverage is exactly 1.  Only a clamped window's
+// first or last point can be so (in a centred window the centre lies between
+// its neighbours' abscissae, which would then equal its own; a periodic
+// window's wrapped points sit a period away); the tie bits tell.
+template <typename R>
+__device__ inline bool lev_one_end(const Frame<R> &fr, int j, int h, int n)
+{
+    if (fr.per) return false;
+    const int lo = win_lo(fr, j, h, n);
+    int a, b;   // pairs (i, i + 1) for i in [a, b) must all be tied
+    if (j == lo) { a = lo + 1; b = lo + 2 * h; }
+    else if (j == lo + 2 * h) { a = lo; b = lo + 2 * h - 1; }
+    else return false;
+    for (int i = a; i < b; ++i)
+        if (!tie_next(fr, i)) return false;
+    return true;
 }
 
 template <typename R, int K, typename Emit>
@@ -1568,6 +1600,7 @@ struct ObjK {
     // generalized-validation factors 1 / (1 - nu/m) of the three windows (m
     // points) for a line (nu = 2) and a constant (nu = 1)
     R gl0, gc0, gl1, gc1, gl2, gc2;
+
     float margin;         // SS: tweeter-vs-midrange margin
     R sens_lim, ymax;     // SP: chi2 budget per point, largest centred magnitude
 };
@@ -2047,17 +2080,30 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
                 win_fit_checked<R, 1>(f1, w1, fr, vy, j, h1, n, o, vsmlsq, near, rf);
                 win_fit_checked<R, 1>(f2, w2, fr, vy, j, h2, n, o, vsmlsq, near, rf);
                 const R yj = fr.Y[j], wj = fr.XW[j].y;
-                const R d0 = R(1) - wj * (f0.rW + f0.dxj * f0.dxj * f0.rS);
-                const R d1 = R(1) - wj * (f1.rW + f1.dxj * f1.dxj * f1.rS);
-                const R d2 = R(1) - wj * (f2.rW + f2.dxj * f2.dxj * f2.rS);
+                R d0 = R(1) - wj * (f0.rW + f0.dxj * f0.dxj * f0.rS);
+                R d1 = R(1) - wj * (f1.rW + f1.dxj * f1.dxj * f1.rS);
+                R d2 = R(1) - wj * (f2.rW + f2.dxj * f2.dxj * f2.rS);
                 if (sizeof(R) == 4 && fmin(fmin(fabs(d0), fabs(d1)), fabs(d2)) < (R)kNearLev)
                     near = true;
-                // leverage within 1e-10 of 1 counts as 1 (it is exactly 1 for
-                // some clamped windows, and 1 - w h is then rounding noise);
-                // FP32C flags any 1 - w h below kNearLev for the FP64 redo
-                fr.C[1][j] = d0 > R(1e-10) ? fdiv(fabs(yj - f0.s[0]), d0) : R(-1);
-                fr.C[3][j] = d1 > R(1e-10) ? fdiv(fabs(yj - f1.s[0]), d1) : R(-1);
-                fr.C[5][j] = d2 > R(1e-10) ? fdiv(fabs(yj - f2.s[0]), d2) : R(-1);
+                if (sizeof(R) == 8) {
+                    // 1 - w h near 0: its sliding-sum value carries the sums'
+                    // history; refit that window in two passes, as the
+                    // definition reads, before the leverage test below
+                    if (d0 < R(1e-6)) cv_refit<R>(f0, d0, fr, vy, j, h0, n, vsmlsq, wj);
+                    if (d1 < R(1e-6)) cv_refit<R>(f1, d1, fr, vy, j, h1, n, vsmlsq, wj);
+                    if (d2 < R(1e-6)) cv_refit<R>(f2, d2, fr, vy, j, h2, n, vsmlsq, wj);
+                }
+                // Leverage 1 is decided exactly: the slope in use and every
+                // other point of the window tied (only a clamped window's end
+                // point can be alone so), where 1 - w h is rounding noise; or
+                // 1 - w h rounding to 0 or below.  FP32C flags any 1 - w h
+                // below kNearLev for the FP64 recompute as well.
+                const bool l0 = ties && f0.slope && lev_one_end(fr, j, h0, n);
+                const bool l1 = ties && f1.slope && lev_one_end(fr, j, h1, n);
+                const bool l2 = ties && f2.slope && lev_one_end(fr, j, h2, n);
+                fr.C[1][j] = (d0 > R(0) && !l0) ? fdiv(fabs(yj - f0.s[0]), d0) : R(-1);
+                fr.C[3][j] = (d1 > R(0) && !l1) ? fdiv(fabs(yj - f1.s[0]), d1) : R(-1);
+                fr.C[5][j] = (d2 > R(0) && !l2) ? fdiv(fabs(yj - f2.s[0]), d2) : R(-1);
                 const R val[3] = {f0.s[0], f1.s[0], f2.s[0]};
                 run_push<R, 3>(ra, fr, j, ties, val, emit);
                 if (j + 1 < c1) {

@@ -24,6 +24,15 @@ int check_freq(const double *freq_grid, int64_t n_freq);
 
 // the device pipeline of ssp_periodogram_device (device t, y, dy, freq and
 // outputs; host n_per_object), enqueued on s
+// SSP_TESTING=1 in the environment: tuning overrides and fault injection on
+bool testing();
+// device allocation of the library's workspaces: cudaMallocAsync, or an
+// injected out-of-memory failure (ssp_test_fault, SSP_FAULT_ALLOC)
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s);
+// serving: true when the next batch is to be treated as stalled
+// (ssp_test_fault, SSP_FAULT_STALL)
+bool stall_injected();
+
 int run(const double *t, const double *y, const double *dy, const int64_t *n_per_object,
         int64_t n_objects, const double *freq, int64_t n_freq, ssp_variant variant,
         const ssp_params &p, void *out_power, double *out_best, cudaStream_t s);

@@ -32,6 +32,7 @@ using Clock = std::chrono::steady_clock;
 using ssp_internal::fail;
 
 constexpr double kDefaultBatchPtf = 4.0e9;
+constexpr double kDefaultStallMs = 60000.0;
 constexpr int64_t kDefaultInFlight = (int64_t)1 << 20;
 constexpr int kSlots = 2;
 constexpr int kVariants = 3;   // SSP_SS, SSP_SP, SSP_SPG
@@ -96,6 +97,7 @@ struct Slot {
     int status = SSP_OK;
     std::string err;
     bool busy = false;         // guarded by the server mutex
+    Clock::time_point t_launch;   // when the batch's work was enqueued
 };
 
 }  // namespace
@@ -127,6 +129,7 @@ namespace {
 // fills slot sl with its batch and enqueues the work on the slot's stream
 void launch_batch(ssp_server *S, Slot &sl, int variant)
 {
+    sl.t_launch = Clock::now();
     sl.status = SSP_OK;
     sl.err.clear();
     const int64_t nobj = (int64_t)sl.reqs.size();
@@ -258,10 +261,30 @@ void completer_main(ssp_server *S)
         S->launched.pop_front();
         Slot &sl = S->slots[k];
         lk.unlock();
-        const cudaError_t e = cudaEventSynchronize(sl.done);
+        // Bounded wait for the batch: past stall_ms its requests end with
+        // SSP_ERR_TIMEOUT at once, and the slot stays reserved until the GPU
+        // has finished with its buffers.  (An injected stall takes the same
+        // path after the batch completes normally.)
+        const auto deadline = sl.t_launch + std::chrono::duration_cast<Clock::duration>(
+                                                std::chrono::duration<double, std::milli>(
+                                                    S->cfg.stall_ms));
+        cudaError_t e = cudaEventQuery(sl.done);
+        bool timed_out = false;
+        while (e == cudaErrorNotReady) {
+            if (Clock::now() >= deadline) {
+                timed_out = true;
+                break;
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+            e = cudaEventQuery(sl.done);
+        }
+        if (ssp_internal::stall_injected()) timed_out = true;
         int status = sl.status;
         std::string err = sl.err;
-        if (status == SSP_OK && e != cudaSuccess) {
+        if (timed_out) {
+            status = SSP_ERR_TIMEOUT;
+            err = "batch did not finish within the server's stall limit";
+        } else if (status == SSP_OK && e != cudaSuccess) {
             status = SSP_ERR_CUDA;
             err = std::string("batch: ") + cudaGetErrorString(e);
         }
@@ -289,8 +312,15 @@ void completer_main(ssp_server *S)
             if (S->live.count(r->ticket)) S->finished.push_back(r->ticket);
         }
         sl.reqs.clear();
-        sl.busy = false;
         S->cv_done.notify_all();
+        if (timed_out) {
+            // the requests have their answer; the buffers are freed for the
+            // next batch only once the GPU is done with them
+            lk.unlock();
+            cudaEventSynchronize(sl.done);
+            lk.lock();
+        }
+        sl.busy = false;
         S->cv_launch.notify_one();
     }
 }
@@ -338,7 +368,9 @@ int ssp_server_create(const double *freq_grid, int64_t n_freq, const ssp_params 
     S->cfg.max_batch_ptf = kDefaultBatchPtf;
     S->cfg.max_wait_ms = 0.0;
     S->cfg.max_in_flight = kDefaultInFlight;
+    S->cfg.stall_ms = kDefaultStallMs;
     if (config) {
+        if (config->stall_ms > 0.0) S->cfg.stall_ms = config->stall_ms;
         if (config->max_batch_ptf > 0.0) S->cfg.max_batch_ptf = config->max_batch_ptf;
         if (config->max_wait_ms > 0.0) S->cfg.max_wait_ms = config->max_wait_ms;
         if (config->max_in_flight > 0) S->cfg.max_in_flight = config->max_in_flight;

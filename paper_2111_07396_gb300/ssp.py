@@ -20,6 +20,7 @@ SSP_FP64, SSP_FP32C = 0, 1
 SSP_OK, SSP_ERR_ARG, SSP_ERR_NOMEM, SSP_ERR_CUDA, SSP_ERR_TIMEOUT, SSP_ERR_UNSUPPORTED = (
     0, -1, -2, -3, -4, -5)
 SSP_ERR_BUSY, SSP_PENDING = -6, 1
+SSP_FAULT_ALLOC, SSP_FAULT_STALL = 1, 2
 VARIANTS = {"ss": SSP_SS, "sp": SSP_SP, "spg": SSP_SPG, SSP_SS: SSP_SS, SSP_SP: SSP_SP,
             SSP_SPG: SSP_SPG}
 PRECISIONS = {"fp64": SSP_FP64, "fp32c": SSP_FP32C, SSP_FP64: SSP_FP64, SSP_FP32C: SSP_FP32C}
@@ -37,7 +38,7 @@ class ssp_phase_time(ctypes.Structure):
 
 class ssp_server_config(ctypes.Structure):
     _fields_ = [("max_batch_ptf", ctypes.c_double), ("max_wait_ms", ctypes.c_double),
-                ("max_in_flight", ctypes.c_int64)]
+                ("max_in_flight", ctypes.c_int64), ("stall_ms", ctypes.c_double)]
 
 
 PHASES = ("prep", "pgram_ss", "pgram_sp", "redo", "argmax")
@@ -106,6 +107,8 @@ def lib():
                                         ctypes.c_int, ctypes.c_int, ctypes.POINTER(ssp_params), P,
                                         P]
         L.ssp_search_refine.restype = ctypes.c_int
+        L.ssp_test_fault.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.ssp_test_fault.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -276,6 +279,13 @@ def ssp_search_refine(t, y, dy, n_per_object, coarse_grid, coarse_variant="sp",
     return bp, bw
 
 
+def ssp_test_fault(kind, count=1) -> None:
+    """Testing only: make the library's next `count` device allocations fail
+    (SSP_FAULT_ALLOC) or its server's next `count` batches count as stalled
+    (SSP_FAULT_STALL).  Needs SSP_TESTING=1 in the environment."""
+    _check(lib().ssp_test_fault(int(kind), int(count)))
+
+
 def ssp_autotune_clear() -> None:
     lib().ssp_autotune_clear()
 
@@ -287,12 +297,13 @@ class Server:
     library's."""
 
     def __init__(self, freq_grid, precision="fp32c", alpha=9.0, spans=None, params=None,
-                 max_batch_ptf=0.0, max_wait_ms=0.0, max_in_flight=0):
+                 max_batch_ptf=0.0, max_wait_ms=0.0, max_in_flight=0, stall_ms=0.0):
         self._p = params if params is not None else ssp_default_params(precision, alpha, spans)
         self.freq = _f64(freq_grid)
         self.n_freq = int(self.freq.size)
         self.dtype = np.float64 if self._p.precision == SSP_FP64 else np.float32
-        cfg = ssp_server_config(float(max_batch_ptf), float(max_wait_ms), int(max_in_flight))
+        cfg = ssp_server_config(float(max_batch_ptf), float(max_wait_ms), int(max_in_flight),
+                                float(stall_ms))
         h = ctypes.c_void_p()
         _check(lib().ssp_server_create(_ptr(self.freq), self.n_freq, ctypes.byref(self._p),
                                        ctypes.byref(cfg), ctypes.byref(h)))

@@ -107,7 +107,7 @@ def test_server_rejects_bad_grid_and_params_before_cuda():
     assert ei.value.status == ssp.SSP_ERR_ARG
     assert ssp.ssp_status_string(ssp.SSP_ERR_BUSY) == "too many requests in flight"
     assert ssp.ssp_status_string(ssp.SSP_PENDING) == "pending"
-    assert ctypes.sizeof(ssp.ssp_server_config) == 24
+    assert ctypes.sizeof(ssp.ssp_server_config) == 32
     # calls on a NULL handle are argument errors, not crashes
     t = ctypes.c_int64()
     assert ssp.lib().ssp_server_next(None, 0, ctypes.byref(t)) == ssp.SSP_ERR_ARG
@@ -138,3 +138,22 @@ def test_search_refine_rejects_bad_arguments_before_cuda():
         with pytest.raises(ssp.SSPError) as ei:
             ssp.ssp_search_refine(**args)
         assert ei.value.status == ssp.SSP_ERR_ARG
+
+
+def test_fault_injection_is_off_unless_testing(monkeypatch):
+    # the failure hooks are test-only: without SSP_TESTING=1 they refuse
+    monkeypatch.delenv("SSP_TESTING", raising=False)
+    with pytest.raises(ssp.SSPError) as ei:
+        ssp.ssp_test_fault(ssp.SSP_FAULT_ALLOC, 1)
+    assert ei.value.status == ssp.SSP_ERR_UNSUPPORTED
+    monkeypatch.setenv("SSP_TESTING", "1")
+    with pytest.raises(ssp.SSPError) as ei:
+        ssp.ssp_test_fault(99, 1)
+    assert ei.value.status == ssp.SSP_ERR_ARG
+    with pytest.raises(ssp.SSPError) as ei:
+        ssp.ssp_test_fault(ssp.SSP_FAULT_STALL, -1)
+    assert ei.value.status == ssp.SSP_ERR_ARG
+    # arm and clear without touching a GPU
+    ssp.ssp_test_fault(ssp.SSP_FAULT_ALLOC, 2)
+    ssp.ssp_test_fault(ssp.SSP_FAULT_ALLOC, 0)
+    ssp.ssp_test_fault(ssp.SSP_FAULT_STALL, 0)

@@ -133,3 +133,48 @@ def test_cv_fallback_for_exact_leverage_one_at_a_clamped_end():
     # exists there, while every other residual is the leave-one-out one
     _, ref = brute.runline(x, v, w, 0.05, 1, 0.0, tie_average=False)
     np.testing.assert_allclose(acvr[:n - 1], ref[:n - 1], rtol=1e-9, atol=1e-11)
+
+
+def test_cv_fallback_is_decided_exactly_not_by_rounding():
+    # Periodic windows of 5 points.  A point 8e10 times heavier than its four
+    # neighbours has leverage 1 - w h of about 5e-11: no absolute cut-off
+    # near 0 may send it to the fallback, its cross-validated residual is the
+    # leave-one-out one.  The same point 1e20 times heavier rounds w h to 1:
+    # the fallback.
+    n = 11
+    g = np.random.default_rng(17)
+    x = np.sort(g.uniform(0.0, 1.0, n))
+    v = g.normal(0, 1, n)
+    w = np.ones(n)
+    j = 5
+    assert brute.half_width(n, 0.3) == 2
+    w[j] = 8e10
+    _, acvr = oracle.runline_raw(x, v, w, 0.3, 2, 0.0)
+    _, ref = brute.runline(x, v, w, 0.3, 2, 0.0, tie_average=False)
+    assert acvr[j] != acvr[j - 1]
+    np.testing.assert_allclose(acvr[j], ref[j], rtol=1e-4)
+    w[j] = 1e20
+    _, acvr = oracle.runline_raw(x, v, w, 0.3, 2, 0.0)
+    assert acvr[j] == acvr[j - 1]
+
+
+@pytest.mark.parametrize("gap", [1e-2, 1e-4, 1e-6, 1e-9])
+def test_cv_fallback_for_exact_leverage_one_whatever_the_gap(gap):
+    # The clamped end window of the last point holds four tied abscissae and
+    # the point itself, gap above them: its leverage is exactly 1 however
+    # small the gap, while the computed 1 - w h is rounding noise that grows
+    # as the gap shrinks (about 1e-13 already at 1e-4).  The residual must
+    # fall back to the previous one at every gap.
+    n = 12
+    g = np.random.default_rng(5)
+    x = np.sort(g.uniform(0.0, 0.8, n))
+    x[n - 5:n - 1] = 0.85
+    x[n - 1] = 0.85 + gap
+    v = g.normal(0, 1, n)
+    w = g.uniform(0.5, 2.0, n)
+    _, acvr = oracle.runline_raw(x, v, w, 0.05, 1, 0.0)
+    assert acvr[n - 1] == acvr[n - 2]
+    _, ref = brute.runline(x, v, w, 0.05, 1, 0.0, tie_average=False)
+    # (the other residuals come from nearly coincident abscissae at the
+    # smallest gap: both computations lose about log10(1/gap) digits)
+    np.testing.assert_allclose(acvr[:n - 1], ref[:n - 1], rtol=1e-5, atol=1e-11)
