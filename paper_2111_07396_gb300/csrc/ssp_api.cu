@@ -259,7 +259,8 @@ struct LaunchCfg {
     bool cnt_smem = false;   // gmem: the sort's bucket counts in shared memory
     bool lng = false;        // SS kernel that initialises windows out of line
     bool smo_out = false;    // SS: pass A's smooths in the global slab
-    size_t smem = 0, slab_bytes = 0, smo_stride = 0;
+    bool redo_inline = false; // SS: flagged frequencies recomputed in binary64 in the kernel
+    size_t smem = 0, slab_bytes = 0, smo_stride = 0, redo_slab_bytes = 0;
     int grid = 0;
 };
 
@@ -274,7 +275,7 @@ struct Bucket {
 
 struct Plan {
     std::vector<Bucket> buckets;
-    size_t items_total = 0, slab_total = 0, smo_total = 0;
+    size_t items_total = 0, slab_total = 0, smo_total = 0, redo_total = 0;
     bool redo = false;
 };
 
@@ -301,6 +302,10 @@ int configure(int precision, int variant, bool per, bool shared, int G, int n_ma
                              (per || shared);
     c.smo_out = smo_ok && long_kernel;
     c.smo_stride = c.smo_out ? align16(smo_bytes(n_max, G, 4)) : 0;
+    // the same kernels recompute their flagged frequencies in binary64 at once,
+    // in per-CTA binary64 frames in global memory
+    c.redo_inline = c.smo_out;
+    c.redo_slab_bytes = c.redo_inline ? align16(pgram_frame_bytes(kPrecRedo, n_max, variant, false)) : 0;
     const size_t small = align16(pgram_small_bytes(precision, G, variant));
     const size_t frame = align16(pgram_frame_bytes(precision, n_max, variant, shared, c.smo_out));
     c.gmem = small + frame + 1024 > max_smem;
@@ -366,6 +371,7 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
     plan.items_total = 0;
     plan.slab_total = 0;
     plan.smo_total = 0;
+    plan.redo_total = 0;
     for (Bucket &b : plan.buckets) {
         rc = configure(precision, variant, per, b.shared, b.G, b.n_max, sms, max_smem, b.main, smo_ok);
         if (rc) return rc;
@@ -397,7 +403,9 @@ int build_plan(const int64_t *npo, int64_t n_obj, int64_t n_freq, int precision,
         plan.items_total += b.items.size();
         plan.slab_total += b.main.gmem ? b.main.slab_bytes * (size_t)b.main.grid : 0;
         plan.smo_total += b.main.smo_stride * (size_t)b.main.grid;
-        if (plan.redo && b.redo.gmem) plan.slab_total += b.redo.slab_bytes * (size_t)b.redo.grid;
+        plan.redo_total += b.main.redo_slab_bytes * (size_t)b.main.grid;
+        if (plan.redo && b.redo.gmem && !b.main.redo_inline)
+            plan.slab_total += b.redo.slab_bytes * (size_t)b.redo.grid;
     }
     return SSP_OK;
 }
@@ -436,6 +444,7 @@ size_t workspace_bytes(const Plan &plan, int64_t n_obj, int64_t n_points, int64_
     if (plan.redo) b += align16((size_t)n_obj * (size_t)n_freq);  // near flags
     b += plan.slab_total;
     b += plan.smo_total;
+    b += plan.redo_total;
     return b;
 }
 
@@ -639,7 +648,7 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
         bool on = prof_begin(SSP_PHASE_PREP, s, mk);
         if ((e = prep_launch(prec, pa, (int)n_obj, s))) break;
         prof_end(on, mk, s);
-        size_t item_base = 0, slab_cur = 0, smo_cur = 0;
+        size_t item_base = 0, slab_cur = 0, smo_cur = 0, redo_cur = 0;
         for (size_t k = 0; k < plan.buckets.size(); ++k) {
             const Bucket &b = plan.buckets[k];
             PgramArgs ga{};
@@ -669,6 +678,10 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
             ga.smo_kmax = smo_rows(b.n_max, b.G);
             ga.smo_nmax = b.n_max;
             smo_cur += b.main.smo_stride * (size_t)b.main.grid;
+            ga.redo_slab = b.main.redo_inline ? d_slab + plan.slab_total + plan.smo_total + redo_cur
+                                              : nullptr;
+            ga.redo_slab_bytes = b.main.redo_slab_bytes;
+            redo_cur += b.main.redo_slab_bytes * (size_t)b.main.grid;
             ga.slab_bytes = b.main.slab_bytes;
             ga.cnt_smem = b.main.cnt_smem ? 1 : 0;
             ga.near = d_near;
@@ -688,13 +701,14 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
                                   ga, s)))
                 break;
             prof_end(on, mk, s);
-            if (plan.redo) {
+            if (plan.redo && !b.main.redo_inline) {
                 // the same items through the FP64 kernel, flagged frequencies only
                 ga.yc = d_yc64;
                 ga.wv = d_wv64;
                 ga.item_counter = d_counters + 2 * k + 1;
                 ga.slab = b.redo.gmem ? d_slab + slab_cur : nullptr;
                 ga.smo = nullptr;
+                ga.redo_slab = nullptr;
                 ga.slab_bytes = b.redo.slab_bytes;
                 ga.cnt_smem = b.redo.cnt_smem ? 1 : 0;
                 ga.recompute = 1;

@@ -114,6 +114,11 @@ struct PgramArgs {
     void *smo;
     size_t smo_stride;      // bytes per CTA
     int smo_kmax, smo_nmax;
+    // FP32C SS, long objects: a flagged frequency is recomputed in binary64
+    // by the same CTA right away (null: flags for the recompute launch).
+    // Per-CTA binary64 frames in global memory of redo_slab_bytes each.
+    unsigned char *redo_slab;
+    size_t redo_slab_bytes;
 };
 
 // rows of the smooth slab's per-thread part: twice the mean chunk length
@@ -2228,6 +2233,30 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
     return chi2_result(chi2, near, sm.red, sm.ired);
 }
 
+// The binary64 recompute of one flagged SS frequency inside an FP32C kernel
+// (long objects), on the binary64 inputs: the same code path, launch shape and
+// therefore results as the separate recompute launch, but run by the CTA that
+// flagged the frequency, right away.  Its FP64-pipe work then overlaps other
+// CTAs' FP32 work instead of a launch of its own whose time is the latency of
+// one frequency on one SM.  The frame lives in this CTA's global slab, the
+// chunk table and prefixes in the shared region of the FP32 path (the same
+// size: both accumulate in 8-byte numbers).  The chi2 is valid on thread 0.
+template <bool PER>
+__device__ __noinline__ double redo_ss_binary64(const PgramArgs a, int obj, int lead, int n, double f,
+                                                unsigned char *smem, unsigned char *slab)
+{
+    Small<double, double> sm = carve_small<double, double>(smem, blockDim.x, VAR_SS);
+    sm.dn = divn_make(n);
+    Frame<double> fr = carve_frame<double>(slab, n, VAR_SS, false, false);
+    fr.per = PER;
+    PgramArgs b = a;
+    b.yc = a.yc64;
+    b.wv = a.wv64;
+    b.smo = nullptr;
+    const ObjK<double> ok = obj_consts<double>(b, n, obj);
+    return process_frequency<double, VAR_SS, false, double>(b, ok, obj, lead, n, f, fr, sm, false).chi2;
+}
+
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
@@ -2241,11 +2270,12 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
 {
     typedef typename AccSel<R, PLAIN>::T A;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_item;
+    __shared__ int s_item, s_redo;
     const int G = blockDim.x;
     Small<R, A> sm = carve_small<R, A>(smem, G, VARIANT);
     unsigned char *big = GMEM ? a.slab + (size_t)blockIdx.x * a.slab_bytes
                               : smem + align16(small_bytes<A>(G, VARIANT));
+    if (threadIdx.x == 0) s_redo = 0;   // (the item fetch's barrier orders this)
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(a.item_counter, 1);
         __syncthreads();
@@ -2275,11 +2305,11 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
                 if (a.recompute && (bad || a.near[at] == 0)) continue;   // block-uniform
                 double pw = 0.0;
                 bool near = false;
+                const double fq = a.freq[(a.fbase ? a.fbase[o] : 0) + q];
                 if (bad) {
                     pw = __longlong_as_double(0x7ff8000000000000LL);
                 } else {
                     if (SHARED && k > 0) ok = obj_consts<R>(a, n, obj);
-                    const double fq = a.freq[(a.fbase ? a.fbase[o] : 0) + q];
                     const FreqResult r = process_frequency<R, VARIANT, LONG>(a, ok, obj, o, n, fq, fr,
                                                                              sm, SHARED && sorted);
                     sorted = true;
@@ -2290,12 +2320,28 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
                         near = r.near;
                     }
                 }
+                constexpr bool kInline = LONG && VARIANT == VAR_SS && sizeof(R) == 4;
+                const bool inl = kInline && a.redo_slab != nullptr;
                 if (threadIdx.x == 0) {
                     if (a.power_f32) ((float *)a.power)[at] = (float)pw;
                     else ((double *)a.power)[at] = pw;
-                    if (near && a.near) a.near[at] = 1;
+                    if (near && inl) s_redo = 1;
+                    else if (near && a.near) a.near[at] = 1;
                 }
                 __syncthreads();
+                if constexpr (kInline) {
+                    if (inl && s_redo) {   // block-uniform
+                        const double c2 = redo_ss_binary64<PER>(
+                            a, obj, o, n, fq, smem, a.redo_slab + (size_t)blockIdx.x * a.redo_slab_bytes);
+                        if (threadIdx.x == 0) {
+                            const double c0 = a.chi0[obj];
+                            ((float *)a.power)[at] = (float)((c0 > 0.0) ? 1.0 - c2 / c0 : 0.0);
+                            s_redo = 0;
+                        }
+                        sorted = false;    // the recompute used the shared scratch
+                        __syncthreads();
+                    }
+                }
             }
         }
     }
