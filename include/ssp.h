@@ -192,10 +192,17 @@ int ssp_periodogram_device_noalloc(const double *t, const double *y, const doubl
  * Serving: one light curve per request, results collected asynchronously.
  * (The paper's batches are whole catalogs, Sec. 4.3; a survey alert stream
  * instead delivers objects one at a time.)  A server owns one frequency grid,
- * one parameter set and a worker on the current device.  It gathers queued
- * requests of one variant into a batch, at most max_batch_ptf points x
- * frequencies.  Two batches are in flight at once: while one computes, the
- * next is copied in.  Each batch runs the pipeline of ssp_periodogram_device.
+ * one parameter set and two workers on the current device, and batches
+ * continuously under a device-memory budget:
+ *  - admission: a submitted request waits on the host until its inputs fit
+ *    the device arena (device_bytes, one ring per variant); it is then
+ *    uploaded and stays resident on the device until its batch has finished;
+ *  - batching: whenever one of `slots` batch slots is free, the oldest
+ *    admitted requests of one variant (at most max_batch_ptf points x
+ *    frequencies) run the pipeline of ssp_periodogram_device on the slot's
+ *    stream, reading their inputs in place; batches overlap on the GPU;
+ *  - completion: each batch's requests finish when it does, in completion
+ *    order, not launch order.
  * A request's results are identical to ssp_periodogram on that object alone,
  * whatever else is in flight.
  */
@@ -210,13 +217,18 @@ typedef struct {
     double stall_ms;        /* bounded wait for a batch on the GPU: a batch not
                                finished this long after it was launched ends
                                its requests with SSP_ERR_TIMEOUT; <= 0: 60000 */
+    int64_t slots;          /* batches on the GPU at once, at most 16; <= 0: 4 */
+    double device_bytes;    /* device arena holding admitted requests' inputs
+                               (t, y, dy), split evenly over the three
+                               variants; <= 0: 768 MiB */
 } ssp_server_config;
 
 /*
  * Creates a server for freq_grid (host, n_freq values, copied) and params
  * (NULL = defaults; copied); config NULL = defaults.  *out receives the
- * handle.  Errors: SSP_ERR_ARG (grid or params), SSP_ERR_UNSUPPORTED,
- * SSP_ERR_CUDA (no device).
+ * handle.  Errors: SSP_ERR_ARG (grid, params, more than 16 slots),
+ * SSP_ERR_UNSUPPORTED, SSP_ERR_NOMEM (the arena does not fit), SSP_ERR_CUDA
+ * (no device).
  */
 int ssp_server_create(const double *freq_grid, int64_t n_freq, const ssp_params *params,
                       const ssp_server_config *config, ssp_server **out);
@@ -226,7 +238,8 @@ int ssp_server_create(const double *freq_grid, int64_t n_freq, const ssp_params 
  * call returns.  *out_ticket receives the request's ticket (increasing from
  * 1).  Errors: SSP_ERR_ARG (the value rules of ssp_periodogram, n outside
  * 4..65535), SSP_ERR_UNSUPPORTED, SSP_ERR_BUSY (max_in_flight requests are
- * submitted and not yet collected; nothing is queued).
+ * submitted and not yet collected; nothing is queued), SSP_ERR_NOMEM (the
+ * object alone exceeds its variant's share of the device arena).
  */
 int ssp_server_submit(ssp_server *s, const double *t, const double *y, const double *dy,
                       int64_t n, ssp_variant variant, int64_t *out_ticket);
@@ -252,7 +265,7 @@ int ssp_server_poll(ssp_server *s, int64_t ticket, int wait_ms, void *out_power,
                     double *out_best_period, double *out_latency_ms);
 
 /*
- * Stops the worker after the batches already on the GPU complete; queued and
+ * Stops the workers after the batches already on the GPU complete; queued and
  * uncollected requests are dropped.  Frees everything the server holds.
  */
 int ssp_server_destroy(ssp_server *s);

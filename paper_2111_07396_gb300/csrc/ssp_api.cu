@@ -935,6 +935,17 @@ int check_freq(const double *freq_grid, int64_t n_freq)
             return ::fail(SSP_ERR_ARG, "freq_grid[%lld] must be finite and > 0", (long long)q);
     return SSP_OK;
 }
+int64_t device_bytes(const int64_t *n_per_object, int64_t n_objects, int64_t n_freq,
+                     ssp_variant variant, const ssp_params &p)
+{
+    Plan plan;
+    const int rc = build_plan(n_per_object, n_objects, n_freq, (int)p.precision,
+                              kernel_variant(variant, p), p.periodic != 0, plan);
+    if (rc) return rc;
+    int64_t N = 0;
+    for (int64_t o = 0; o < n_objects; ++o) N += n_per_object[o];
+    return (int64_t)workspace_bytes(plan, n_objects, N, n_freq, (int)p.precision);
+}
 int run(const double *t, const double *y, const double *dy, const int64_t *n_per_object,
         int64_t n_objects, const double *freq, int64_t n_freq, ssp_variant variant,
         const ssp_params &p, void *out_power, double *out_best, cudaStream_t s)

@@ -33,6 +33,11 @@ cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s);
 // (ssp_test_fault, SSP_FAULT_STALL)
 bool stall_injected();
 
+// device bytes that run() takes from the stream-ordered pool for this batch
+// (workspace, slabs), or a negative status
+int64_t device_bytes(const int64_t *n_per_object, int64_t n_objects, int64_t n_freq,
+                     ssp_variant variant, const ssp_params &p);
+
 int run(const double *t, const double *y, const double *dy, const int64_t *n_per_object,
         int64_t n_objects, const double *freq, int64_t n_freq, ssp_variant variant,
         const ssp_params &p, void *out_power, double *out_best, cudaStream_t s);

@@ -1,15 +1,29 @@
-// ssp_server.cu -- the serving loop of include/ssp.h (ssp_server_*).
+// ssp_server.cu -- the serving loop of include/ssp.h (ssp_server_*): continuous
+// batching of single light curves under a device-memory budget.
 //
-// Requests (one light curve each) are copied at submission into per-variant
-// FIFO queues.  A launcher thread takes the queued requests of one variant,
-// up to a points x frequencies cap, into one of two batch slots; it copies
-// them into the slot's pinned buffer, then enqueues the H2D copy, the device
-// pipeline of ssp_periodogram_device and the D2H copy of the powers and best
-// periods on the slot's stream.  A completer thread waits for each slot in
-// launch order and hands the results to the requests.  While one slot
-// computes, the next batch is copied in, so the GPU is not left idle between
-// batches.  Results are per (object, frequency) and do not depend on what
-// else shares a batch.
+// Admission.  A submitted request waits in a host queue until its inputs fit
+// the device arena of its variant: one ring buffer per variant in device
+// memory (t, y, dy as three arrays), sized from the server's byte budget.
+// Admitted requests are uploaded into the ring at once (upload stream) and
+// stay resident there until their batch has finished, so a batch reads its
+// inputs in place: consecutive admitted requests of one variant are
+// contiguous in the ring, which is the CSR layout the device pipeline takes.
+//
+// Batching.  A worker forms a batch from the oldest admitted requests of one
+// variant (up to max_batch_ptf points x frequencies, never across the ring's
+// wrap) whenever one of `slots` batch slots is free, and launches the device
+// pipeline of ssp_periodogram_device on the slot's stream after the uploads
+// it reads.  Several slots run at once, so requests that arrive while other
+// batches are on the GPU start as soon as a slot and memory allow, and their
+// kernels overlap.
+//
+// Completion.  A second worker watches every slot's completion event and
+// hands each finished batch's results to its requests in completion order
+// (a short batch that started after a long one may finish first).  A batch
+// still running stall_ms after its launch ends its requests with
+// SSP_ERR_TIMEOUT; its slot and ring space are released only once the GPU
+// has finished with them.  Results are per (object, frequency) and do not
+// depend on what else shares a batch.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -32,9 +46,11 @@ using Clock = std::chrono::steady_clock;
 using ssp_internal::fail;
 
 constexpr double kDefaultBatchPtf = 4.0e9;
-constexpr double kDefaultStallMs = 60000.0;
 constexpr int64_t kDefaultInFlight = (int64_t)1 << 20;
-constexpr int kSlots = 2;
+constexpr double kDefaultStallMs = 60000.0;
+constexpr int kDefaultSlots = 4;
+constexpr int kMaxSlots = 16;
+constexpr double kDefaultArenaBytes = 768.0 * 1024 * 1024;   // all variants together
 constexpr int kVariants = 3;   // SSP_SS, SSP_SP, SSP_SPG
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -42,12 +58,33 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 struct Request {
     int64_t ticket = 0;
     int variant = 0;
-    std::vector<double> t, y, dy;
+    int64_t n = 0;
+    std::vector<double> t, y, dy;   // host copy until uploaded
+    int64_t pos = -1;               // position in its ring (virtual, increasing), once admitted
+    bool launched = false;          // in a batch on the GPU (or finished)
+    bool released = false;          // its batch finished: ring space reusable
     Clock::time_point t_submit, t_done;
-    int status = SSP_PENDING;   // guarded by the server mutex
+    int status = SSP_PENDING;       // guarded by the server mutex
     std::string err;
     std::vector<unsigned char> power;
     double best = 0.0;
+};
+
+// Ring of points in device memory for one variant.  Positions are virtual
+// (they only grow); a request occupies [pos, pos + n), physically
+// pos % cap .. (pos % cap) + n, never across the end of the buffer.
+struct Ring {
+    double *t = nullptr, *y = nullptr, *dy = nullptr;
+    int64_t cap = 0;                 // points
+    int64_t head = 0, tail = 0;      // next free position; start of live data
+    std::deque<std::shared_ptr<Request>> live;   // admitted, in ring order
+    // where a request of n points would go, or -1 if the ring lacks room now
+    int64_t place(int64_t n) const
+    {
+        int64_t p = head;
+        if (p % cap + n > cap) p += cap - p % cap;   // skip the end of the buffer
+        return (p + n - tail <= cap) ? p : -1;
+    }
 };
 
 // pinned host or device buffer that grows by doubling
@@ -89,15 +126,19 @@ void buf_free(Buf &b)
 
 struct Slot {
     cudaStream_t stream = nullptr;
+    cudaEvent_t uploaded = nullptr;   // recorded on the upload stream at launch
     cudaEvent_t done = nullptr;
-    Buf h_in, h_out, d_in, d_out;
+    Buf h_out, d_out;
     std::vector<std::shared_ptr<Request>> reqs;
     std::vector<int64_t> npo;
+    int variant = 0;
     size_t power_bytes = 0;    // offset of the best periods in h_out / d_out
     int status = SSP_OK;
     std::string err;
     bool busy = false;         // guarded by the server mutex
-    Clock::time_point t_launch;   // when the batch's work was enqueued
+    bool enqueued = false;     // launch_batch has returned: `done` marks this batch
+    bool answered = false;     // its requests have their status (a timeout answers early)
+    Clock::time_point t_launch;
 };
 
 }  // namespace
@@ -109,15 +150,17 @@ struct ssp_server {
     int64_t n_freq = 0;
     size_t rs = 4;             // bytes per power value
     double *d_freq = nullptr;
+    int nslots = kDefaultSlots;
+    cudaStream_t upload = nullptr;
 
     std::mutex mu;
-    std::condition_variable cv_launch, cv_complete, cv_done;
-    std::deque<std::shared_ptr<Request>> queue[kVariants];
-    double pending_ptf[kVariants] = {0.0, 0.0, 0.0};
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Request>> waiting[kVariants];   // submitted, not yet admitted
+    Ring ring[kVariants];
     std::unordered_map<int64_t, std::shared_ptr<Request>> live;   // submitted, not collected
     std::deque<int64_t> finished;                                // not yet reported by next
-    std::deque<int> launched;                                    // slots, in launch order
-    Slot slots[kSlots];
+    Slot slots[kMaxSlots];
+    int in_flight = 0;         // busy slots
     int64_t next_ticket = 1;
     bool stop = false;
     bool launcher_done = false;   // no batch will be launched any more
@@ -126,118 +169,170 @@ struct ssp_server {
 
 namespace {
 
-// fills slot sl with its batch and enqueues the work on the slot's stream
-void launch_batch(ssp_server *S, Slot &sl, int variant)
+// Admits waiting requests, oldest first across variants, while their ring has
+// room; uploads each into its ring.  Called by the launcher with the lock
+// held; releases it around the copies.
+void admit(ssp_server *S, std::unique_lock<std::mutex> &lk)
 {
-    sl.t_launch = Clock::now();
-    sl.status = SSP_OK;
-    sl.err.clear();
-    const int64_t nobj = (int64_t)sl.reqs.size();
-    int64_t pts = 0;
-    sl.npo.resize((size_t)nobj);
-    for (int64_t i = 0; i < nobj; ++i) {
-        sl.npo[(size_t)i] = (int64_t)sl.reqs[(size_t)i]->t.size();
-        pts += sl.npo[(size_t)i];
-    }
-    const size_t in_col = align256(8 * (size_t)pts);
-    sl.power_bytes = align256(S->rs * (size_t)nobj * (size_t)S->n_freq);
-    const size_t out_bytes = sl.power_bytes + 8 * (size_t)nobj;
-    int rc = buf_reserve(sl.h_in, 3 * in_col);
-    if (!rc) rc = buf_reserve(sl.d_in, 3 * in_col);
-    if (!rc) rc = buf_reserve(sl.h_out, out_bytes);
-    if (!rc) rc = buf_reserve(sl.d_out, out_bytes);
-    if (rc) {
-        sl.status = rc;
-        sl.err = ssp_internal::last_error();
-        cudaEventRecord(sl.done, sl.stream);
-        return;
-    }
-    double *ht = (double *)sl.h_in.p, *hy = (double *)(sl.h_in.p + in_col),
-           *hdy = (double *)(sl.h_in.p + 2 * in_col);
-    size_t at = 0;
-    for (const auto &r : sl.reqs) {
-        const size_t n = r->t.size();
-        std::memcpy(ht + at, r->t.data(), 8 * n);
-        std::memcpy(hy + at, r->y.data(), 8 * n);
-        std::memcpy(hdy + at, r->dy.data(), 8 * n);
-        at += n;
-    }
-    cudaError_t e = cudaMemcpyAsync(sl.d_in.p, sl.h_in.p, 3 * in_col, cudaMemcpyHostToDevice,
-                                    sl.stream);
-    if (e == cudaSuccess) {
-        const double *dt = (const double *)sl.d_in.p;
-        const double *dyv = (const double *)(sl.d_in.p + in_col);
-        const double *ddy = (const double *)(sl.d_in.p + 2 * in_col);
-        rc = ssp_internal::run(dt, dyv, ddy, sl.npo.data(), nobj, S->d_freq, S->n_freq,
-                               (ssp_variant)variant, S->P, sl.d_out.p,
-                               (double *)(sl.d_out.p + sl.power_bytes), sl.stream);
-        if (rc) {
-            sl.status = rc;
-            sl.err = ssp_internal::last_error();
-        } else {
-            e = cudaMemcpyAsync(sl.h_out.p, sl.d_out.p, out_bytes, cudaMemcpyDeviceToHost,
-                                sl.stream);
+    for (;;) {
+        int v = -1;
+        for (int k = 0; k < kVariants; ++k)
+            if (!S->waiting[k].empty() &&
+                (v < 0 || S->waiting[k].front()->t_submit < S->waiting[v].front()->t_submit))
+                v = k;
+        if (v < 0) return;
+        Ring &rg = S->ring[v];
+        const auto r = S->waiting[v].front();
+        const int64_t p = rg.place(r->n);
+        if (p < 0) return;   // the oldest waits for room: admission stays in order
+        S->waiting[v].pop_front();
+        r->pos = p;
+        rg.head = p + r->n;
+        rg.live.push_back(r);
+        lk.unlock();
+        const size_t at = (size_t)(p % rg.cap), bytes = 8 * (size_t)r->n;
+        cudaError_t e = cudaMemcpyAsync(rg.t + at, r->t.data(), bytes, cudaMemcpyHostToDevice, S->upload);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(rg.y + at, r->y.data(), bytes, cudaMemcpyHostToDevice, S->upload);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(rg.dy + at, r->dy.data(), bytes, cudaMemcpyHostToDevice, S->upload);
+        // (copies from pageable memory are staged before the calls return)
+        std::vector<double>().swap(r->t);
+        std::vector<double>().swap(r->y);
+        std::vector<double>().swap(r->dy);
+        lk.lock();
+        if (e != cudaSuccess) {
+            // answered at once and never batched; its ring space is reused
+            // once the requests before it are done
+            cudaGetLastError();
+            r->status = SSP_ERR_CUDA;
+            r->err = std::string("upload: ") + cudaGetErrorString(e);
+            r->launched = r->released = true;
+            r->t_done = Clock::now();
+            if (S->live.count(r->ticket)) S->finished.push_back(r->ticket);
+            S->cv_done.notify_all();
         }
     }
-    if (e != cudaSuccess && sl.status == SSP_OK) {
-        sl.status = SSP_ERR_CUDA;
-        sl.err = std::string("batch copy: ") + cudaGetErrorString(e);
-    }
-    cudaEventRecord(sl.done, sl.stream);
+}
+
+// oldest admitted, not yet launched request of variant v, as an index into
+// its ring's live list, or -1
+int64_t first_unlaunched(const Ring &rg)
+{
+    for (size_t i = 0; i < rg.live.size(); ++i)
+        if (!rg.live[i]->launched) return (int64_t)i;
+    return -1;
 }
 
 int free_slot(const ssp_server *S)
 {
-    for (int k = 0; k < kSlots; ++k)
+    for (int k = 0; k < S->nslots; ++k)
         if (!S->slots[k].busy) return k;
     return -1;
+}
+
+// Enqueues slot sl's batch (its requests lie contiguously in the ring of its
+// variant) on the slot's stream, after the uploads it reads.
+void launch_batch(ssp_server *S, Slot &sl)
+{
+    sl.t_launch = Clock::now();
+    sl.status = SSP_OK;
+    sl.err.clear();
+    Ring &rg = S->ring[sl.variant];
+    const int64_t nobj = (int64_t)sl.reqs.size();
+    sl.npo.resize((size_t)nobj);
+    for (int64_t i = 0; i < nobj; ++i) sl.npo[(size_t)i] = sl.reqs[(size_t)i]->n;
+    sl.power_bytes = align256(S->rs * (size_t)nobj * (size_t)S->n_freq);
+    const size_t out_bytes = sl.power_bytes + 8 * (size_t)nobj;
+    int rc = buf_reserve(sl.h_out, out_bytes);
+    if (!rc) rc = buf_reserve(sl.d_out, out_bytes);
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+        e = cudaEventRecord(sl.uploaded, S->upload);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sl.stream, sl.uploaded, 0);
+    }
+    if (!rc && e == cudaSuccess) {
+        const size_t at = (size_t)(sl.reqs.front()->pos % rg.cap);
+        rc = ssp_internal::run(rg.t + at, rg.y + at, rg.dy + at, sl.npo.data(), nobj, S->d_freq,
+                               S->n_freq, (ssp_variant)sl.variant, S->P, sl.d_out.p,
+                               (double *)(sl.d_out.p + sl.power_bytes), sl.stream);
+        if (!rc)
+            e = cudaMemcpyAsync(sl.h_out.p, sl.d_out.p, out_bytes, cudaMemcpyDeviceToHost, sl.stream);
+    }
+    if (rc) {
+        sl.status = rc;
+        sl.err = ssp_internal::last_error();
+    } else if (e != cudaSuccess) {
+        cudaGetLastError();
+        sl.status = SSP_ERR_CUDA;
+        sl.err = std::string("batch: ") + cudaGetErrorString(e);
+    }
+    cudaEventRecord(sl.done, sl.stream);
 }
 
 void launcher_loop(ssp_server *S, std::unique_lock<std::mutex> &lk)
 {
     for (;;) {
         int slot = -1, v = -1;
+        int64_t first = -1;
         for (;;) {
             if (S->stop) return;
+            admit(S, lk);
+            if (S->stop) return;
             slot = free_slot(S);
-            // the variant whose oldest request has waited longest
+            // the variant whose oldest admitted request has waited longest
             v = -1;
-            for (int k = 0; k < kVariants; ++k)
-                if (!S->queue[k].empty() &&
-                    (v < 0 || S->queue[k].front()->t_submit < S->queue[v].front()->t_submit))
+            first = -1;
+            for (int k = 0; k < kVariants; ++k) {
+                const int64_t f = first_unlaunched(S->ring[k]);
+                if (f >= 0 && (v < 0 || S->ring[k].live[(size_t)f]->t_submit <
+                                            S->ring[v].live[(size_t)first]->t_submit)) {
                     v = k;
+                    first = f;
+                }
+            }
             if (slot >= 0 && v >= 0) {
-                const auto deadline = S->queue[v].front()->t_submit +
-                                      std::chrono::duration_cast<Clock::duration>(
-                                          std::chrono::duration<double, std::milli>(
-                                              S->cfg.max_wait_ms));
-                if (S->cfg.max_wait_ms > 0.0 && S->pending_ptf[v] < S->cfg.max_batch_ptf &&
-                    Clock::now() < deadline) {
-                    S->cv_launch.wait_until(lk, deadline);
+                const auto r0 = S->ring[v].live[(size_t)first];
+                const auto deadline = r0->t_submit + std::chrono::duration_cast<Clock::duration>(
+                                                         std::chrono::duration<double, std::milli>(
+                                                             S->cfg.max_wait_ms));
+                double ptf = 0.0;
+                for (size_t i = (size_t)first; i < S->ring[v].live.size(); ++i)
+                    ptf += (double)S->ring[v].live[i]->n * (double)S->n_freq;
+                if (S->cfg.max_wait_ms > 0.0 && ptf < S->cfg.max_batch_ptf && Clock::now() < deadline) {
+                    S->cv_work.wait_until(lk, deadline);
                     continue;
                 }
                 break;
             }
-            S->cv_launch.wait(lk);
+            S->cv_work.wait(lk);
         }
         Slot &sl = S->slots[slot];
+        Ring &rg = S->ring[v];
         sl.reqs.clear();
+        sl.variant = v;
         double ptf = 0.0;
-        auto &q = S->queue[v];
-        while (!q.empty()) {
-            const double add = (double)q.front()->t.size() * (double)S->n_freq;
+        int64_t end = -1;
+        for (size_t i = (size_t)first; i < rg.live.size(); ++i) {
+            const auto &r = rg.live[i];
+            // contiguous in the ring, and within the cap (at least one request)
+            if (end >= 0 && r->pos != end) break;
+            const double add = (double)r->n * (double)S->n_freq;
             if (!sl.reqs.empty() && ptf + add > S->cfg.max_batch_ptf) break;
             ptf += add;
-            sl.reqs.push_back(q.front());
-            q.pop_front();
+            end = r->pos + r->n;
+            r->launched = true;
+            sl.reqs.push_back(r);
         }
-        S->pending_ptf[v] = q.empty() ? 0.0 : S->pending_ptf[v] - ptf;
         sl.busy = true;
+        sl.enqueued = false;
+        sl.answered = false;
+        ++S->in_flight;
         lk.unlock();
-        launch_batch(S, sl, v);
+        launch_batch(S, sl);
         lk.lock();
-        S->launched.push_back(slot);
-        S->cv_complete.notify_one();
+        sl.enqueued = true;
+        S->cv_done.notify_all();   // wakes the completer
     }
 }
 
@@ -247,7 +342,46 @@ void launcher_main(ssp_server *S)
     std::unique_lock<std::mutex> lk(S->mu);
     launcher_loop(S, lk);
     S->launcher_done = true;
-    S->cv_complete.notify_all();
+    S->cv_done.notify_all();
+}
+
+// Hands slot sl's outcome to its requests (status, and results when OK).
+// Lock held.
+void answer(ssp_server *S, Slot &sl, int status, const std::string &err)
+{
+    const auto now = Clock::now();
+    const size_t row = S->rs * (size_t)S->n_freq;
+    const double *best = (const double *)(sl.h_out.p + sl.power_bytes);
+    for (size_t i = 0; i < sl.reqs.size(); ++i) {
+        Request &r = *sl.reqs[i];
+        if (status == SSP_OK) {
+            r.power.assign(sl.h_out.p + i * row, sl.h_out.p + (i + 1) * row);
+            r.best = best[i];
+        }
+        r.status = status;
+        r.err = err;
+        r.t_done = now;
+        if (S->live.count(r.ticket)) S->finished.push_back(r.ticket);
+    }
+    sl.answered = true;
+    S->cv_done.notify_all();
+}
+
+// The GPU has finished with slot sl: its ring space and the slot are free.
+// Lock held.
+void release_slot(ssp_server *S, Slot &sl)
+{
+    for (const auto &r : sl.reqs) r->released = true;
+    Ring &rg = S->ring[sl.variant];
+    while (!rg.live.empty() && rg.live.front()->released) {
+        rg.live.pop_front();
+        rg.tail = rg.live.empty() ? rg.head : rg.live.front()->pos;
+    }
+    sl.reqs.clear();
+    sl.busy = false;
+    sl.enqueued = false;
+    --S->in_flight;
+    S->cv_work.notify_all();   // a slot and ring space for the launcher
 }
 
 void completer_main(ssp_server *S)
@@ -255,86 +389,65 @@ void completer_main(ssp_server *S)
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
-        while (S->launched.empty() && !S->launcher_done) S->cv_complete.wait(lk);
-        if (S->launched.empty()) return;   // the launcher has stopped and all is drained
-        const int k = S->launched.front();
-        S->launched.pop_front();
-        Slot &sl = S->slots[k];
-        lk.unlock();
-        // Bounded wait for the batch: past stall_ms its requests end with
-        // SSP_ERR_TIMEOUT at once, and the slot stays reserved until the GPU
-        // has finished with its buffers.  (An injected stall takes the same
-        // path after the batch completes normally.)
-        const auto deadline = sl.t_launch + std::chrono::duration_cast<Clock::duration>(
-                                                std::chrono::duration<double, std::milli>(
-                                                    S->cfg.stall_ms));
-        cudaError_t e = cudaEventQuery(sl.done);
-        bool timed_out = false;
-        while (e == cudaErrorNotReady) {
-            if (Clock::now() >= deadline) {
-                timed_out = true;
-                break;
-            }
-            std::this_thread::sleep_for(std::chrono::microseconds(50));
-            e = cudaEventQuery(sl.done);
-        }
-        if (ssp_internal::stall_injected()) timed_out = true;
-        int status = sl.status;
-        std::string err = sl.err;
-        if (timed_out) {
-            status = SSP_ERR_TIMEOUT;
-            err = "batch did not finish within the server's stall limit";
-        } else if (status == SSP_OK && e != cudaSuccess) {
-            status = SSP_ERR_CUDA;
-            err = std::string("batch: ") + cudaGetErrorString(e);
-        }
-        const auto now = Clock::now();
-        const size_t row = S->rs * (size_t)S->n_freq;
-        if (status == SSP_OK) {
-            const double *best = (const double *)(sl.h_out.p + sl.power_bytes);
-            for (size_t i = 0; i < sl.reqs.size(); ++i) {
-                Request &r = *sl.reqs[i];
-                r.power.assign(sl.h_out.p + i * row, sl.h_out.p + (i + 1) * row);
-                r.best = best[i];
-            }
-        }
-        lk.lock();
-        for (const auto &r : sl.reqs) {
-            r->status = status;
-            r->err = err;
-            r->t_done = now;
-            r->t.clear();
-            r->t.shrink_to_fit();
-            r->y.clear();
-            r->y.shrink_to_fit();
-            r->dy.clear();
-            r->dy.shrink_to_fit();
-            if (S->live.count(r->ticket)) S->finished.push_back(r->ticket);
-        }
-        sl.reqs.clear();
-        S->cv_done.notify_all();
-        if (timed_out) {
-            // the requests have their answer; the buffers are freed for the
-            // next batch only once the GPU is done with them
+        while (S->in_flight == 0 && !S->launcher_done) S->cv_done.wait(lk);
+        if (S->in_flight == 0) return;   // the launcher has stopped and all is drained
+        bool progress = false;
+        for (int k = 0; k < S->nslots; ++k) {
+            Slot &sl = S->slots[k];
+            if (!sl.busy || !sl.enqueued) continue;   // (a batch still being enqueued)
             lk.unlock();
-            cudaEventSynchronize(sl.done);
+            const cudaError_t e = cudaEventQuery(sl.done);
+            lk.lock();
+            if (e == cudaErrorNotReady) {
+                // bounded wait: past stall_ms the requests are answered now,
+                // the slot is freed when the GPU is done with it
+                if (!sl.answered &&
+                    Clock::now() >= sl.t_launch + std::chrono::duration_cast<Clock::duration>(
+                                                      std::chrono::duration<double, std::milli>(
+                                                          S->cfg.stall_ms))) {
+                    answer(S, sl, SSP_ERR_TIMEOUT,
+                           "batch did not finish within the server's stall limit");
+                    progress = true;
+                }
+                continue;
+            }
+            if (!sl.answered) {
+                int status = sl.status;
+                std::string err = sl.err;
+                if (ssp_internal::stall_injected()) {
+                    status = SSP_ERR_TIMEOUT;
+                    err = "batch did not finish within the server's stall limit";
+                } else if (status == SSP_OK && e != cudaSuccess) {
+                    cudaGetLastError();
+                    status = SSP_ERR_CUDA;
+                    err = std::string("batch: ") + cudaGetErrorString(e);
+                }
+                answer(S, sl, status, err);
+            }
+            release_slot(S, sl);
+            progress = true;
+        }
+        if (!progress) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
             lk.lock();
         }
-        sl.busy = false;
-        S->cv_launch.notify_one();
     }
 }
 
 void release(ssp_server *S)
 {
-    for (Slot &sl : S->slots) {
-        buf_free(sl.h_in);
+    for (int k = 0; k < kMaxSlots; ++k) {
+        Slot &sl = S->slots[k];
         buf_free(sl.h_out);
-        buf_free(sl.d_in);
         buf_free(sl.d_out);
         if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.uploaded) cudaEventDestroy(sl.uploaded);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
+    for (Ring &rg : S->ring)
+        if (rg.t) cudaFree(rg.t);
+    if (S->upload) cudaStreamDestroy(S->upload);
     if (S->d_freq) cudaFree(S->d_freq);
     delete S;
 }
@@ -356,6 +469,8 @@ int ssp_server_create(const double *freq_grid, int64_t n_freq, const ssp_params 
     if (rc) return rc;
     rc = ssp_internal::check_freq(freq_grid, n_freq);
     if (rc) return rc;
+    if (config && config->slots > kMaxSlots)
+        return fail(SSP_ERR_ARG, "at most 16 batch slots");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
@@ -369,27 +484,46 @@ int ssp_server_create(const double *freq_grid, int64_t n_freq, const ssp_params 
     S->cfg.max_wait_ms = 0.0;
     S->cfg.max_in_flight = kDefaultInFlight;
     S->cfg.stall_ms = kDefaultStallMs;
+    S->cfg.slots = kDefaultSlots;
+    S->cfg.device_bytes = kDefaultArenaBytes;
     if (config) {
-        if (config->stall_ms > 0.0) S->cfg.stall_ms = config->stall_ms;
         if (config->max_batch_ptf > 0.0) S->cfg.max_batch_ptf = config->max_batch_ptf;
         if (config->max_wait_ms > 0.0) S->cfg.max_wait_ms = config->max_wait_ms;
         if (config->max_in_flight > 0) S->cfg.max_in_flight = config->max_in_flight;
+        if (config->stall_ms > 0.0) S->cfg.stall_ms = config->stall_ms;
+        if (config->slots > 0) S->cfg.slots = config->slots;
+        if (config->device_bytes > 0.0) S->cfg.device_bytes = config->device_bytes;
     }
+    S->nslots = (int)S->cfg.slots;
     S->n_freq = n_freq;
     S->rs = P.precision == SSP_FP64 ? 8 : 4;
     e = cudaMalloc((void **)&S->d_freq, 8 * (size_t)n_freq);
     if (e == cudaSuccess)
         e = cudaMemcpy(S->d_freq, freq_grid, 8 * (size_t)n_freq, cudaMemcpyHostToDevice);
-    for (int k = 0; k < kSlots && e == cudaSuccess; ++k) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->upload, cudaStreamNonBlocking);
+    // the arena: one ring per variant, t, y and dy of 8 bytes a point each
+    const int64_t cap = std::max<int64_t>(4, (int64_t)(S->cfg.device_bytes / (kVariants * 24.0)));
+    for (int v = 0; v < kVariants && e == cudaSuccess; ++v) {
+        Ring &rg = S->ring[v];
+        rg.cap = cap;
+        e = cudaMalloc((void **)&rg.t, 24 * (size_t)cap);
+        if (e == cudaSuccess) {
+            rg.y = rg.t + cap;
+            rg.dy = rg.t + 2 * cap;
+        }
+    }
+    for (int k = 0; k < S->nslots && e == cudaSuccess; ++k) {
         Slot &sl = S->slots[k];
-        sl.h_in.host = sl.h_out.host = true;
+        sl.h_out.host = true;
         e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.uploaded, cudaEventDisableTiming);
     }
     if (e != cudaSuccess) {
+        const int code = e == cudaErrorMemoryAllocation ? SSP_ERR_NOMEM : SSP_ERR_CUDA;
         cudaGetLastError();
         release(S);
-        return fail(SSP_ERR_CUDA, cudaGetErrorString(e));
+        return fail(code, cudaGetErrorString(e));
     }
     S->launcher = std::thread(launcher_main, S);
     S->completer = std::thread(completer_main, S);
@@ -406,8 +540,11 @@ int ssp_server_submit(ssp_server *s, const double *t, const double *y, const dou
         return fail(SSP_ERR_ARG, "unknown variant");
     int rc = ssp_internal::check_one_object(s->P, t, y, dy, n);
     if (rc) return rc;
+    if (n > s->ring[variant].cap)
+        return fail(SSP_ERR_NOMEM, "object larger than the server's device arena for its variant");
     auto r = std::make_shared<Request>();
     r->variant = (int)variant;
+    r->n = n;
     r->t.assign(t, t + n);
     r->y.assign(y, y + n);
     r->dy.assign(dy, dy + n);
@@ -417,10 +554,9 @@ int ssp_server_submit(ssp_server *s, const double *t, const double *y, const dou
     r->ticket = s->next_ticket++;
     r->t_submit = Clock::now();
     s->live[r->ticket] = r;
-    s->queue[r->variant].push_back(r);
-    s->pending_ptf[r->variant] += (double)n * (double)s->n_freq;
+    s->waiting[r->variant].push_back(r);
     *out_ticket = r->ticket;
-    s->cv_launch.notify_one();
+    s->cv_work.notify_all();
     return SSP_OK;
 }
 
@@ -473,11 +609,11 @@ int ssp_server_destroy(ssp_server *s)
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
-        for (auto &q : s->queue) q.clear();
-        s->cv_launch.notify_all();
-        s->cv_complete.notify_all();
+        for (auto &q : s->waiting) q.clear();
+        s->cv_work.notify_all();
         s->cv_done.notify_all();
     }
+    // the launcher stops; the completer drains the batches already on the GPU
     if (s->launcher.joinable()) s->launcher.join();
     if (s->completer.joinable()) s->completer.join();
     release(s);

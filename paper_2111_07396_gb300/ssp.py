@@ -38,7 +38,8 @@ class ssp_phase_time(ctypes.Structure):
 
 class ssp_server_config(ctypes.Structure):
     _fields_ = [("max_batch_ptf", ctypes.c_double), ("max_wait_ms", ctypes.c_double),
-                ("max_in_flight", ctypes.c_int64), ("stall_ms", ctypes.c_double)]
+                ("max_in_flight", ctypes.c_int64), ("stall_ms", ctypes.c_double),
+                ("slots", ctypes.c_int64), ("device_bytes", ctypes.c_double)]
 
 
 PHASES = ("prep", "pgram_ss", "pgram_sp", "redo", "argmax")
@@ -297,13 +298,14 @@ class Server:
     library's."""
 
     def __init__(self, freq_grid, precision="fp32c", alpha=9.0, spans=None, params=None,
-                 max_batch_ptf=0.0, max_wait_ms=0.0, max_in_flight=0, stall_ms=0.0):
+                 max_batch_ptf=0.0, max_wait_ms=0.0, max_in_flight=0, stall_ms=0.0, slots=0,
+                 device_bytes=0.0):
         self._p = params if params is not None else ssp_default_params(precision, alpha, spans)
         self.freq = _f64(freq_grid)
         self.n_freq = int(self.freq.size)
         self.dtype = np.float64 if self._p.precision == SSP_FP64 else np.float32
         cfg = ssp_server_config(float(max_batch_ptf), float(max_wait_ms), int(max_in_flight),
-                                float(stall_ms))
+                                float(stall_ms), int(slots), float(device_bytes))
         h = ctypes.c_void_p()
         _check(lib().ssp_server_create(_ptr(self.freq), self.n_freq, ctypes.byref(self._p),
                                        ctypes.byref(cfg), ctypes.byref(h)))

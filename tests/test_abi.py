@@ -107,7 +107,7 @@ def test_server_rejects_bad_grid_and_params_before_cuda():
     assert ei.value.status == ssp.SSP_ERR_ARG
     assert ssp.ssp_status_string(ssp.SSP_ERR_BUSY) == "too many requests in flight"
     assert ssp.ssp_status_string(ssp.SSP_PENDING) == "pending"
-    assert ctypes.sizeof(ssp.ssp_server_config) == 32
+    assert ctypes.sizeof(ssp.ssp_server_config) == 48
     # calls on a NULL handle are argument errors, not crashes
     t = ctypes.c_int64()
     assert ssp.lib().ssp_server_next(None, 0, ctypes.byref(t)) == ssp.SSP_ERR_ARG

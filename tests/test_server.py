@@ -102,3 +102,51 @@ def test_destroy_with_requests_outstanding():
         srv.submit(t, y, dy)
     srv.close()                            # drops the queue, waits for the GPU
     srv.close()                            # idempotent in the binding
+
+
+def test_request_arriving_during_a_batch_finishes_first():
+    # Continuous batching: a short request submitted while a long batch is on
+    # the GPU runs in another slot at once and finishes (and is reported)
+    # first.  The long batch is one 65,535-point object in binary64 on a
+    # 16-frequency grid: 16 CTAs for tens of milliseconds, which leaves SMs
+    # free for the short one.
+    import time
+    g = np.random.default_rng(8)
+    freq = synth.uniform_grid(0.05, 3.0, 16)
+    tl = np.sort(g.uniform(0, 1000, 65535))
+    long_obj = (tl, np.sin(tl) + g.normal(0, 0.1, tl.size), np.full(tl.size, 0.1))
+    ts = np.sort(g.uniform(0, 100, 40))
+    short_obj = (ts, np.cos(ts) + g.normal(0, 0.1, ts.size), np.full(ts.size, 0.1))
+    with ssp.Server(freq, precision="fp64") as srv:
+        a = srv.submit(*long_obj, "ss")
+        time.sleep(0.005)                  # a's batch is on the GPU
+        b = srv.submit(*short_obj, "sp")
+        first = srv.next(wait_ms=60000)
+        second = srv.next(wait_ms=60000)
+        assert (first, second) == (b, a)
+        pb, bb, _ = srv.poll(b)
+        pa, ba, _ = srv.poll(a)
+    ref_b, rb = ssp.ssp_periodogram(*short_obj, [ts.size], freq, variant="sp", precision="fp64")
+    ref_a, ra = ssp.ssp_periodogram(*long_obj, [tl.size], freq, variant="ss", precision="fp64")
+    np.testing.assert_array_equal(pb, ref_b[0])
+    np.testing.assert_array_equal(pa, ref_a[0])
+    assert (bb, ba) == (rb[0], ra[0])
+
+
+def test_admission_waits_for_arena_room():
+    # An arena of about 4,000 points per variant: requests beyond it wait on
+    # the host until earlier ones finish, then run with the same results; an
+    # object larger than the arena is refused at submission.
+    freq, objs = _objects(24)
+    with ssp.Server(freq, device_bytes=3 * 24 * 4000, slots=2) as srv:
+        assert all(t.size <= 4000 for t, _, _ in objs)
+        tks = [srv.submit(t, y, dy, "ss") for t, y, dy in objs]
+        for tk, (t, y, dy) in zip(tks, objs):
+            power, _, _ = srv.poll(tk, wait_ms=60000)
+            ref, _ = ssp.ssp_periodogram(t, y, dy, [t.size], freq, variant="ss")
+            np.testing.assert_array_equal(power, ref[0])
+    with ssp.Server(freq, device_bytes=3 * 24 * 1000) as srv:
+        k = np.arange(2000.0)
+        with pytest.raises(ssp.SSPError) as ei:
+            srv.submit(k * 0.37, np.sin(k), np.ones(k.size))
+        assert ei.value.status == ssp.SSP_ERR_NOMEM
