@@ -675,6 +675,39 @@ def run_extras(args):
                        "api": "ssp_periodogram (host arrays)", "precision": "fp32c"}}),
             flush=True)
 
+    # launch plans: the single-object C1 workload (100 points, 2,000
+    # frequencies), called again and again on device arrays; the device entry
+    # point plans, allocates and launches each call, the plan replays a graph
+    import torch
+    c1 = synth.config1()
+    put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    dt_, dy_, dd_, df_ = put(c1.t), put(c1.y), put(c1.dy), put(c1.freq)
+    for v in ("ss", "sp"):
+        pw = torch.empty((1, c1.freq.size), dtype=torch.float32, device="cuda")
+        bp = torch.empty(1, dtype=torch.float64, device="cuda")
+        reps = 200
+        res = {}
+        with ssp.Plan(c1.n_per_object, c1.freq.size, variant=v) as plan:
+            calls = {"device_entry": lambda: ssp.ssp_periodogram_device(
+                         dt_, dy_, dd_, c1.n_per_object, df_, pw, bp, variant=v),
+                     "plan": lambda: plan.execute(dt_, dy_, dd_, df_, pw, bp)}
+            for name, fn in calls.items():
+                for _ in range(5):
+                    fn()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    fn()
+                torch.cuda.synchronize()
+                res[name] = (time.perf_counter() - t0) / reps * 1e6
+        print(json.dumps({
+            "metric": "microseconds per call", "unit": "us", "extra": "launch_plan", "variant": v,
+            "device_entry_us": res["device_entry"], "plan_us": res["plan"],
+            "speedup": res["device_entry"] / res["plan"],
+            "config": {"workload": "one 100-point object, 2,000 freqs in [0.1, 10), FP32C, "
+                                   f"{reps} back-to-back calls on one stream",
+                       "api": "ssp_periodogram_device vs ssp_plan_execute"}}), flush=True)
+
     cat = synth.config3(n_objects=2000, n_freq=20_000)
     step = float(cat.freq[1] - cat.freq[0])
     with ClockSampler(0) as clk:

@@ -189,6 +189,36 @@ int ssp_periodogram_device_noalloc(const double *t, const double *y, const doubl
                                    double *out_best_period, void *stream);
 
 /*
+ * Launch plans: the device pipeline captured into a CUDA graph (spec:
+ * a graph-captured launch sequence for the batched path; the paper has no
+ * counterpart).  For callers that run one shape again and again -- the same
+ * objects' point counts, frequency count, variant and params, new values --
+ * ssp_plan_create does the host work of ssp_periodogram_device once: it
+ * builds the launch plan, takes the workspace (cudaMalloc, held until
+ * ssp_plan_destroy), uploads the plan's tables and captures the pipeline
+ * (counters cleared, prep, the periodogram kernels and their FP64
+ * recompute, argmax) into a CUDA graph on the current device.
+ * ssp_plan_execute then runs that graph on the caller's DEVICE arrays
+ * (t, y, dy, freq_grid, out_power, out_best_period as in
+ * ssp_periodogram_device, n_freq values in freq_grid) enqueued on `stream`
+ * with one graph launch; its results are bit for bit those of
+ * ssp_periodogram_device with the same plan.  Executions of one plan share
+ * its workspace, so they must not overlap on the GPU (one stream, or the
+ * caller's ordering).  The plan follows the threads-per-CTA choices in force
+ * when it was created (ssp_autotune).
+ * Errors: ssp_plan_create as ssp_periodogram_device (shape and params),
+ * SSP_ERR_NOMEM (workspace), SSP_ERR_CUDA (capture); ssp_plan_execute
+ * SSP_ERR_ARG (NULL arrays), SSP_ERR_CUDA.
+ */
+typedef struct ssp_plan ssp_plan;
+int ssp_plan_create(const int64_t *n_per_object, int64_t n_objects, int64_t n_freq,
+                    ssp_variant variant, const ssp_params *params, ssp_plan **out);
+int ssp_plan_execute(ssp_plan *plan, const double *t, const double *y, const double *dy,
+                     const double *freq_grid, void *out_power, double *out_best_period,
+                     void *stream);
+int ssp_plan_destroy(ssp_plan *plan);
+
+/*
  * Serving: one light curve per request, results collected asynchronously.
  * (The paper's batches are whole catalogs, Sec. 4.3; a survey alert stream
  * instead delivers objects one at a time.)  A server owns one frequency grid,

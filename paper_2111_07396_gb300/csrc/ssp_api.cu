@@ -301,7 +301,9 @@ int configure(int precision, int variant, bool per, bool shared, int G, int n_ma
     const bool long_kernel = variant == VAR_SS && precision == SSP_FP32C && n_max > kLongN &&
                              (per || shared);
     c.smo_out = smo_ok && long_kernel;
-    c.smo_stride = c.smo_out ? align16(smo_bytes(n_max, G, 4)) : 0;
+    c.smo_stride = c.smo_out ? align16(smo_bytes(n_max, G, 4)) +
+                                   (shared ? kept_perm_bytes(n_max) : 0)
+                             : 0;
     // the same kernels recompute their flagged frequencies in binary64 at once,
     // in per-CTA binary64 frames in global memory
     c.redo_inline = c.smo_out;
@@ -570,8 +572,195 @@ Grouping group_by_times(const double *t, const int64_t *npo, int64_t o0, int64_t
     return g;
 }
 
-// fbase (device, or null): object o's grid is freq[fbase[o] .. + n_freq);
-// out_best_power (device, or null) receives each object's largest power
+// Device pointers of one batch's workspace (run_device carves them from one
+// allocation in this order; workspace_bytes sizes it).
+struct Workspace {
+    int64_t *off = nullptr;
+    double *tt = nullptr;
+    int *bad = nullptr;
+    void *yc = nullptr, *wv = nullptr;
+    double *yc64 = nullptr, *wv64 = nullptr;
+    float2 *ydf = nullptr, *wdf = nullptr;
+    double *chi0 = nullptr, *ymax = nullptr;
+    int4 *items = nullptr;
+    int *counters = nullptr;
+    size_t n_counters = 0;
+    unsigned char *near = nullptr, *slab = nullptr;
+};
+
+Workspace carve_workspace(unsigned char *base, const Plan &plan, int64_t n_obj, int64_t N,
+                          int64_t n_freq, int prec)
+{
+    Workspace w;
+    size_t cur = 0;
+    auto take = [&](size_t bytes) {
+        unsigned char *p = base + cur;
+        cur += align16(bytes);
+        return p;
+    };
+    w.off = (int64_t *)take(8 * (size_t)(n_obj + 1));
+    w.tt = (double *)take(8 * (size_t)N);
+    w.bad = (int *)take(4 * (size_t)n_obj);
+    w.yc = take(rsize(prec) * (size_t)N);
+    w.wv = take(rsize(prec) * (size_t)N);
+    w.yc64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
+    w.wv64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
+    w.ydf = plan.redo ? (float2 *)take(8 * (size_t)N) : nullptr;
+    w.wdf = plan.redo ? (float2 *)take(8 * (size_t)N) : nullptr;
+    w.chi0 = (double *)take(8 * (size_t)n_obj);
+    w.ymax = (double *)take(8 * (size_t)n_obj);
+    w.items = (int4 *)take(sizeof(int4) * plan.items_total);
+    w.n_counters = 2 * plan.buckets.size() + 2;
+    w.counters = (int *)take(4 * w.n_counters);
+    w.near = plan.redo ? (unsigned char *)take((size_t)n_obj * (size_t)n_freq) : nullptr;
+    w.slab = base + cur;
+    return w;
+}
+
+// CSR offsets and the work items of a plan, as the kernels read them
+void plan_tables(const Plan &plan, const int64_t *npo, int64_t n_obj, std::vector<int64_t> &off,
+                 std::vector<int4> &items)
+{
+    off.assign((size_t)n_obj + 1, 0);
+    for (int64_t o = 0; o < n_obj; ++o) off[o + 1] = off[o] + npo[o];
+    items.clear();
+    items.reserve(plan.items_total);
+    for (const Bucket &b : plan.buckets) items.insert(items.end(), b.items.begin(), b.items.end());
+}
+
+// what enqueue_pipeline tells its caller after each kernel it enqueues
+enum LaunchKind { LK_PREP = 0, LK_PGRAM = 1, LK_ARGMAX = 2 };
+struct LaunchHook {
+    virtual void launched(LaunchKind k, const void *args) = 0;
+};
+
+// The device pipeline of one batch after its tables are on the device: the
+// counters and flags cleared, prep, each length bucket's periodogram (and its
+// FP64 recompute), argmax.  fbase (device, or null): object o's grid is
+// freq[fbase[o] .. + n_freq); out_best_power (device, or null) receives each
+// object's largest power.  prof: record the per-phase timers.
+cudaError_t enqueue_pipeline(const Plan &plan, const Workspace &w, const double *t, const double *y,
+                             const double *dy, int64_t n_obj, const double *freq, int64_t n_freq,
+                             ssp_variant variant, const ssp_params &P, void *out_power,
+                             double *out_best, cudaStream_t s, const int64_t *fbase,
+                             double *out_best_power, bool prof, LaunchHook *hook)
+{
+    const int prec = (int)P.precision;
+    const int kv = kernel_variant(variant, P);
+    const bool per = P.periodic != 0;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w.counters, 0, 4 * w.n_counters, s))) return e;
+    if (w.near && (e = cudaMemsetAsync(w.near, 0, (size_t)n_obj * (size_t)n_freq, s))) return e;
+    PrepArgs pa{};
+    pa.t = t;
+    pa.y = y;
+    pa.dy = dy;
+    pa.off = w.off;
+    pa.tt = w.tt;
+    pa.yc = w.yc;
+    pa.wv = w.wv;
+    pa.yc64 = w.yc64;
+    pa.wv64 = w.wv64;
+    pa.ydf = w.ydf;
+    pa.wdf = w.wdf;
+    pa.chi0 = w.chi0;
+    pa.ymax = w.ymax;
+    pa.bad = w.bad;
+    Mark mk;
+    bool on = prof && prof_begin(SSP_PHASE_PREP, s, mk);
+    if ((e = prep_launch(prec, pa, (int)n_obj, s))) return e;
+    if (hook) hook->launched(LK_PREP, &pa);
+    prof_end(on, mk, s);
+    size_t item_base = 0, slab_cur = 0, smo_cur = 0, redo_cur = 0;
+    for (size_t k = 0; k < plan.buckets.size(); ++k) {
+        const Bucket &b = plan.buckets[k];
+        PgramArgs ga{};
+        ga.off = w.off;
+        ga.tt = w.tt;
+        ga.yc = w.yc;
+        ga.wv = w.wv;
+        ga.chi0 = w.chi0;
+        ga.ymax = w.ymax;
+        ga.yc64 = w.yc64;
+        ga.wv64 = w.wv64;
+        ga.ydf = w.ydf;
+        ga.wdf = w.wdf;
+        ga.bad = w.bad;
+        ga.freq = freq;
+        ga.n_freq = n_freq;
+        ga.items = w.items + item_base;
+        ga.n_items = (int)b.items.size();
+        ga.item_counter = w.counters + 2 * k;
+        ga.power = out_power;
+        ga.power_f32 = prec == SSP_FP32C;
+        for (int i = 0; i < 3; ++i) ga.spans[i] = P.spans[i];
+        ga.alpha = P.alpha;
+        ga.slab = b.main.gmem ? w.slab + slab_cur : nullptr;
+        ga.smo = b.main.smo_out ? w.slab + plan.slab_total + smo_cur : nullptr;
+        ga.smo_stride = b.main.smo_stride;
+        ga.smo_kmax = smo_rows(b.n_max, b.G);
+        ga.smo_nmax = b.n_max;
+        smo_cur += b.main.smo_stride * (size_t)b.main.grid;
+        ga.redo_slab = b.main.redo_inline ? w.slab + plan.slab_total + plan.smo_total + redo_cur
+                                          : nullptr;
+        ga.redo_slab_bytes = b.main.redo_slab_bytes;
+        redo_cur += b.main.redo_slab_bytes * (size_t)b.main.grid;
+        ga.slab_bytes = b.main.slab_bytes;
+        ga.cnt_smem = b.main.cnt_smem ? 1 : 0;
+        ga.near = w.near;
+        ga.near_ss = near_margin("SSP_NEAR_SS", ssp::kNearSS);
+        ga.near_sp = near_margin("SSP_NEAR_SP", ssp::kNearSP);
+        ga.refit_frac = near_margin("SSP_REFIT_FRAC", ssp::kRefitFrac);
+        ga.sens_ulps = near_margin("SSP_SENS_ULPS", ssp::kSensUlps);
+        ga.sens_tau = near_margin("SSP_SENS_TAU", (float)ssp::kSensTau);
+        ga.recompute = 0;
+        ga.periodic = P.periodic;
+        ga.span = P.span;
+        ga.fbase = fbase;
+        slab_cur += b.main.gmem ? b.main.slab_bytes * (size_t)b.main.grid : 0;
+        const int ph = variant == SSP_SS ? SSP_PHASE_PGRAM_SS : SSP_PHASE_PGRAM_SP;
+        on = prof && prof_begin(ph, s, mk);
+        if ((e = pgram_launch(prec, kv, b.main.gmem, b.main.lng, per, b.shared, b.main.grid, b.G,
+                              b.main.smem, ga, s)))
+            return e;
+        if (hook) hook->launched(LK_PGRAM, &ga);
+        prof_end(on, mk, s);
+        if (plan.redo && !b.main.redo_inline) {
+            // the same items through the FP64 kernel, flagged frequencies only
+            ga.yc = w.yc64;
+            ga.wv = w.wv64;
+            ga.item_counter = w.counters + 2 * k + 1;
+            ga.slab = b.redo.gmem ? w.slab + slab_cur : nullptr;
+            ga.smo = nullptr;
+            ga.redo_slab = nullptr;
+            ga.slab_bytes = b.redo.slab_bytes;
+            ga.cnt_smem = b.redo.cnt_smem ? 1 : 0;
+            ga.recompute = 1;
+            slab_cur += b.redo.gmem ? b.redo.slab_bytes * (size_t)b.redo.grid : 0;
+            on = prof && prof_begin(SSP_PHASE_REDO, s, mk);
+            if ((e = pgram_launch(kPrecRedo, kv, b.redo.gmem, b.redo.lng, per, b.shared, b.redo.grid,
+                                  b.G_redo, b.redo.smem, ga, s)))
+                return e;
+            if (hook) hook->launched(LK_PGRAM, &ga);
+            prof_end(on, mk, s);
+        }
+        item_base += b.items.size();
+    }
+    ArgmaxArgs aa{};
+    aa.power = out_power;
+    aa.freq = freq;
+    aa.fbase = fbase;
+    aa.n_freq = n_freq;
+    aa.bad = w.bad;
+    aa.best_period = out_best;
+    aa.best_power = out_best_power;
+    on = prof && prof_begin(SSP_PHASE_ARGMAX, s, mk);
+    if ((e = argmax_launch(prec, aa, (int)n_obj, s))) return e;
+    if (hook) hook->launched(LK_ARGMAX, &aa);
+    prof_end(on, mk, s);
+    return cudaSuccess;
+}
+
 int run_device(const double *t, const double *y, const double *dy, const int64_t *npo,
                int64_t n_obj, const double *freq, int64_t n_freq, ssp_variant variant,
                const ssp_params &P, void *out_power, double *out_best, cudaStream_t s,
@@ -580,12 +769,12 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
 {
     const int prec = (int)P.precision;
     Plan plan;
-    const int kv = kernel_variant(variant, P);
-    const bool per = P.periodic != 0;
-    int rc = build_plan(npo, n_obj, n_freq, prec, kv, per, plan, group);
+    int rc = build_plan(npo, n_obj, n_freq, prec, kernel_variant(variant, P), P.periodic != 0,
+                        plan, group);
     if (rc) return rc;
-    std::vector<int64_t> off((size_t)n_obj + 1, 0);
-    for (int64_t o = 0; o < n_obj; ++o) off[o + 1] = off[o] + npo[o];
+    std::vector<int64_t> off;
+    std::vector<int4> items;
+    plan_tables(plan, npo, n_obj, off, items);
     const int64_t N = off[n_obj];
     const size_t ws = workspace_bytes(plan, n_obj, N, n_freq, prec);
     unsigned char *base = nullptr;
@@ -594,146 +783,15 @@ int run_device(const double *t, const double *y, const double *dy, const int64_t
         cudaGetLastError();
         return fail(SSP_ERR_NOMEM, "workspace of %zu bytes: %s", ws, cudaGetErrorString(e));
     }
-    size_t cur = 0;
-    auto take = [&](size_t bytes) {
-        unsigned char *p = base + cur;
-        cur += align16(bytes);
-        return p;
-    };
-    int64_t *d_off = (int64_t *)take(8 * (size_t)(n_obj + 1));
-    double *d_tt = (double *)take(8 * (size_t)N);
-    int *d_bad = (int *)take(4 * (size_t)n_obj);
-    void *d_yc = take(rsize(prec) * (size_t)N);
-    void *d_wv = take(rsize(prec) * (size_t)N);
-    double *d_yc64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
-    double *d_wv64 = plan.redo ? (double *)take(8 * (size_t)N) : nullptr;
-    float2 *d_ydf = plan.redo ? (float2 *)take(8 * (size_t)N) : nullptr;
-    float2 *d_wdf = plan.redo ? (float2 *)take(8 * (size_t)N) : nullptr;
-    double *d_chi0 = (double *)take(8 * (size_t)n_obj);
-    double *d_ymax = (double *)take(8 * (size_t)n_obj);
-    int4 *d_items = (int4 *)take(sizeof(int4) * plan.items_total);
-    const size_t n_counters = 2 * plan.buckets.size() + 2;
-    int *d_counters = (int *)take(4 * n_counters);
-    unsigned char *d_near =
-        plan.redo ? (unsigned char *)take((size_t)n_obj * (size_t)n_freq) : nullptr;
-    unsigned char *d_slab = base + cur;
-
-    std::vector<int4> items;
-    items.reserve(plan.items_total);
-    for (const Bucket &b : plan.buckets) items.insert(items.end(), b.items.begin(), b.items.end());
+    const Workspace w = carve_workspace(base, plan, n_obj, N, n_freq, prec);
     int status = SSP_OK;
-    do {
-        if ((e = cudaMemcpyAsync(d_off, off.data(), 8 * off.size(), cudaMemcpyHostToDevice, s))) break;
-        if ((e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(),
-                                 cudaMemcpyHostToDevice, s)))
-            break;
-        if ((e = cudaMemsetAsync(d_counters, 0, 4 * n_counters, s))) break;
-        if (d_near && (e = cudaMemsetAsync(d_near, 0, (size_t)n_obj * (size_t)n_freq, s))) break;
-        PrepArgs pa{};
-        pa.t = t;
-        pa.y = y;
-        pa.dy = dy;
-        pa.off = d_off;
-        pa.tt = d_tt;
-        pa.yc = d_yc;
-        pa.wv = d_wv;
-        pa.yc64 = d_yc64;
-        pa.wv64 = d_wv64;
-        pa.ydf = d_ydf;
-        pa.wdf = d_wdf;
-        pa.chi0 = d_chi0;
-        pa.ymax = d_ymax;
-        pa.bad = d_bad;
-        Mark mk;
-        bool on = prof_begin(SSP_PHASE_PREP, s, mk);
-        if ((e = prep_launch(prec, pa, (int)n_obj, s))) break;
-        prof_end(on, mk, s);
-        size_t item_base = 0, slab_cur = 0, smo_cur = 0, redo_cur = 0;
-        for (size_t k = 0; k < plan.buckets.size(); ++k) {
-            const Bucket &b = plan.buckets[k];
-            PgramArgs ga{};
-            ga.off = d_off;
-            ga.tt = d_tt;
-            ga.yc = d_yc;
-            ga.wv = d_wv;
-            ga.chi0 = d_chi0;
-            ga.ymax = d_ymax;
-            ga.yc64 = d_yc64;
-            ga.wv64 = d_wv64;
-            ga.ydf = d_ydf;
-            ga.wdf = d_wdf;
-            ga.bad = d_bad;
-            ga.freq = freq;
-            ga.n_freq = n_freq;
-            ga.items = d_items + item_base;
-            ga.n_items = (int)b.items.size();
-            ga.item_counter = d_counters + 2 * k;
-            ga.power = out_power;
-            ga.power_f32 = prec == SSP_FP32C;
-            for (int i = 0; i < 3; ++i) ga.spans[i] = P.spans[i];
-            ga.alpha = P.alpha;
-            ga.slab = b.main.gmem ? d_slab + slab_cur : nullptr;
-            ga.smo = b.main.smo_out ? d_slab + plan.slab_total + smo_cur : nullptr;
-            ga.smo_stride = b.main.smo_stride;
-            ga.smo_kmax = smo_rows(b.n_max, b.G);
-            ga.smo_nmax = b.n_max;
-            smo_cur += b.main.smo_stride * (size_t)b.main.grid;
-            ga.redo_slab = b.main.redo_inline ? d_slab + plan.slab_total + plan.smo_total + redo_cur
-                                              : nullptr;
-            ga.redo_slab_bytes = b.main.redo_slab_bytes;
-            redo_cur += b.main.redo_slab_bytes * (size_t)b.main.grid;
-            ga.slab_bytes = b.main.slab_bytes;
-            ga.cnt_smem = b.main.cnt_smem ? 1 : 0;
-            ga.near = d_near;
-            ga.near_ss = near_margin("SSP_NEAR_SS", ssp::kNearSS);
-            ga.near_sp = near_margin("SSP_NEAR_SP", ssp::kNearSP);
-            ga.refit_frac = near_margin("SSP_REFIT_FRAC", ssp::kRefitFrac);
-            ga.sens_ulps = near_margin("SSP_SENS_ULPS", ssp::kSensUlps);
-            ga.sens_tau = near_margin("SSP_SENS_TAU", (float)ssp::kSensTau);
-            ga.recompute = 0;
-            ga.periodic = P.periodic;
-            ga.span = P.span;
-            ga.fbase = fbase;
-            slab_cur += b.main.gmem ? b.main.slab_bytes * (size_t)b.main.grid : 0;
-            const int ph = variant == SSP_SS ? SSP_PHASE_PGRAM_SS : SSP_PHASE_PGRAM_SP;
-            on = prof_begin(ph, s, mk);
-            if ((e = pgram_launch(prec, kv, b.main.gmem, b.main.lng, per, b.shared, b.main.grid, b.G, b.main.smem,
-                                  ga, s)))
-                break;
-            prof_end(on, mk, s);
-            if (plan.redo && !b.main.redo_inline) {
-                // the same items through the FP64 kernel, flagged frequencies only
-                ga.yc = d_yc64;
-                ga.wv = d_wv64;
-                ga.item_counter = d_counters + 2 * k + 1;
-                ga.slab = b.redo.gmem ? d_slab + slab_cur : nullptr;
-                ga.smo = nullptr;
-                ga.redo_slab = nullptr;
-                ga.slab_bytes = b.redo.slab_bytes;
-                ga.cnt_smem = b.redo.cnt_smem ? 1 : 0;
-                ga.recompute = 1;
-                slab_cur += b.redo.gmem ? b.redo.slab_bytes * (size_t)b.redo.grid : 0;
-                on = prof_begin(SSP_PHASE_REDO, s, mk);
-                if ((e = pgram_launch(kPrecRedo, kv, b.redo.gmem, b.redo.lng, per, b.shared, b.redo.grid,
-                                      b.G_redo, b.redo.smem, ga, s)))
-                    break;
-                prof_end(on, mk, s);
-            }
-            item_base += b.items.size();
-        }
-        if (e) break;
-        ArgmaxArgs aa{};
-        aa.power = out_power;
-        aa.freq = freq;
-        aa.fbase = fbase;
-        aa.n_freq = n_freq;
-        aa.bad = d_bad;
-        aa.best_period = out_best;
-        aa.best_power = out_best_power;
-        on = prof_begin(SSP_PHASE_ARGMAX, s, mk);
-        if ((e = argmax_launch(prec, aa, (int)n_obj, s))) break;
-        prof_end(on, mk, s);
-    } while (0);
+    e = cudaMemcpyAsync(w.off, off.data(), 8 * off.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w.items, items.data(), sizeof(int4) * items.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = enqueue_pipeline(plan, w, t, y, dy, n_obj, freq, n_freq, variant, P, out_power, out_best,
+                             s, fbase, out_best_power, true, nullptr);
     if (e) status = cuda_fail(e, "enqueue");
     cudaError_t ef = cudaFreeAsync(base, s);
     if (status == SSP_OK && ef != cudaSuccess) status = cuda_fail(ef, "cudaFreeAsync");
@@ -956,6 +1014,65 @@ int run(const double *t, const double *y, const double *dy, const int64_t *n_per
 }
 }  // namespace ssp_internal
 
+namespace {
+// ---- launch plans: the device pipeline captured into a CUDA graph ----
+struct PlanNode {
+    cudaGraphNode_t node;
+    LaunchKind kind;
+    union {
+        PrepArgs prep;
+        PgramArgs pgram;
+        ArgmaxArgs argmax;
+    } args;
+};
+
+struct PlanRecorder : LaunchHook {
+    cudaStream_t s = nullptr;
+    std::vector<PlanNode> nodes;
+    cudaError_t err = cudaSuccess;
+    void launched(LaunchKind k, const void *a) override
+    {
+        cudaStreamCaptureStatus st;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        const cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &nd);
+        if (e != cudaSuccess || nd != 1) {
+            if (err == cudaSuccess) err = e != cudaSuccess ? e : cudaErrorStreamCaptureUnsupported;
+            return;
+        }
+        PlanNode pn{};
+        pn.node = deps[0];   // the kernel just captured: the capture's only dependency
+        pn.kind = k;
+        if (k == LK_PREP) pn.args.prep = *(const PrepArgs *)a;
+        else if (k == LK_PGRAM) pn.args.pgram = *(const PgramArgs *)a;
+        else pn.args.argmax = *(const ArgmaxArgs *)a;
+        nodes.push_back(pn);
+    }
+};
+
+}  // namespace
+
+struct ssp_plan {
+    ssp_params P{};
+    ssp_variant variant = SSP_SS;
+    int64_t n_obj = 0, n_freq = 0;
+    unsigned char *base = nullptr;   // workspace (cudaMalloc), held by the plan
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<PlanNode> nodes;
+};
+
+namespace {
+void plan_free(ssp_plan *pl)
+{
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->base) cudaFree(pl->base);
+    delete pl;
+}
+}  // namespace
+
+
 extern "C" {
 
 void ssp_default_params(ssp_params *p)
@@ -989,6 +1106,120 @@ const char *ssp_status_string(int status)
 const char *ssp_last_error(void) { return g_err.c_str(); }
 
 const char *ssp_version(void) { return "ssp 0.1 sm_103a"; }
+
+int ssp_plan_create(const int64_t *n_per_object, int64_t n_objects, int64_t n_freq,
+                    ssp_variant variant, const ssp_params *params, ssp_plan **out)
+{
+    g_err.clear();
+    if (!out) return fail(SSP_ERR_ARG, "NULL plan handle pointer");
+    *out = nullptr;
+    ssp_params P;
+    ssp_default_params(&P);
+    if (params) P = *params;
+    int rc = check_params(&P);
+    if (rc) return rc;
+    rc = check_shape(n_per_object, n_objects, n_freq, variant);
+    if (rc) return rc;
+    const int prec = (int)P.precision;
+    Plan plan;
+    rc = build_plan(n_per_object, n_objects, n_freq, prec, kernel_variant(variant, P),
+                    P.periodic != 0, plan);
+    if (rc) return rc;
+    std::vector<int64_t> off;
+    std::vector<int4> items;
+    plan_tables(plan, n_per_object, n_objects, off, items);
+    const int64_t N = off[n_objects];
+    ssp_plan *pl = new ssp_plan;
+    pl->P = P;
+    pl->variant = variant;
+    pl->n_obj = n_objects;
+    pl->n_freq = n_freq;
+    const size_t ws = workspace_bytes(plan, n_objects, N, n_freq, prec);
+    cudaError_t e = cudaMalloc((void **)&pl->base, ws);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        pl->base = nullptr;
+        plan_free(pl);
+        return fail(SSP_ERR_NOMEM, "plan workspace of %zu bytes", ws);
+    }
+    const Workspace w = carve_workspace(pl->base, plan, n_objects, N, n_freq, prec);
+    e = cudaMemcpy(w.off, off.data(), 8 * off.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(w.items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
+    cudaStream_t s = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    PlanRecorder rec;
+    rec.s = s;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        // placeholders for the caller's arrays: every execute sets them
+        const cudaError_t ee = enqueue_pipeline(plan, w, nullptr, nullptr, nullptr, n_objects, nullptr,
+                                                n_freq, variant, P, nullptr, nullptr, s, nullptr,
+                                                nullptr, false, &rec);
+        e = cudaStreamEndCapture(s, &pl->graph);
+        if (e == cudaSuccess) e = ee;
+        if (e == cudaSuccess) e = rec.err;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
+    if (s) cudaStreamDestroy(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        plan_free(pl);
+        return cuda_fail(e, "plan capture");
+    }
+    pl->nodes = std::move(rec.nodes);
+    *out = pl;
+    return SSP_OK;
+}
+
+int ssp_plan_execute(ssp_plan *pl, const double *t, const double *y, const double *dy,
+                     const double *freq_grid, void *out_power, double *out_best_period,
+                     void *stream)
+{
+    g_err.clear();
+    if (!pl) return fail(SSP_ERR_ARG, "NULL plan");
+    if (!t || !y || !dy || !freq_grid || !out_power || !out_best_period)
+        return fail(SSP_ERR_ARG, "NULL array argument");
+    for (PlanNode &pn : pl->nodes) {
+        cudaKernelNodeParams kp;
+        SSP_CUDA(cudaGraphKernelNodeGetParams(pn.node, &kp));
+        PrepArgs pa;
+        PgramArgs ga;
+        ArgmaxArgs aa;
+        void *argp[1];
+        if (pn.kind == LK_PREP) {
+            pa = pn.args.prep;
+            pa.t = t;
+            pa.y = y;
+            pa.dy = dy;
+            argp[0] = &pa;
+        } else if (pn.kind == LK_PGRAM) {
+            ga = pn.args.pgram;
+            ga.freq = freq_grid;
+            ga.power = out_power;
+            argp[0] = &ga;
+        } else {
+            aa = pn.args.argmax;
+            aa.power = out_power;
+            aa.freq = freq_grid;
+            aa.best_period = out_best_period;
+            argp[0] = &aa;
+        }
+        kp.kernelParams = argp;
+        kp.extra = nullptr;
+        SSP_CUDA(cudaGraphExecKernelNodeSetParams(pl->exec, pn.node, &kp));
+    }
+    SSP_CUDA(cudaGraphLaunch(pl->exec, (cudaStream_t)stream));
+    return SSP_OK;
+}
+
+int ssp_plan_destroy(ssp_plan *pl)
+{
+    g_err.clear();
+    if (!pl) return fail(SSP_ERR_ARG, "NULL plan");
+    plan_free(pl);
+    return SSP_OK;
+}
 
 int ssp_test_fault(int kind, int count)
 {

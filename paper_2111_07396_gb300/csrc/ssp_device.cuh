@@ -236,19 +236,24 @@ __host__ __device__ inline int frame_cols(int variant, bool smo_out = false)
 
 // keep_perm: objects with identical times share one sort (their frame keeps
 // perm for every member's gather); an SS frame then holds perm past the tie
-// bitmask, clear of the smoother columns that overlay the sort region
+// bitmask, clear of the smoother columns that overlay the sort region -- or,
+// when the smooths live in the global slab (smo_out), in that slab too, so
+// that two CTAs still share an SM
 template <typename R>
 __host__ __device__ inline size_t frame_bytes(int n, int variant, bool keep_perm = false,
                                               bool smo_out = false)
 {
     size_t b = tie_offset<R>(n, frame_cols(variant, smo_out)) + align16(4 * tie_words(n));
-    if (keep_perm && variant == VAR_SS) b += align16(2 * (size_t)pow2_at_least(n));
+    if (keep_perm && variant == VAR_SS && !smo_out) b += align16(2 * (size_t)pow2_at_least(n));
     return b;
 }
+// bytes of the kept perm in the smooth slab (shared sorts, smo_out)
+__host__ __device__ inline size_t kept_perm_bytes(int n) { return align16(2 * (size_t)pow2_at_least(n)); }
 
 template <typename R>
 __device__ inline Frame<R> carve_frame(unsigned char *base, int n, int variant,
-                                       bool keep_perm = false, bool smo_out = false)
+                                       bool keep_perm = false, bool smo_out = false,
+                                       uint16_t *perm_slab = nullptr)
 {
     Frame<R> f;
     const size_t col = align16(sizeof(R) * (size_t)n), xwy = xwy_bytes<R>(n);
@@ -273,8 +278,9 @@ __device__ inline Frame<R> carve_frame(unsigned char *base, int n, int variant,
     f.ph = (double *)(s + 2 * a4 + ap + align16(4 * (size_t)bucket_count(n)));
     f.tie = (uint32_t *)(base + tie_offset<R>(n, frame_cols(variant, smo_out)));
     if (keep_perm && variant == VAR_SS)
-        f.perm = (uint16_t *)(base + tie_offset<R>(n, frame_cols(variant, smo_out)) +
-                              align16(4 * tie_words(n)));
+        f.perm = smo_out ? perm_slab
+                         : (uint16_t *)(base + tie_offset<R>(n, frame_cols(variant, smo_out)) +
+                                        align16(4 * tie_words(n)));
     f.per = 1;
     return f;
 }
@@ -2288,8 +2294,14 @@ __global__ void __launch_bounds__(kMaxThreads) pgram_kernel(PgramArgs a)
         // frequency's fold and sort
         const int m = SHARED && item.w > 1 ? item.w : 1;
         const int n = (int)(a.off[o + 1] - a.off[o]);
-        // only the kernels for long objects address the smooth slab
-        Frame<R> fr = carve_frame<R>(big, n, VARIANT, SHARED, LONG && a.smo != nullptr);
+        // only the kernels for long objects address the smooth slab; a shared
+        // sort keeps its perm there, past the three smooth columns
+        const bool smo_out = LONG && a.smo != nullptr;
+        uint16_t *perm_slab =
+            smo_out ? (uint16_t *)((unsigned char *)a.smo + (size_t)blockIdx.x * a.smo_stride +
+                                   smo_bytes(a.smo_nmax, G, sizeof(R)))
+                    : nullptr;
+        Frame<R> fr = carve_frame<R>(big, n, VARIANT, SHARED, smo_out, perm_slab);
         sm.dn = divn_make(n);
         ObjK<R> ok = obj_consts<R>(a, n, o);
         fr.per = PER;

@@ -108,6 +108,13 @@ def lib():
                                         ctypes.c_int, ctypes.c_int, ctypes.POINTER(ssp_params), P,
                                         P]
         L.ssp_search_refine.restype = ctypes.c_int
+        L.ssp_plan_create.argtypes = [P, i64, i64, ctypes.c_int, ctypes.POINTER(ssp_params),
+                                      ctypes.POINTER(P)]
+        L.ssp_plan_create.restype = ctypes.c_int
+        L.ssp_plan_execute.argtypes = [P, P, P, P, P, P, P, P]
+        L.ssp_plan_execute.restype = ctypes.c_int
+        L.ssp_plan_destroy.argtypes = [P]
+        L.ssp_plan_destroy.restype = ctypes.c_int
         L.ssp_test_fault.argtypes = [ctypes.c_int, ctypes.c_int]
         L.ssp_test_fault.restype = ctypes.c_int
         _lib = L
@@ -278,6 +285,51 @@ def ssp_search_refine(t, y, dy, n_per_object, coarse_grid, coarse_variant="sp",
                                    VARIANTS[fine_variant], int(n_peaks), int(n_fine),
                                    ctypes.byref(p), _ptr(bp), _ptr(bw)))
     return bp, bw
+
+
+class Plan:
+    """A launch plan (ssp_plan_create / execute / destroy): the device pipeline
+    of one shape captured into a CUDA graph, run on new device arrays."""
+
+    def __init__(self, n_per_object, n_freq, variant="ss", precision="fp32c", alpha=9.0,
+                 spans=None, params=None):
+        self._p = params if params is not None else ssp_default_params(precision, alpha, spans)
+        self._npo = np.ascontiguousarray(n_per_object, dtype=np.int64)
+        self.n_freq = int(n_freq)
+        h = ctypes.c_void_p()
+        _check(lib().ssp_plan_create(_ptr(self._npo), int(self._npo.size), self.n_freq,
+                                     VARIANTS[variant], ctypes.byref(self._p), ctypes.byref(h)))
+        self._h = h
+
+    def ssp_plan_execute(self, t, y, dy, freq_grid, out_power, out_best_period, stream=None):
+        """Device arrays (torch CUDA tensors or raw addresses); enqueued on
+        `stream` (default: torch's current stream)."""
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream()
+        s = stream if isinstance(stream, int) else stream.cuda_stream
+        _check(lib().ssp_plan_execute(self._h, _dev_ptr(t), _dev_ptr(y), _dev_ptr(dy),
+                                      _dev_ptr(freq_grid), _dev_ptr(out_power),
+                                      _dev_ptr(out_best_period), ctypes.c_void_p(s)))
+
+    def ssp_plan_destroy(self) -> None:
+        if self._h:
+            h, self._h = self._h, None
+            _check(lib().ssp_plan_destroy(h))
+
+    execute, close = ssp_plan_execute, ssp_plan_destroy
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ssp_test_fault(kind, count=1) -> None:
