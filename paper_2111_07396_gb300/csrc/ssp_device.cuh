@@ -1481,47 +1481,67 @@ __device__ inline void df_acc(df &s, df x)
     s.lo += t.lo + x.lo;
 }
 __device__ inline double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
+// quotient of two double-floats to about 2^-44 relative: an approximate
+// quotient q1, the residual a - q1 b (its leading part exact by an FMA, the
+// difference a.hi - q1 b.hi exact by Sterbenz's lemma), and its quotient as
+// the correction
+__device__ inline df df_div(df a, df b)
+{
+    const float q1 = __fdividef(a.hi, b.hi);
+    const float p = q1 * b.hi;
+    const float e = fmaf(q1, b.hi, -p);
+    const float r = fmaf(-q1, b.lo, ((a.hi - p) - e) + a.lo);
+    return x_fast(q1, __fdividef(r, b.hi));
+}
+__device__ inline df df_sub(df a, df b) { return acc_add(a, acc_neg(b)); }
+// a < b for normalised double-floats (|lo| at most half an ulp of hi)
+__device__ inline bool df_less(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ inline df df_abs(df a) { return a.hi < 0.f ? acc_neg(a) : a; }
 
 // Settles one contested SP centre je beyond FP32 precision: the line fits of
-// its three span windows from the exact phases (the sorted 64-bit
-// fixed-point keys) and the inputs as double-float pairs read through perm,
-// then the span choice and interpolation in binary64.  The window sums run on
-// the FP32 pipe as double-float sums of error-free products (about 2^-44
-// relative, against binary64's 2^-53; the FP64 pipe issues at 1/64 of the
-// FP32 rate on this chip, which made a binary64 walk over a woofer window the
-// largest wait of the SP kernel).  The windows share their centre and nest
-// (h0 <= h1 <= h2, periodic or clamped), so each point is loaded and summed
-// once: into the tweeter window, or the ring the midrange window adds around
-// it, or the woofer's ring around that (each ring's two segments in one walk);
-// the wider windows' sums are running totals.  sl: bit k set when span k's fit
-// kept its slope, which picks the validation factor as in the FP32 choice.
-// Bit 3 of sl asks for the woofer window too.  Without it (a near-tie whose
-// smaller residual lies more than 1e-4 relative below the woofer's) the
-// woofer's FP32 fit s2f and residual g2f stand in: the span then depends on
-// them only continuously (bass enhancement, interpolation), so their FP32
-// error moves the smooth by about 1e-6 of the fits' spread, and the woofer's
-// ring, the longest walk, is skipped.
+// its span windows from the exact phases (the sorted 64-bit fixed-point keys)
+// and the inputs as double-float pairs read through perm, and the residual
+// comparisons of the span choice, all in double-float arithmetic on the FP32
+// pipe (about 2^-44 relative, against binary64's 2^-53; the FP64 pipe issues
+// at 1/64 of the FP32 rate on this chip).  Once the choice is taken, bass
+// enhancement and interpolation depend on the residuals and fits only
+// continuously, and run in FP32 like every other centre's.  The windows share
+// their centre and nest (h0 <= h1 <= h2, periodic or clamped), so each point
+// is loaded and summed once: into the tweeter window, or the ring the
+// midrange window adds around it, or the woofer's ring around that (each
+// ring's two segments in one walk); the wider windows' sums are running
+// totals.  sl: bit k set when span k's fit kept its slope, which picks the
+// validation factor as in the FP32 choice.  Bit 3 of sl asks for the woofer
+// window too.  Without it (a near-tie whose smaller residual lies more than
+// 1e-4 relative below the woofer's) the woofer's FP32 fit s2f and residual
+// g2f stand in: the span then depends on them only continuously, and the
+// woofer's ring, the longest walk, is skipped.
 // The code runs rarely, from a cold instruction cache, so it is out of line
 // and written once per step (only the walk is unrolled).  All lanes of the
 // warp call it together with the same centre; every lane returns the smooth.
 template <typename R>
-__device__ __noinline__ double sp_settle(const Frame<R> fr, const float2 *ydf, const float2 *wdf,
-                                         int je, int h0, int h1, int h2, int n, int qi, int qj,
-                                         int sl, bool lim0, bool lim1, const double *spans,
-                                         double alpha, float s2f, float g2f)
+__device__ __noinline__ float sp_settle(const Frame<R> fr, const float2 *ydf, const float2 *wdf,
+                                        int je, int h0, int h1, int h2, int n, int qi, int qj,
+                                        int sl, const SpanK<float> K, float s2f, float g2f)
 {
     // bit 3 of sl: refit the woofer window as well, else take its FP32 fit
     const int nk = (sl & 8) ? 3 : 2;
     const uint64_t *key = fr.key;
-    // Listing 1's vsmlsq from the exact phases at the scale indices qi, qj
-    const double sq = df_to_double(key_diff_df(key[qj], key[qi], 0));
-    const double vsmlsq64 = 1.0e-6 * sq * sq;
+    // Listing 1's vsmlsq = 1e-6 scale^2 from the exact phases at the scale
+    // indices qi, qj (1e-6 as a double-float: the binary64 constant split)
+    const df sq = key_diff_df(key[qj], key[qi], 0);
+    const df vsm = df_mul(df_mul(sq, sq), df{1.0e-6f, 2.5247572e-15f});
     const uint16_t *perm = fr.perm;
     const uint64_t kj = key[je];
     const int lo[3] = {win_lo(fr, je, h0, n), win_lo(fr, je, h1, n), win_lo(fr, je, h2, n)};
     const int hw[3] = {h0, h1, h2};
-    double sw = 0.0, sa = 0.0, sb = 0.0, sc = 0.0, sd = 0.0, fit[3];
-    fit[2] = (double)s2f;
+    const float2 y2e = ydf[perm[je]];
+    const df ye{y2e.x, y2e.y};
+    df sw{0.f, 0.f}, sa = sw, sb = sw, sc = sw, sd = sw;
+    df e[3];
+    float fit[3];
+    fit[2] = s2f;
+    e[2] = df{g2f, 0.f};
 #pragma unroll 1
     for (int k = 0; k < nk; ++k) {
         const int hi = lo[k] + 2 * hw[k];
@@ -1529,11 +1549,11 @@ __device__ __noinline__ double sp_settle(const Frame<R> fr, const float2 *ydf, c
         const int ea = lo[k], na = k ? lo[k - 1] - lo[k] : 2 * hw[0] + 1;
         const int eb = k ? lo[k - 1] + 2 * hw[k - 1] + 1 : 0, nb = k ? hi - (eb - 1) : 0;
         df aw{0.f, 0.f}, aa = aw, ab = aw, ac = aw, ad = aw;
-#pragma unroll 2
+#pragma unroll 4
         for (int v = (int)(threadIdx.x & 31); v < na + nb; v += 32) {
-            const int e = v < na ? ea + v : eb + (v - na);
+            const int e_ = v < na ? ea + v : eb + (v - na);
             int sh;
-            const int p = slot_point(e, n, sh);
+            const int p = slot_point(e_, n, sh);
             const uint32_t i = perm[p];
             const df dx = key_diff_df(key[p], kj, sh);
             const float2 w2 = wdf[i], y2 = ydf[i];
@@ -1551,28 +1571,36 @@ __device__ __noinline__ double sp_settle(const Frame<R> fr, const float2 *ydf, c
             q[m] = x_two_sum(q[m].hi, q[m].lo);
             for (int o = 16; o > 0; o >>= 1) q[m] = acc_add(q[m], acc_shfl_xor(q[m], o));
         }
-        sw += df_to_double(q[0]);
-        sa += df_to_double(q[1]);
-        sb += df_to_double(q[2]);
-        sc += df_to_double(q[3]);
-        sd += df_to_double(q[4]);
-        const double xb = sa / sw;   // xbar - x_j
-        const double sxx = sb - xb * sa;
-        const double sxv = sd - xb * sc;
-        const double b = sxx > vsmlsq64 ? sxv / sxx : 0.0;
-        fit[k] = sc / sw + b * (0.0 - xb);
+        sw = acc_add(sw, q[0]);
+        sa = acc_add(sa, q[1]);
+        sb = acc_add(sb, q[2]);
+        sc = acc_add(sc, q[3]);
+        sd = acc_add(sd, q[4]);
+        // x about x_j: xbar - x_j = sa / sw; the fit at x_j
+        const df xb = df_div(sa, sw);
+        const df sxx = df_sub(sb, df_mul(xb, sa));
+        df f = df_div(sc, sw);
+        if (df_less(vsm, sxx)) f = df_sub(f, df_mul(df_div(df_sub(sd, df_mul(xb, sc)), sxx), xb));
+        fit[k] = f.hi + f.lo;
+        // generalized-validation residual |y_j - fit| / (1 - nu/m)
+        const float m = u22f((uint32_t)(2 * hw[k] + 1));
+        const df d = df_sub(df{1.f, 0.f}, df_div(df{((sl >> k) & 1) ? 2.f : 1.f, 0.f}, df{m, 0.f}));
+        e[k] = df_div(df_abs(df_sub(ye, f)), d);
     }
-    const double ye = df_to_double(df{ydf[perm[je]].x, ydf[perm[je]].y});
-    double e[3];
-    e[2] = (double)g2f;
-#pragma unroll 1
-    for (int k = 0; k < nk; ++k) {
-        const double d = 1.0 - (((sl >> k) & 1) ? 2.0 : 1.0) / (double)(2 * hw[k] + 1);
-        e[k] = fabs(ye - fit[k]) / d;
+    // the choice as Listing 1 takes it (first strict minimum; bass only below
+    // the woofer's residual), on the double-float residuals
+    df resmin{1.0e20f, 0.f};
+    float s = K.s2;
+    if (df_less(e[0], resmin)) { resmin = e[0]; s = K.s0; }
+    if (df_less(e[1], resmin)) { resmin = e[1]; s = K.s1; }
+    if (df_less(e[2], resmin)) { resmin = e[2]; s = K.s2; }
+    if (K.bass && df_less(resmin, e[2]) && resmin.hi > 0.f) {
+        float tmp = fdiv(resmin.hi, e[2].hi);
+        if (tmp < 1.0e-7f) tmp = 1.0e-7f;
+        const float pw = (K.ex == 1.f) ? tmp : span_pow(tmp, K.ex);
+        s += (K.s2 - s) * pw;
     }
-    const SpanK<double> K64 = span_consts<double>(spans, alpha);
-    const double sp = choose_span<double>(K64, e[0], e[1], e[2], e[2], K64.s2, lim0, lim1);
-    return interpolate_span<double>(K64, sp, fit[0], fit[1], fit[2]);
+    return interpolate_span<float>(K, s, fit[0], fit[1], fit[2]);
 }
 
 // Where pass A leaves the three smooths for pass C: the frame's columns C0,
@@ -1852,6 +1880,9 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
     const int h0 = ok.h0, h1 = ok.h1, h2 = ok.h2;
     const bool lim0 = ok.lim0, lim1 = ok.lim1;
     const SpanK<R> &K = ok.K;
+    // the span constants in FP32, for the SP settle's continuous steps
+    const SpanK<float> K32{(float)K.s0, (float)K.s1, (float)K.s2, (float)K.inv01,
+                           (float)K.inv21, (float)K.ex, K.bass};
 
     // ---- chunks: contiguous centre ranges that never split a run of ties ----
     {
@@ -2038,8 +2069,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
                                                             (need2 ? 8 : 0), src);
                 const float s2f = __shfl_sync(0xffffffffu, (float)s2, src);
                 const float g2f = __shfl_sync(0xffffffffu, (float)g2, src);
-                const double v = sp_settle<R>(fr, y64, w64, je, h0, h1, h2, n, qi, qj, sl, lim0, lim1,
-                                              a.spans, a.alpha, s2f, g2f);
+                const float v = sp_settle<R>(fr, y64, w64, je, h0, h1, h2, n, qi, qj, sl, K32, s2f, g2f);
                 if (lane == src) val[0] = (R)v;
             }
             if (act) {
