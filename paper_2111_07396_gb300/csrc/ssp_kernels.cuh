@@ -4,6 +4,9 @@
 #pragma once
 #include <cfloat>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "ssp_launch.h"
 
@@ -228,6 +231,29 @@ __global__ void __launch_bounds__(256) peaks_kernel(PeaksArgs a)
     }                                                                                         \
     }
 
+// A kernel's dynamic shared-memory limit is one setting per function and
+// device for the whole process, read when a launch is enqueued.  Plans are
+// built and launched by several host threads (the serving loop's launcher
+// beside direct calls), so the limit is only ever raised: lowering it for a
+// small plan could fail another thread's launch that was planned with more
+// ("invalid argument").
+namespace ssp {
+inline cudaError_t raise_smem_limit(void (*kernel)(PgramArgs), int smem)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int> cur;   // (device, kernel) -> limit set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    int &c = cur[std::make_pair(dev, (const void *)kernel)];
+    if (c >= smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) c = smem;
+    return e;
+}
+}  // namespace ssp
+
 // periodogram kernels of one precision, accumulator and window mode (PER:
 // periodic windows, else clamped inside the data); SHARED: work items may
 // cover several objects with identical times; WL: also the SS kernels that
@@ -237,9 +263,8 @@ __global__ void __launch_bounds__(256) peaks_kernel(PeaksArgs a)
     template <int V, bool GM, bool L>                                                         \
     static cudaError_t occ_##SUF(int G, size_t smem, int *bps)                                \
     {                                                                                         \
-        cudaError_t e = cudaFuncSetAttribute(pgram_kernel<R, V, GM, PLAIN, PER, SHARED, L>,   \
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                                             (int)smem);                                      \
+        cudaError_t e = raise_smem_limit(pgram_kernel<R, V, GM, PLAIN, PER, SHARED, L>,       \
+                                         (int)smem);                                          \
         if (e != cudaSuccess) return e;                                                       \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                 \
             bps, pgram_kernel<R, V, GM, PLAIN, PER, SHARED, L>, G, smem);                     \
