@@ -995,84 +995,113 @@ __device__ inline void win_add_slot(Win<R, NCH> &s, const Frame<R> &fr, const R 
     }
 }
 
-// Sums of the window [c - h, c + h] about origin o.  Whole chunks come from
-// the extended-precision prefixes (raw moments about 0, shifted by -1/+1 for
-// the wrapped parts, then moved to origin o), the ragged ends point by point.
+// Prefix of the chunks before chunk boundary u of period k (-1, 0, +1) of the
+// periodic extension, in extended slot order: with P_u the prefix of period 0
+// and T the total, Q = P_u for k = 0, T + P_u with x -> x + 1 for k = +1 and
+// (P_u - T) with x -> x - 1 for k = -1 (the slots of period -1 before the
+// boundary are those of chunks u.. of period 0, counted negatively).  The
+// moments transform as sum w (x+k) = S1 + k W, sum w (x+k)^2 = S2 + 2k S1 + W,
+// sum w (x+k) v = D + k C.
+template <typename R, int NCH, typename A>
+__device__ inline void ext_prefix(const Small<R, A> &sm, int u, int k, A &W, A &S1, A &S2,
+                                  A (&C)[NCH], A (&D)[NCH])
+{
+    const int L = blockDim.x + 1, G = blockDim.x;
+    W = sm.px[0 * L + u];
+    S1 = sm.px[1 * L + u];
+    S2 = sm.px[2 * L + u];
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+        C[ch] = sm.pc[(2 * ch) * L + u];
+        D[ch] = sm.pc[(2 * ch + 1) * L + u];
+    }
+    if (k == 0) return;
+    if (k < 0) {
+        W = acc_add(W, acc_neg(sm.px[0 * L + G]));
+        S1 = acc_add(S1, acc_neg(sm.px[1 * L + G]));
+        S2 = acc_add(S2, acc_neg(sm.px[2 * L + G]));
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+            C[ch] = acc_add(C[ch], acc_neg(sm.pc[(2 * ch) * L + G]));
+            D[ch] = acc_add(D[ch], acc_neg(sm.pc[(2 * ch + 1) * L + G]));
+        }
+    }
+    const R sg = k < 0 ? R(-1) : R(1);
+    S2 = acc_add(S2, acc_add(acc_mul(S1, R(2) * sg), W));
+    S1 = acc_add(S1, acc_mul(W, sg));
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) D[ch] = acc_add(D[ch], acc_mul(C[ch], sg));
+    if (k > 0) {
+        W = acc_add(W, sm.px[0 * L + G]);
+        S1 = acc_add(S1, sm.px[1 * L + G]);
+        S2 = acc_add(S2, sm.px[2 * L + G]);
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+            C[ch] = acc_add(C[ch], sm.pc[(2 * ch) * L + G]);
+            D[ch] = acc_add(D[ch], sm.pc[(2 * ch + 1) * L + G]);
+        }
+    }
+}
+
+// Chunk boundary nearest to position p (0 <= p <= n) of one period: the
+// first boundary at or after p, or the one before it when that is closer.
+__device__ inline int chunk_nearest(const int *cs, int G, int n, DivN dn, int p)
+{
+    const int u = chunk_lower(cs, G, n, dn, p);
+    return (u > 0 && p - cs[u - 1] < cs[u] - p) ? u - 1 : u;
+}
+
+// Sums of the window [c - h, c + h] about origin o.  In the periodic
+// extension of the sorted points (slot e is point e mod n with x shifted by
+// floor(e / n)), each end of the window is taken to its nearest chunk
+// boundary; the whole chunks between the two boundaries come from the
+// extended-precision prefixes (raw moments about 0, ext_prefix), and the
+// points between each end and its boundary are added or subtracted one by
+// one, both ends in one loop.  The sums are then moved to origin o in the
+// extended type and rounded once.
 template <typename R, int NCH, bool DIFF = false, typename A>
 __device__ inline void win_init_body(Win<R, NCH> &s, const Frame<R> &fr, const Small<R, A> &sm,
                                      const R *const *v, int c, int h, int n, R o)
 {
     const int G = blockDim.x, L = G + 1;
-    A W = acc_from<A>(R(0)), S1 = W, S2 = W, C[NCH], D[NCH];
-#pragma unroll
-    for (int ch = 0; ch < NCH; ++ch) C[ch] = D[ch] = W;
     s.zero();
-    // three segments of constant shift: slots before 0, inside, after n-1
     const int ea = win_lo(fr, c, h, n), eb = ea + 2 * h;
     if (2 * h + 1 <= kDirectInit) {
         // a short window costs less summed point by point than from prefixes
         for (int e = ea; e <= eb; ++e) win_add<R, NCH, DIFF>(s, fr, v, e, n, o, R(1));
         return;
     }
-#pragma unroll 1
-    for (int seg = -1; seg <= 1; ++seg) {
-        int pa, pb;
-        if (seg < 0) { pa = ea + n; pb = n - 1; if (ea >= 0) continue; }
-        else if (seg == 0) { pa = ea < 0 ? 0 : ea; pb = eb >= n ? n - 1 : eb; }
-        else { pa = 0; pb = eb - n; if (eb < n) continue; }
-        int ua = chunk_lower(sm.cs, G, n, sm.dn, pa);
-        int ub = chunk_upper(sm.cs, G, n, sm.dn, pb + 1);
-        // points walked one by one: [la, la + nl) with sign sl, then
-        // [pr + nl, pr + nt) with sign sr
-        int nl = pb - pa + 1, nt = nl, pr = pa, la = pa;
-        R sl = R(1), sr = R(1);
-        if (ua < ub) {
-            // Each ragged end is walked from the nearer chunk boundary: the
-            // points between the window's end and the chunk boundary inside
-            // it are added, or those between it and the boundary outside it
-            // subtracted from a whole chunk's sums, whichever are fewer.
-            const bool wide_l = ua > 0 && pa - sm.cs[ua - 1] < sm.cs[ua] - pa;
-            const bool wide_r = ub < G && sm.cs[ub + 1] - (pb + 1) < (pb + 1) - sm.cs[ub];
-            if (wide_l) { --ua; sl = R(-1); }
-            if (wide_r) { ++ub; sr = R(-1); }
-            // chunks ua..ub-1 lie inside [pa, pb]
-            const A w = acc_add(sm.px[0 * L + ub], acc_neg(sm.px[0 * L + ua]));
-            A s1 = acc_add(sm.px[1 * L + ub], acc_neg(sm.px[1 * L + ua]));
-            A s2 = acc_add(sm.px[2 * L + ub], acc_neg(sm.px[2 * L + ua]));
-            A cc[NCH], dd[NCH];
+    // ends of the half-open slot range [ea, eb + 1): period and position
+    // (-n < ea < n and 0 < eb + 1 < 2n; clamped windows lie in period 0)
+    const int ka = ea < 0 ? -1 : 0, kb = eb + 1 > n ? 1 : 0;
+    const int pa = ea - ka * n, pb = eb + 1 - kb * n;
+    const int ua = chunk_nearest(sm.cs, G, n, sm.dn, pa);
+    const int ub = chunk_nearest(sm.cs, G, n, sm.dn, pb);
+    A W, S1, S2, C[NCH], D[NCH];
+    {
+        A W0, S10, S20, C0[NCH], D0[NCH];
+        ext_prefix<R, NCH, A>(sm, ua, ka, W0, S10, S20, C0, D0);
+        ext_prefix<R, NCH, A>(sm, ub, kb, W, S1, S2, C, D);
+        W = acc_add(W, acc_neg(W0));
+        S1 = acc_add(S1, acc_neg(S10));
+        S2 = acc_add(S2, acc_neg(S20));
 #pragma unroll
-            for (int ch = 0; ch < NCH; ++ch) {
-                cc[ch] = acc_add(sm.pc[(2 * ch) * L + ub], acc_neg(sm.pc[(2 * ch) * L + ua]));
-                dd[ch] = acc_add(sm.pc[(2 * ch + 1) * L + ub], acc_neg(sm.pc[(2 * ch + 1) * L + ua]));
-            }
-            if (seg != 0) {
-                // x -> x + seg: s2 += 2 seg s1 + W, s1 += seg W, D += seg C
-                const R sg = seg < 0 ? R(-1) : R(1);
-                s2 = acc_add(s2, acc_add(acc_mul(s1, R(2) * sg), w));
-                s1 = acc_add(s1, acc_mul(w, sg));
-#pragma unroll
-                for (int ch = 0; ch < NCH; ++ch) dd[ch] = acc_add(dd[ch], acc_mul(cc[ch], sg));
-            }
-            W = acc_add(W, w);
-            S1 = acc_add(S1, s1);
-            S2 = acc_add(S2, s2);
-#pragma unroll
-            for (int ch = 0; ch < NCH; ++ch) {
-                C[ch] = acc_add(C[ch], cc[ch]);
-                D[ch] = acc_add(D[ch], dd[ch]);
-            }
-            // ragged ends, both in one loop
-            const int fa = sm.cs[ua], fb = sm.cs[ub];
-            la = wide_l ? fa : pa;
-            nl = wide_l ? pa - fa : fa - pa;
-            const int ra = wide_r ? pb + 1 : fb;
-            nt = nl + (wide_r ? fb - (pb + 1) : pb + 1 - fb);
-            pr = ra - nl;
+        for (int ch = 0; ch < NCH; ++ch) {
+            C[ch] = acc_add(C[ch], acc_neg(C0[ch]));
+            D[ch] = acc_add(D[ch], acc_neg(D0[ch]));
         }
-        for (int k = 0; k < nt; ++k)
-            win_add_slot<R, NCH, DIFF>(s, fr, v, k < nl ? la + k : pr + k,
-                                       seg == 0 ? R(0) : (seg < 0 ? R(-1) : R(1)), o,
-                                       k < nl ? sl : sr);
+    }
+    // ragged ends, both in one loop: points [la, la + nl) of period ka with
+    // sign sl, points [lb, lb + nr) of period kb with sign sr
+    const int qa = sm.cs[ua], qb = sm.cs[ub];
+    const int la = qa >= pa ? pa : qa, nl = qa >= pa ? qa - pa : pa - qa;
+    const int lb = qb <= pb ? qb : pb, nr = qb <= pb ? pb - qb : qb - pb;
+    const R sl = qa >= pa ? R(1) : R(-1), sr = qb <= pb ? R(1) : R(-1);
+    const R sha = (R)ka, shb = (R)kb;
+    const int nm = nl > nr ? nl : nr;
+    for (int k = 0; k < nm; ++k) {
+        if (k < nl) win_add_slot<R, NCH, DIFF>(s, fr, v, la + k, sha, o, sl);
+        if (k < nr) win_add_slot<R, NCH, DIFF>(s, fr, v, lb + k, shb, o, sr);
     }
     // about o: A = S1 - o W, B = S2 - 2 o S1 + o^2 W, D = D - o C
     const A oW = acc_mul(W, o);
