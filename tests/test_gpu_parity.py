@@ -283,13 +283,16 @@ def test_bass_alpha(variant, code, alpha):
 @pytest.mark.parametrize("variant,code,env", [
     ("sp", oracle.SP, {"SSP_NEAR_SP": "100000", "SSP_SENS_TAU": "0"}),
     ("ss", oracle.SS, {"SSP_REFIT_FRAC": "100000"}),
+    ("ss", oracle.SS, {"SSP_NEAR_SS": "100000"}),
 ])
 def test_forced_binary64_paths(variant, code, env, periodic, monkeypatch):
     # The FP32C path's binary64 fallbacks run only where a decision or a window
     # is marginal.  Widening their triggers (read at each launch) sends nearly
     # every centre through them: SP settles each contested centre in binary64
-    # over its three nested windows; SS refits every window in binary64.  The
-    # result must still be the oracle's.
+    # over its three nested windows; SS refits every window in binary64, or
+    # recomputes every frequency in binary64 (in the same CTA for objects of
+    # more than 1,536 points, by a second launch below).  The result must
+    # still be the oracle's.
     c1 = synth.config1(n_freq=120)
     # minimum size, duplicated times (tie runs), 385 and 1,537 points (the
     # latter takes the SS kernel whose windows initialise out of line)
