@@ -1590,7 +1590,7 @@ __device__ __noinline__ float sp_settle(const Frame<R> fr, const float2 *ydf, co
         const int ea = lo[k], na = k ? lo[k - 1] - lo[k] : 2 * hw[0] + 1;
         const int eb = k ? lo[k - 1] + 2 * hw[k - 1] + 1 : 0, nb = k ? hi - (eb - 1) : 0;
         df aw{0.f, 0.f}, aa = aw, ab = aw, ac = aw, ad = aw;
-#pragma unroll 4
+#pragma unroll 2
         for (int v = (int)(threadIdx.x & 31); v < na + nb; v += 32) {
             const int e_ = v < na ? ea + v : eb + (v - na);
             int sh;
@@ -1610,6 +1610,7 @@ __device__ __noinline__ float sp_settle(const Frame<R> fr, const float2 *ydf, co
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
             q[m] = x_two_sum(q[m].hi, q[m].lo);
+#pragma unroll 1
             for (int o = 16; o > 0; o >>= 1) q[m] = acc_add(q[m], acc_shfl_xor(q[m], o));
         }
         sw = acc_add(sw, q[0]);
