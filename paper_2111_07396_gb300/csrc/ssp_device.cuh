@@ -2235,7 +2235,11 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
             }
         }
     }
-    __syncthreads();
+    // No barrier here, nor after pass C: the next pass's prefix build reads
+    // only this thread's own chunk, and its scan's barrier comes before any
+    // thread reads another's columns or overwrites what this pass reads (the
+    // barrier after pass A stays: its leverage-1 fix-up reads the previous
+    // chunk).
 
     // pass C: midrange smooth of the chosen spans, clamp and interpolate -> C1
     {
@@ -2284,7 +2288,6 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
             }
         }
     }
-    __syncthreads();
 
     // pass D: final tweeter smooth and chi2
     {
