@@ -60,6 +60,14 @@ UNIT = "pt*f/s"
 OPS_PER_PTF = {"ss": 3 * 49 + 3 * 40 + 40 + 40 + 8 + 8 + 3,
                "sp": 3 * 40 + 3 * 3 + 8 + 8 + 3,
                "spg": 3 * 40 + 3 * 3 + 3}
+
+
+def ops_per_ptf(variant, n_per_object):
+    """The smoothing ops above plus the sort, counted as compare/exchange
+    steps at the same rate: log2 n per point, the comparison-sort bound,
+    averaged over the catalog's points."""
+    npo = np.asarray(n_per_object, dtype=np.float64)
+    return OPS_PER_PTF[variant] + float(np.sum(npo * np.log2(npo)) / np.sum(npo))
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per full-size launch of the FP32C periodogram
 # kernels, from one ncu capture of this workload.  They apply only to the
@@ -420,16 +428,17 @@ def run_ours(args):
     sp_launches, sp_ms = prof["pgram_sp"]
     clk_mhz = clocks["sm_mhz"] if clocks else 1432.0
     peak = FP32_LANES_PER_SM * sms * clk_mhz * 1e6 / 1e12
-    ach_ss = OPS_PER_PTF["ss"] * n * nf / (ss_ms / ss_launches / 1e3) / 1e12
-    ach_sp = OPS_PER_PTF["sp"] * n * nf / (sp_ms / sp_launches / 1e3) / 1e12
+    ops_ss, ops_sp = ops_per_ptf("ss", [n]), ops_per_ptf("sp", [n])
+    ach_ss = ops_ss * n * nf / (ss_ms / ss_launches / 1e3) / 1e12
+    ach_sp = ops_sp * n * nf / (sp_ms / sp_launches / 1e3) / 1e12
     roof = {"bound": "alu", "kernel": "pgram_kernel<float,SS>", "achieved": ach_ss,
             "peak": peak, "unit": "TFLOP/s", "frac": ach_ss / peak,
             "traffic": traffic_per_launch("ss"),
-            "ops_per_ptf": OPS_PER_PTF["ss"], "avg_launch_ms": ss_ms / ss_launches,
+            "ops_per_ptf": ops_ss, "avg_launch_ms": ss_ms / ss_launches,
             "peak_basis": f"{FP32_LANES_PER_SM} FP32 ops/clk/SM x {sms} SMs x "
                           f"{clk_mhz:.0f} MHz (median SM clock sampled during the timed region)",
             "sp": {"kernel": "pgram_kernel<float,SP>", "achieved": ach_sp,
-                   "frac": ach_sp / peak, "ops_per_ptf": OPS_PER_PTF["sp"],
+                   "frac": ach_sp / peak, "ops_per_ptf": ops_sp,
                    "traffic": traffic_per_launch("sp"),
                    "avg_launch_ms": sp_ms / sp_launches}}
 
@@ -626,10 +635,10 @@ def run_matrix(args):
                                       "max_abs_err": float(np.max(np.abs(p32s - p64s))),
                                       "best_index_same": same,
                                       "best_period_same": float(np.mean(b32[:ns] == b64s))},
-                    "roofline": {"bound": "alu", "ops_per_ptf": OPS_PER_PTF[v],
-                                 "achieved": OPS_PER_PTF[v] * ptf / (k_ms / 1e3) / 1e12,
+                    "roofline": {"bound": "alu", "ops_per_ptf": ops_per_ptf(v, cat.n_per_object),
+                                 "achieved": ops_per_ptf(v, cat.n_per_object) * ptf / (k_ms / 1e3) / 1e12,
                                  "peak": peak, "unit": "TFLOP/s",
-                                 "frac": OPS_PER_PTF[v] * ptf / (k_ms / 1e3) / 1e12 / peak},
+                                 "frac": ops_per_ptf(v, cat.n_per_object) * ptf / (k_ms / 1e3) / 1e12 / peak},
                     "autotune": tune, "clocks": clocks,
                     "cpu_baseline": cpu}
             print(json.dumps(line), flush=True)
