@@ -189,9 +189,8 @@ int ssp_periodogram_device_noalloc(const double *t, const double *y, const doubl
                                    double *out_best_period, void *stream);
 
 /*
- * Launch plans: the device pipeline captured into a CUDA graph (spec:
- * a graph-captured launch sequence for the batched path; the paper has no
- * counterpart).  For callers that run one shape again and again -- the same
+ * Launch plans: the device pipeline captured into a CUDA graph (the paper
+ * has no counterpart; it launches each kernel from the host, Sec. 4).  For callers that run one shape again and again -- the same
  * objects' point counts, frequency count, variant and params, new values --
  * ssp_plan_create does the host work of ssp_periodogram_device once: it
  * builds the launch plan, takes the workspace (cudaMalloc, held until
