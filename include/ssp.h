@@ -190,8 +190,9 @@ int ssp_periodogram_device_noalloc(const double *t, const double *y, const doubl
 
 /*
  * Launch plans: the device pipeline captured into a CUDA graph (the paper
- * has no counterpart; it launches each kernel from the host, Sec. 4).  For callers that run one shape again and again -- the same
- * objects' point counts, frequency count, variant and params, new values --
+ * has no counterpart; it launches each kernel from the host, Sec. 4).  For
+ * callers that run one shape again and again -- the same objects' point
+ * counts, frequency count, variant and params, new values --
  * ssp_plan_create does the host work of ssp_periodogram_device once: it
  * builds the launch plan, takes the workspace (cudaMalloc, held until
  * ssp_plan_destroy), uploads the plan's tables and captures the pipeline
