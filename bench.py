@@ -74,8 +74,8 @@ FP32_LANES_PER_SM = 128
 # kernel sources they were taken on: bench.py reports them while the hash of
 # those sources still matches, else null.
 TRAFFIC_SOURCES = ("ssp_device.cuh", "ssp_kernels.cuh", "ssp_fold.h", "ssp_launch.h", "ssp_fp32.cu")
-TRAFFIC = {"sha256": "cbf1daac7365a67bedc65c636e4f0f70ef7e3892b52fbc37547b013f839cb839",
-           "ss": 2385664 + 815360, "sp": 1213696 + 18432}
+TRAFFIC = {"sha256": "82c63a68a2f9e2661cc3da8f30fd31d7712eb194ef6c69cc5dd4b84d2f65c77f",
+           "ss": 2444032 + 799744, "sp": 1696768 + 15360}
 
 
 def traffic_per_launch(variant):
@@ -119,6 +119,11 @@ def parse():
     ap.add_argument("--serve", action="store_true", help="serving workload (ssp_server_*)")
     ap.add_argument("--rate", type=float, default=2000.0, help="--serve: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="--serve: seconds of arrivals")
+    ap.add_argument("--serve-autotune", action="store_true",
+                    help="--serve: tune the CTA sizes on a sample of the stream's objects first (not timed)")
+    ap.add_argument("--serve-slots", type=int, default=0, help="--serve: batch slots (0: the server's default)")
+    ap.add_argument("--serve-batch-ptf", type=float, default=0.0,
+                    help="--serve: points x frequencies per batch at most (0: the server's default)")
     ap.add_argument("--serve-freq", type=int, default=10_000, help="--serve: trial frequencies")
     ap.add_argument("--matrix", default="", help="comma list of configurations (c1..c4)")
     ap.add_argument("--extras", action="store_true",
@@ -486,7 +491,17 @@ def run_serve(args):
     N, nf = int(arrivals.size), int(cat.freq.size)
     objs = [cat.obj(k) for k in range(N)]
     names = ("ss", "sp")
-    srv = ssp.Server(cat.freq, precision="fp32c")
+    tune = None
+    if args.serve_autotune:
+        # a sample of the stream (every 50th object) and of the grid; the choice
+        # holds for the rest of the process, as for any later call
+        t_tune = time.perf_counter()
+        sub = cat.subset(list(range(0, N, 50)))
+        tune = {v: ssp.ssp_autotune(sub.t, sub.y, sub.dy, sub.n_per_object, sub.freq, variant=v,
+                                    budget_ptf=1e9).tolist() for v in names}
+        tune["s"] = time.perf_counter() - t_tune
+    srv = ssp.Server(cat.freq, precision="fp32c", slots=args.serve_slots,
+                     max_batch_ptf=args.serve_batch_ptf)
     for k in range(8):                              # warm-up: plans, pools, pinned buffers
         t, y, dy = objs[k]
         srv.poll(srv.submit(t, y, dy, names[k % 2]), wait_ms=60000)
@@ -541,11 +556,12 @@ def run_serve(args):
             "latency_ms": {"p50": q(lat, 50), "p90": q(lat, 90), "p99": q(lat, 99),
                            "max": float(np.nanmax(lat))},
             "server_latency_ms": {"p50": q(lat_srv, 50), "p99": q(lat_srv, 99)},
-            "dtype": "f32", "data": "synthetic", "clocks": clk.summary(),
+            "dtype": "f32", "data": "synthetic", "clocks": clk.summary(), "autotune": tune,
             "config": {"workload": f"Poisson arrivals {args.rate:g}/s for {args.duration:g} s, "
                                    f"n ~ logU(30, 3000), {nf} freqs in [0.05, 15), "
                                    "variant per request Bernoulli(0.5), FP32C",
-                       "api": "ssp_server_submit / next / poll (host arrays)"}}
+                       "api": "ssp_server_submit / next / poll (host arrays)",
+                       "slots": args.serve_slots or "default", "max_batch_ptf": args.serve_batch_ptf or "default"}}
     print(json.dumps(line), flush=True)
 
 

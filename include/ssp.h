@@ -61,10 +61,13 @@ typedef enum {
  * more, or an empty one, keeps the default; a negative margin disables its
  * test):
  *   SSP_NEAR_SS     SS tweeter-vs-midrange margin for n <= 256 (default 1e-6,
- *                   relative; scaled down for larger n).  Flags the frequency
- *                   for the binary64 recompute.
- *   SSP_NEAR_SP     SP near-tie margin in FP32 ulps of the magnitude scale
- *                   (default 64).
+ *                   relative; scaled down for larger n, off above 2,048
+ *                   points).  Flags the frequency for the binary64 recompute.
+ *   SSP_NEAR_SS_ABS the same margin's absolute part, in FP32 units of the
+ *                   object's largest centred magnitude (default 16; off
+ *                   above 2,048 points).
+ *   SSP_NEAR_SP     SP near-tie margin in FP32 units of the magnitude scale
+ *                   (default 32).
  *   SSP_SENS_TAU    SP: power budget per point; a near-tie whose other choice
  *                   could move the power by more is settled in binary64
  *                   (default 1e-6).

@@ -232,8 +232,8 @@ int group_size_rule(int n, int variant, int precision, bool smo_ok = true)
     int g;
     if (n <= 384) g = 32;
     else if (n <= 768) g = 64;
-    else if (n <= 1536) g = 128;
-    else if (variant == SSP_SS && precision == SSP_FP32C && n > 2048) g = smo_ok ? 256 : 512;
+    else if (n <= 2048) g = 128;   // 12-16 centres per thread
+    else if (variant == SSP_SS && precision == SSP_FP32C) g = smo_ok ? 256 : 512;
     else g = 256;
     if (scale > 1) g = std::min(512, g * scale);
     if (scale < 0) g = std::max(32, g / -scale);
@@ -709,6 +709,7 @@ cudaError_t enqueue_pipeline(const Plan &plan, const Workspace &w, const double 
         ga.cnt_smem = b.main.cnt_smem ? 1 : 0;
         ga.near = w.near;
         ga.near_ss = near_margin("SSP_NEAR_SS", ssp::kNearSS);
+        ga.near_ss_abs = near_margin("SSP_NEAR_SS_ABS", ssp::kNearSSAbs);
         ga.near_sp = near_margin("SSP_NEAR_SP", ssp::kNearSP);
         ga.refit_frac = near_margin("SSP_REFIT_FRAC", ssp::kRefitFrac);
         ga.sens_ulps = near_margin("SSP_SENS_ULPS", ssp::kSensUlps);
@@ -933,6 +934,7 @@ int run_device_noalloc(const double *t, const double *y, const double *dy, const
             ga.alpha = P.alpha;
             ga.near = d_near;
             ga.near_ss = near_margin("SSP_NEAR_SS", ssp::kNearSS);
+            ga.near_ss_abs = near_margin("SSP_NEAR_SS_ABS", ssp::kNearSSAbs);
             ga.near_sp = near_margin("SSP_NEAR_SP", ssp::kNearSP);
             ga.refit_frac = near_margin("SSP_REFIT_FRAC", ssp::kRefitFrac);
             ga.sens_ulps = near_margin("SSP_SENS_ULPS", ssp::kSensUlps);

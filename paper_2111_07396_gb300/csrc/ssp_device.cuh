@@ -61,6 +61,7 @@ constexpr int kBucketRankMax = 64;   // larger buckets switch to the bitonic sor
 // and the settles spread evenly over |g0 - g1| (half of them in the top
 // octave of the margin): kNearSP keeps twice the largest distance seen.
 constexpr float kNearSS = 1e-6f;
+constexpr float kNearSSAbs = 8.f;
 // Above this many points the SS tweeter/midrange margin flags nothing: one
 // choice decided either way moves the power by little there.  Measured by
 // recomputing every flagged frequency in binary64 (3.6e4 of them, catalogs of
@@ -114,6 +115,7 @@ struct PgramArgs {
     const int64_t *fbase;   // null: one grid; else object o's grid starts at freq[fbase[o]]
     int power_f32;          // power array holds float
     float near_ss;          // SS margin for n <= 256 (scaled down above)
+    float near_ss_abs;      // SS margin in units of eps_fp32 * the object's largest magnitude
     float near_sp;          // SP margin in units of eps_fp32 * magnitude scale
     float refit_frac;       // refit windows whose spread fell below this part of hiB
     float sens_ulps;        // SP sensitivity: rounding of a residual, in ulps of its scale
@@ -1382,10 +1384,14 @@ __device__ inline R choose_span(const SpanK<R> &K, R r0, R r1, R r2, R res_woof,
 }
 
 // tweeter and midrange residuals so close that FP32 rounding could reorder them
+// (diff is their directly smoothed difference).  Each CV residual carries
+// an FP32 error of a few ulps of the magnitudes its window sums held, not of
+// the residual itself, so the margin has a relative part and an absolute
+// one at the object's magnitude scale.
 template <typename R>
-__device__ inline bool span_contested(R diff, R r0, R r1, float margin)
+__device__ inline bool span_contested(R diff, R r0, R r1, float margin, float margin_abs)
 {
-    return sizeof(R) == 4 && fabs(diff) <= (R)margin * fmax(r0, r1);
+    return sizeof(R) == 4 && (fabs(diff) <= (R)margin * fmax(r0, r1) || fabs(diff) <= (R)margin_abs);
 }
 
 template <typename R>
@@ -1682,7 +1688,8 @@ struct ObjK {
     // points) for a line (nu = 2) and a constant (nu = 1)
     R gl0, gc0, gl1, gc1, gl2, gc2;
 
-    float margin;         // SS: tweeter-vs-midrange margin
+    float margin;         // SS: tweeter-vs-midrange margin, relative
+    float margin_abs;     // and absolute (the residuals' FP32 error scale)
     R sens_lim, ymax;     // SP: chi2 budget per point, largest centred magnitude
 };
 template <typename R>
@@ -1703,8 +1710,10 @@ __device__ inline ObjK<R> obj_consts(const PgramArgs &a, int n, int obj)
     k.gl2 = R(1) / (R(1) - R(2) / m2);
     k.gc2 = R(1) / (R(1) - R(1) / m2);
     k.K = span_consts<R>(a.spans, a.alpha);
-    k.margin = n > kNearSSMaxN ? -1.f
-                               : a.near_ss * fminf(1.f, 256.f / (float)n) * fminf(1.f, 512.f / (float)n);
+    // both parts shrink with n as the effect of one flipped choice does
+    const float shrink = fminf(1.f, 256.f / (float)n) * fminf(1.f, 512.f / (float)n);
+    k.margin = n > kNearSSMaxN ? -1.f : a.near_ss * shrink;
+    k.margin_abs = n > kNearSSMaxN ? -1.f : a.near_ss_abs * shrink * 1.1920929e-7f * (float)a.ymax[obj];
     k.sens_lim = (R)(a.sens_tau * a.chi0[obj]);
     k.ymax = (R)a.ymax[obj];
     return k;
@@ -2207,7 +2216,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
         constexpr bool DIFF = sizeof(R) == 4;
         constexpr int NB = DIFF ? 4 : 3;
         const R *vr[3] = {fr.C[1], fr.C[3], fr.C[5]};
-        const float margin = ok.margin;
+        const float margin = ok.margin, margin_abs = ok.margin_abs;
         // resolves the -1 residuals of pass A while it sums them
         build_channel_prefix<R, NB, DIFF, true, !LONG>(fr, sm, vr, c0, c1, o);
         __syncthreads();
@@ -2218,7 +2227,7 @@ __device__ FreqResult process_frequency(const PgramArgs &a, const ObjK<R> &ok, i
             ra.reset(c0);
             auto emit = [&](int i, const R (&v)[NB]) {
                 const R d01 = DIFF ? v[NB - 1] : v[0] - v[1];
-                if (span_contested(d01, v[0], v[1], margin)) near = true;
+                if (span_contested(d01, v[0], v[1], margin, margin_abs)) near = true;
                 // when no residual is below 1e20 the span column keeps the
                 // woofer's CV residual, as Listing 1's column 6 does
                 fr.C[6][i] = choose_span<R>(K, v[0], v[1], v[2], v[2], fr.C[5][i], lim0, lim1,

@@ -242,6 +242,23 @@ def test_sp_tweeter_midrange_near_tie(obj, q):
     assert gate_error(got, ref) <= TOL["fp32c"]
 
 
+def test_ss_tweeter_midrange_near_tie_at_magnitude_scale():
+    # A 32-point object of the serving mix (n ~ logU(30, 3000), 10^4
+    # frequencies in [0.05, 15)) whose smoothed tweeter and midrange residuals
+    # differ by 1.4e-7, about 1.5 FP32 units of its largest magnitude but 13
+    # ulps of the residuals themselves: FP32 took the other span, and the
+    # power moved by 9e-4 of itself.  The SS margin's absolute part must send
+    # this frequency to the binary64 recompute.
+    cat = synth.config3(n_objects=1325, n_freq=10_000, n_lo=30, n_hi=3000, f_range=(0.05, 15.0))
+    t, y, dy = cat.obj(1324)
+    assert t.size == 32
+    fq = cat.freq[9619:9624]
+    ref, _ = oracle.periodogram(t, y, dy, [t.size], fq, oracle.SS)
+    for precision in ("fp64", "fp32c"):
+        got, _ = ssp.ssp_periodogram(t, y, dy, [t.size], fq, variant="ss", precision=precision)
+        assert gate_error(got, ref) <= TOL[precision], precision
+
+
 @pytest.mark.parametrize("periodic,span", [(False, 0.0), (True, 0.3), (False, 0.12)])
 @pytest.mark.parametrize("variant,code", VARIANTS)
 def test_window_modes(variant, code, periodic, span):
