@@ -242,6 +242,20 @@ def test_sp_tweeter_midrange_near_tie(obj, q):
     assert gate_error(got, ref) <= TOL["fp32c"]
 
 
+@pytest.mark.parametrize("variant", ["ss", "sp"])
+def test_serving_mix_fp32c_within_gate_of_fp64(variant):
+    # The serving workload's size mix (n ~ logU(30, 3000), frequencies in
+    # [0.05, 15)) on 400 objects: every FP32C power within the gate of the
+    # FP64 path (itself oracle-checked) and the same best frequency.
+    cat = synth.config3(n_objects=400, n_freq=2000, n_lo=30, n_hi=3000, f_range=(0.05, 15.0),
+                        config_index=5)
+    args = (cat.t, cat.y, cat.dy, cat.n_per_object, cat.freq)
+    p64, _ = ssp.ssp_periodogram(*args, variant=variant, precision="fp64")
+    p32, _ = ssp.ssp_periodogram(*args, variant=variant, precision="fp32c")
+    assert gate_error(p32, p64) <= TOL["fp32c"]
+    assert np.array_equal(np.argmax(p32, axis=1), np.argmax(p64, axis=1))
+
+
 def test_ss_tweeter_midrange_near_tie_at_magnitude_scale():
     # A 32-point object of the serving mix (n ~ logU(30, 3000), 10^4
     # frequencies in [0.05, 15)) whose smoothed tweeter and midrange residuals
