@@ -108,3 +108,32 @@ def test_sp_reading_on_the_same_cases():
     sgn = (-1.0) ** np.arange(n)
     got = oracle.supsmu_sp(x, sgn, w, iper=2, alpha=9.0)
     np.testing.assert_allclose(got, sgn / 57.0, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("n,span,fit", [(100, 1, 1.0 / 21.0), (110, 2, 1.0 / 57.0)])
+def test_spg_reading_on_alternating_sequences(n, span, fit):
+    # The SPG reading (one span per frequency, least summed squared
+    # generalized-validation residual, reading 15): on y = (-1)^j every point
+    # has the same residual per span, |1 - fit_h| / (1 - 2/m) with the window
+    # means fit_h = +-1/(2h+1) of the cases above: n = 100 gives 1.6, 20/19
+    # and 52/49 (the midrange wins), n = 110 gives 1.6, 8/7 and 56/55 (the
+    # woofer wins).  The smooth is that span's fit, (-1)^j / 21 or / 57.
+    x, w = _grid(n)
+    sgn = (-1.0) ** np.arange(n)
+    got, k = oracle.supsmu_spg(x, sgn, w, iper=2)
+    assert k == span
+    np.testing.assert_allclose(got, sgn * fit, rtol=0, atol=1e-15)
+
+
+def test_spg_reading_on_a_cosine():
+    # On y = cos(2 pi x) the residual of span h is |cos(2 pi x_j)| (1 - m_h) /
+    # (1 - 2/m): the same column times a constant per span, smallest for the
+    # tweeter (the least curvature bias), so SPG takes the tweeter's fit,
+    # cos(2 pi x) m_3.
+    n = 100
+    x, w = _grid(n)
+    y = np.cos(2 * np.pi * x)
+    got, k = oracle.supsmu_spg(x, y, w, iper=2)
+    assert k == 0
+    m3 = _cos_sum(3, n) / 7
+    np.testing.assert_allclose(got, y * m3, rtol=0, atol=1e-13)
