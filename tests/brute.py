@@ -105,11 +105,14 @@ def _interp(s, tw, mid, woof, spans):
     return (1 - g) * mid + g * woof
 
 
-def supsmu(x, y, w, alpha=9.0, iper=2, spans=SPANS):
-    """Listing 1 on top of brute-force running lines (CV by explicit LOO)."""
+def supsmu(x, y, w, alpha=9.0, iper=2, spans=SPANS, return_span=False):
+    """Listing 1 on top of brute-force running lines (CV by explicit LOO).
+    With return_span the smoothed span column (before its clamp) comes back
+    as well, so that a test can show which clamp its input reaches."""
     n = x.size
     if x[-1] <= x[0]:
-        return np.full(n, np.sum(w * y) / np.sum(w))
+        out = np.full(n, np.sum(w * y) / np.sum(w))
+        return (out, None) if return_span else out
     vs = vsmlsq_of(x)
     smo, res, raw = [], [], []
     for s in spans:
@@ -124,7 +127,7 @@ def supsmu(x, y, w, alpha=9.0, iper=2, spans=SPANS):
     v = np.array([_interp(sm_span[j], smo[0][j], smo[1][j], smo[2][j], spans)
                   for j in range(n)])
     out, _ = runline(x, v, w, spans[0], -iper, vs)
-    return out
+    return (out, sm_span) if return_span else out
 
 
 def supsmu_sp(x, y, w, alpha=9.0, iper=2, spans=SPANS):

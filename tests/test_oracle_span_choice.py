@@ -10,7 +10,8 @@ columns are one column times a constant per span, and so the span choice is
 the same at every centre.  The expected outputs below are written from those
 sums and from hand-evaluated span arithmetic; nothing re-walks the Listing.
 A wrong argmin, a woofer/tweeter swap, a wrong bass exponent or target, or an
-interpolation toward the wrong fit changes the output at every point.
+interpolation toward the wrong fit changes the output at every point; so does,
+on an exact three-way tie, taking the last minimum or a bass step at equality.
 """
 import numpy as np
 import pytest
@@ -31,6 +32,7 @@ def test_half_widths_of_the_cases():
     # trunc(0.5 span n + 0.5), as the cases below assume
     assert [oracle.half_width(100, s) for s in (0.05, 0.2, 0.5)] == [3, 10, 25]
     assert [oracle.half_width(110, s) for s in (0.05, 0.2, 0.5)] == [3, 11, 28]
+    assert [oracle.half_width(96, s) for s in (0.05, 0.2, 0.5)] == [2, 10, 24]
 
 
 @pytest.mark.parametrize("alpha", [0.0, 9.0])
@@ -93,6 +95,25 @@ def test_woofer_wins_on_an_alternating_sequence(alpha):
     expected = -sgn / 399.0
     got = oracle.supsmu(x, sgn, w, iper=2, alpha=alpha)
     np.testing.assert_allclose(got, expected, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("alpha", [0.0, 9.0, 10.0])
+def test_three_way_tie_keeps_the_tweeter(alpha):
+    # n = 96, half widths 2, 10, 24, all even: every leave-one-out mean of
+    # (-1)^j is 0, so all three residuals are exactly 1 at every centre.  The
+    # span choice takes the first strict minimum (the tweeter), and since
+    # that minimum is not below the woofer's residual no bass step applies,
+    # for any alpha.  The tie is exact in binary64 as well: the residual is
+    # |y_j - fit_j| / (1 - leverage_j) with fit_j = (-1)^j / m and leverage
+    # 1/m, so numerator and denominator are the same rounded 1 - 1/m.
+    # Smooth: tweeter mean (-1)^j / 5, then the final tweeter smooth, 1/25.
+    # Taking the last minimum, or a bass step at equality, gives the woofer
+    # instead: (-1)^j / 245.
+    n = 96
+    x, w = _grid(n)
+    sgn = (-1.0) ** np.arange(n)
+    got = oracle.supsmu(x, sgn, w, iper=2, alpha=alpha)
+    np.testing.assert_allclose(got, sgn / 25.0, rtol=0, atol=1e-15)
 
 
 def test_sp_reading_on_the_same_cases():

@@ -135,6 +135,23 @@ def test_clamp_of_smoothed_span_matters():
                                rtol=1e-9, atol=1e-10)
 
 
+def test_both_clamps_of_smoothed_span_matter():
+    # with clamped (one-sided at the ends) windows the same kind of input
+    # drives the smoothed span below the tweeter's 0.05 at one end and above
+    # the woofer's 0.5 elsewhere, so each clamp bound changes the output
+    # (40 points, so that the tweeter's and the midrange's half widths differ
+    # and the interpolation below the tweeter's span is not flat)
+    g = np.random.default_rng(138)
+    x = np.sort(np.concatenate([g.uniform(0.0, 0.08, 16), g.uniform(0.5, 0.55, 16),
+                                g.uniform(0, 1, 8)]))
+    y = np.where(x < 0.3, 0.0, 1.0) + g.normal(0, 0.05, 40) + 3 * np.sin(6 * x)
+    w = g.uniform(0.5, 3, 40)
+    assert oracle.half_width(40, 0.05) < oracle.half_width(40, 0.2)
+    ref, span = brute.supsmu(x, y, w, iper=1, return_span=True)
+    assert span.min() < 0.03 and span.max() > 0.52
+    np.testing.assert_allclose(oracle.supsmu(x, y, w, iper=1), ref, rtol=1e-9, atol=1e-10)
+
+
 @pytest.mark.parametrize("iper", [1, 2])
 @pytest.mark.parametrize("n", [8, 17, 40])
 def test_spg_matches_brute_force(n, iper):
