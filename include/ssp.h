@@ -118,7 +118,7 @@ void ssp_default_params(ssp_params *p);
  *   t, y, dy        host f64 [sum n]; t and y finite, dy finite and > 0.
  *   n_per_object    host i64 [n_objects]; every n >= 4 (Listing 1 reads
  *                   x[3(n/4)-1]) and n <= 65535.
- *   freq_grid       host f64 [n_freq]; finite and > 0.
+ *   freq_grid       host f64 [n_freq]; finite and > 0; 1 <= n_freq <= 2^31 - 1.
  *   params          NULL selects ssp_default_params.
  *   out_power       host [n_objects][n_freq], double (FP64) or float (FP32C).
  *   out_best_period host f64 [n_objects].

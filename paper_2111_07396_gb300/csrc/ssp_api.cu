@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -187,7 +188,8 @@ int check_shape(const int64_t *n_per_object, int64_t n_objects, int64_t n_freq, 
     if (n_objects < 1) return fail(SSP_ERR_ARG, "n_objects must be >= 1");
     if (n_objects > (int64_t)1 << 30) return fail(SSP_ERR_ARG, "n_objects too large");
     if (n_freq < 1) return fail(SSP_ERR_ARG, "n_freq must be >= 1");
-    if (n_freq > (int64_t)1 << 31) return fail(SSP_ERR_ARG, "n_freq too large");
+    // work items carry frequency bounds as int
+    if (n_freq > (int64_t)INT32_MAX) return fail(SSP_ERR_ARG, "n_freq too large (at most 2^31 - 1)");
     if (v != SSP_SS && v != SSP_SP && v != SSP_SPG)
         return fail(SSP_ERR_ARG, "unknown variant %d", (int)v);
     if (!n_per_object) return fail(SSP_ERR_ARG, "n_per_object is NULL");
@@ -989,7 +991,7 @@ int check_one_object(const ssp_params &p, const double *t, const double *y, cons
 int check_freq(const double *freq_grid, int64_t n_freq)
 {
     if (!freq_grid) return ::fail(SSP_ERR_ARG, "NULL frequency grid");
-    if (n_freq < 1 || n_freq > (int64_t)1 << 31) return ::fail(SSP_ERR_ARG, "n_freq out of range");
+    if (n_freq < 1 || n_freq > (int64_t)INT32_MAX) return ::fail(SSP_ERR_ARG, "n_freq out of range");
     for (int64_t q = 0; q < n_freq; ++q)
         if (!std::isfinite(freq_grid[q]) || !(freq_grid[q] > 0.0))
             return ::fail(SSP_ERR_ARG, "freq_grid[%lld] must be finite and > 0", (long long)q);

@@ -80,6 +80,19 @@ def test_invalid_arguments_rejected_before_cuda(kw, status):
     assert ei.value.status == status
 
 
+def test_frequency_count_limit():
+    # work items hold frequency bounds as int: 2^31 frequencies are refused
+    # by the shape check, before any array is read
+    p = ssp.ssp_default_params()
+    npo = (ctypes.c_int64 * 1)(8)
+    rc = ssp.lib().ssp_periodogram(None, None, None, npo, 1, None, 2 ** 31, ssp.SSP_SS,
+                                   ctypes.byref(p), None, None)
+    assert rc == ssp.SSP_ERR_ARG and "n_freq too large" in ssp.ssp_last_error()
+    rc = ssp.lib().ssp_periodogram(None, None, None, npo, 1, None, 2 ** 31 - 1, ssp.SSP_SS,
+                                   ctypes.byref(p), None, None)
+    assert rc == ssp.SSP_ERR_ARG and "NULL array" in ssp.ssp_last_error()
+
+
 @pytest.mark.parametrize("field,value", [("periodic", 2), ("periodic", -1), ("span", -0.1),
                                          ("span", 1.5), ("span", float("nan"))])
 def test_mode_fields_checked(field, value):
