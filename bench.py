@@ -132,7 +132,7 @@ def parse():
                     help="--matrix: keep the first K objects of each configuration")
     ap.add_argument("--subset-freq", type=int, default=0,
                     help="--matrix: keep F frequencies, evenly spaced over the grid")
-    ap.add_argument("--no-oracle", action="store_true", help="--matrix: skip the oracle sample")
+    ap.add_argument("--no-oracle", action="store_true", help="--matrix, --serve: skip the oracle sample")
     ap.add_argument("--matrix-variants", default="ss,sp", help="--matrix: comma list of ss, sp, spg")
     return ap.parse_args()
 
@@ -474,6 +474,25 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------
+def serve_oracle_check(objs, served, variants, freq, k=12):
+    """The FP64 oracle at k sampled frequencies of each request in `served`
+    ({request index: served power}), the served best frequency among them,
+    against the served powers, under the parity gate."""
+    import oracle
+    from tests.parity import TOL, gate_error, oracle_powers, sample_freqs
+    codes = (oracle.SS, oracle.SP)
+    worst, n_f = 0.0, 0
+    t0 = time.perf_counter()
+    for i, p in sorted(served.items()):
+        t, y, dy = objs[i]
+        qs = sample_freqs(freq.size, k, seed=i, include=[int(np.argmax(p))])
+        ref = oracle_powers(t, y, dy, freq[qs], codes[variants[i]])
+        worst = max(worst, gate_error(p[qs], ref))
+        n_f += qs.size
+    return {"requests": len(served), "frequencies": n_f, "max_gate_err": worst,
+            "tolerance": TOL["fp32c"], "oracle_s": time.perf_counter() - t0}
+
+
 def run_serve(args):
     """Serving workload through ssp_server_*: a submitter thread replays the
     Poisson arrival times, a collector thread takes each finished ticket and
@@ -512,6 +531,7 @@ def run_serve(args):
     best = np.zeros(N)
     t0 = time.perf_counter() + 0.1
     errors = []
+    served = {}                                     # every 100th request's powers
 
     def submitter():
         for k in range(N):
@@ -536,6 +556,8 @@ def run_serve(args):
             lat[k] = (time.perf_counter() - (t0 + arrivals[k])) * 1e3
             lat_srv[k] = r[2]
             best[k] = r[1]
+            if k % 100 == 0:
+                served[k] = r[0].astype(np.float64)
             got += 1
 
     ts = threading.Thread(target=submitter)
@@ -548,6 +570,8 @@ def run_serve(args):
     end = float(np.nanmax(arrivals + lat / 1e3))    # first arrival to last result, s
     srv.close()
     ptf = float(np.sum(cat.n_per_object)) * nf
+    # after the timed region: 1 % of the requests against the oracle
+    check = None if args.no_oracle else serve_oracle_check(objs, served, variants, cat.freq)
     q = lambda a, p: float(np.nanpercentile(a, p))
     line = {"metric": "served objects/s (Poisson arrivals, single-object requests)",
             "value": N / end, "unit": "objects/s", "higher_is_better": True,
@@ -557,6 +581,7 @@ def run_serve(args):
                            "max": float(np.nanmax(lat))},
             "server_latency_ms": {"p50": q(lat_srv, 50), "p99": q(lat_srv, 99)},
             "dtype": "f32", "data": "synthetic", "clocks": clk.summary(), "autotune": tune,
+            "oracle_check_fp32c": check,
             "config": {"workload": f"Poisson arrivals {args.rate:g}/s for {args.duration:g} s, "
                                    f"n ~ logU(30, 3000), {nf} freqs in [0.05, 15), "
                                    "variant per request Bernoulli(0.5), FP32C",
