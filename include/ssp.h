@@ -363,10 +363,13 @@ int ssp_search_refine(const double *t, const double *y, const double *dy,
  *                    is left allocated or enqueued;
  *   SSP_FAULT_STALL  the serving worker treats its next `count` batches as
  *                    not finished within stall_ms: their requests end with
- *                    SSP_ERR_TIMEOUT (the batches themselves complete).
+ *                    SSP_ERR_TIMEOUT (the batches themselves complete);
+ *   SSP_FAULT_UPLOAD the serving worker's next `count` uploads of a request
+ *                    into the device arena fail as a CUDA error would: those
+ *                    requests end with SSP_ERR_CUDA and are never batched.
  * count 0 clears the kind.  Errors: SSP_ERR_ARG (unknown kind, count < 0).
  */
-enum { SSP_FAULT_ALLOC = 1, SSP_FAULT_STALL = 2 };
+enum { SSP_FAULT_ALLOC = 1, SSP_FAULT_STALL = 2, SSP_FAULT_UPLOAD = 3 };
 int ssp_test_fault(int kind, int count);
 
 /* Static text for a status code. */

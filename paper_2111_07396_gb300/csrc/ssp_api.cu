@@ -109,7 +109,7 @@ size_t pgram_frame_bytes(int p, int n, int variant, bool keep_perm, bool smo_out
 using namespace ssp;
 
 namespace ssp_internal {
-std::atomic<int> g_fault_alloc{0}, g_fault_stall{0};
+std::atomic<int> g_fault_alloc{0}, g_fault_stall{0}, g_fault_upload{0};
 
 bool testing()
 {
@@ -136,6 +136,7 @@ cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s)
 }
 
 bool stall_injected() { return take_fault(g_fault_stall); }
+bool upload_fault_injected() { return take_fault(g_fault_upload); }
 }  // namespace ssp_internal
 
 namespace {
@@ -1233,6 +1234,7 @@ int ssp_test_fault(int kind, int count)
     if (count < 0) return fail(SSP_ERR_ARG, "count must be >= 0");
     if (kind == SSP_FAULT_ALLOC) ssp_internal::g_fault_alloc.store(count);
     else if (kind == SSP_FAULT_STALL) ssp_internal::g_fault_stall.store(count);
+    else if (kind == SSP_FAULT_UPLOAD) ssp_internal::g_fault_upload.store(count);
     else return fail(SSP_ERR_ARG, "unknown fault kind %d", kind);
     return SSP_OK;
 }

@@ -32,6 +32,9 @@ cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s);
 // serving: true when the next batch is to be treated as stalled
 // (ssp_test_fault, SSP_FAULT_STALL)
 bool stall_injected();
+// serving: true when the next upload of a request is to fail
+// (ssp_test_fault, SSP_FAULT_UPLOAD)
+bool upload_fault_injected();
 
 // device bytes that run() takes from the stream-ordered pool for this batch
 // (workspace, slabs), or a negative status

@@ -169,6 +169,16 @@ struct ssp_server {
 
 namespace {
 
+// Drops the finished requests at the start of a ring's live list: their
+// space is free.
+void pop_released(Ring &rg)
+{
+    while (!rg.live.empty() && rg.live.front()->released) {
+        rg.live.pop_front();
+        rg.tail = rg.live.empty() ? rg.head : rg.live.front()->pos;
+    }
+}
+
 // Admits waiting requests, oldest first across variants, while their ring has
 // room; uploads each into its ring.  Called by the launcher with the lock
 // held; releases it around the copies.
@@ -191,7 +201,10 @@ void admit(ssp_server *S, std::unique_lock<std::mutex> &lk)
         rg.live.push_back(r);
         lk.unlock();
         const size_t at = (size_t)(p % rg.cap), bytes = 8 * (size_t)r->n;
-        cudaError_t e = cudaMemcpyAsync(rg.t + at, r->t.data(), bytes, cudaMemcpyHostToDevice, S->upload);
+        cudaError_t e = ssp_internal::upload_fault_injected()
+                            ? cudaErrorInvalidValue
+                            : cudaMemcpyAsync(rg.t + at, r->t.data(), bytes, cudaMemcpyHostToDevice,
+                                              S->upload);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(rg.y + at, r->y.data(), bytes, cudaMemcpyHostToDevice, S->upload);
         if (e == cudaSuccess)
@@ -202,14 +215,15 @@ void admit(ssp_server *S, std::unique_lock<std::mutex> &lk)
         std::vector<double>().swap(r->dy);
         lk.lock();
         if (e != cudaSuccess) {
-            // answered at once and never batched; its ring space is reused
-            // once the requests before it are done
+            // answered at once and never batched (batches stop at it); its
+            // ring space is reused once the requests before it are done
             cudaGetLastError();
             r->status = SSP_ERR_CUDA;
             r->err = std::string("upload: ") + cudaGetErrorString(e);
             r->launched = r->released = true;
             r->t_done = Clock::now();
             if (S->live.count(r->ticket)) S->finished.push_back(r->ticket);
+            pop_released(rg);
             S->cv_done.notify_all();
         }
     }
@@ -315,8 +329,10 @@ void launcher_loop(ssp_server *S, std::unique_lock<std::mutex> &lk)
         int64_t end = -1;
         for (size_t i = (size_t)first; i < rg.live.size(); ++i) {
             const auto &r = rg.live[i];
-            // contiguous in the ring, and within the cap (at least one request)
-            if (end >= 0 && r->pos != end) break;
+            // not yet launched (a failed upload is answered and never
+            // batched), contiguous in the ring, and within the cap (at least
+            // one request)
+            if (r->launched || (end >= 0 && r->pos != end)) break;
             const double add = (double)r->n * (double)S->n_freq;
             if (!sl.reqs.empty() && ptf + add > S->cfg.max_batch_ptf) break;
             ptf += add;
@@ -372,11 +388,7 @@ void answer(ssp_server *S, Slot &sl, int status, const std::string &err)
 void release_slot(ssp_server *S, Slot &sl)
 {
     for (const auto &r : sl.reqs) r->released = true;
-    Ring &rg = S->ring[sl.variant];
-    while (!rg.live.empty() && rg.live.front()->released) {
-        rg.live.pop_front();
-        rg.tail = rg.live.empty() ? rg.head : rg.live.front()->pos;
-    }
+    pop_released(S->ring[sl.variant]);
     sl.reqs.clear();
     sl.busy = false;
     sl.enqueued = false;

@@ -20,7 +20,7 @@ SSP_FP64, SSP_FP32C = 0, 1
 SSP_OK, SSP_ERR_ARG, SSP_ERR_NOMEM, SSP_ERR_CUDA, SSP_ERR_TIMEOUT, SSP_ERR_UNSUPPORTED = (
     0, -1, -2, -3, -4, -5)
 SSP_ERR_BUSY, SSP_PENDING = -6, 1
-SSP_FAULT_ALLOC, SSP_FAULT_STALL = 1, 2
+SSP_FAULT_ALLOC, SSP_FAULT_STALL, SSP_FAULT_UPLOAD = 1, 2, 3
 VARIANTS = {"ss": SSP_SS, "sp": SSP_SP, "spg": SSP_SPG, SSP_SS: SSP_SS, SSP_SP: SSP_SP,
             SSP_SPG: SSP_SPG}
 PRECISIONS = {"fp64": SSP_FP64, "fp32c": SSP_FP32C, SSP_FP64: SSP_FP64, SSP_FP32C: SSP_FP32C}
@@ -334,8 +334,9 @@ class Plan:
 
 def ssp_test_fault(kind, count=1) -> None:
     """Testing only: make the library's next `count` device allocations fail
-    (SSP_FAULT_ALLOC) or its server's next `count` batches count as stalled
-    (SSP_FAULT_STALL).  Needs SSP_TESTING=1 in the environment."""
+    (SSP_FAULT_ALLOC), its server's next `count` batches count as stalled
+    (SSP_FAULT_STALL) or its server's next `count` request uploads fail
+    (SSP_FAULT_UPLOAD).  Needs SSP_TESTING=1 in the environment."""
     _check(lib().ssp_test_fault(int(kind), int(count)))
 
 

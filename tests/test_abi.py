@@ -170,3 +170,5 @@ def test_fault_injection_is_off_unless_testing(monkeypatch):
     ssp.ssp_test_fault(ssp.SSP_FAULT_ALLOC, 2)
     ssp.ssp_test_fault(ssp.SSP_FAULT_ALLOC, 0)
     ssp.ssp_test_fault(ssp.SSP_FAULT_STALL, 0)
+    ssp.ssp_test_fault(ssp.SSP_FAULT_UPLOAD, 1)
+    ssp.ssp_test_fault(ssp.SSP_FAULT_UPLOAD, 0)

@@ -7,6 +7,8 @@ injection is test-only: ssp_test_fault with SSP_TESTING=1).
   requests with SSP_ERR_TIMEOUT while the server keeps serving; both a real
   expiry (a wait of microseconds) and an injected one are covered.
 - A served batch whose allocation fails ends its requests with SSP_ERR_NOMEM.
+- A served request whose upload fails ends with SSP_ERR_CUDA and never joins
+  a batch, even one formed later from requests on both sides of it.
 """
 import numpy as np
 import pytest
@@ -29,6 +31,7 @@ def testing(monkeypatch):
     yield
     ssp.ssp_test_fault(ssp.SSP_FAULT_ALLOC, 0)
     ssp.ssp_test_fault(ssp.SSP_FAULT_STALL, 0)
+    ssp.ssp_test_fault(ssp.SSP_FAULT_UPLOAD, 0)
 
 
 def _cat():
@@ -88,6 +91,34 @@ def test_server_injected_stall_times_out_then_serves(testing):
         assert ei.value.status == ssp.SSP_ERR_TIMEOUT
         pw, _, _ = srv.poll(srv.submit(*cat.obj(1)), wait_ms=60000)
         np.testing.assert_array_equal(pw, ref[0])
+
+
+def test_server_failed_upload_is_answered_and_never_batched(testing):
+    # With a one-second batching window, request B is admitted and waits for
+    # company; request A's upload then fails (injected) and C follows.  A is
+    # answered with SSP_ERR_CUDA at once and sits in the ring between B and
+    # C: the batches formed at the end of the window must leave it out.  B
+    # and C are collected first, so a batch that had taken A in would have
+    # overwritten its answer before A is polled.
+    import time
+    cat = _cat()
+    refs = [ssp.ssp_periodogram(*cat.obj(k), [cat.n_per_object[k]], cat.freq)[0][0]
+            for k in range(3)]
+    with ssp.Server(cat.freq, max_wait_ms=1000.0) as srv:
+        tb = srv.submit(*cat.obj(0))
+        time.sleep(0.2)                          # B admitted (uploaded), batch window open
+        ssp.ssp_test_fault(ssp.SSP_FAULT_UPLOAD, 1)
+        ta = srv.submit(*cat.obj(1))
+        tc = srv.submit(*cat.obj(2))
+        for tk, ref in ((tb, refs[0]), (tc, refs[2])):
+            pw, _, _ = srv.poll(tk, wait_ms=60000)
+            np.testing.assert_array_equal(pw, ref)
+        with pytest.raises(ssp.SSPError) as ei:
+            srv.poll(ta, wait_ms=60000)
+        assert ei.value.status == ssp.SSP_ERR_CUDA
+        # the ring space is reused: the server keeps serving
+        pw, _, _ = srv.poll(srv.submit(*cat.obj(1)), wait_ms=60000)
+        np.testing.assert_array_equal(pw, refs[1])
 
 
 def test_server_bounded_wait_expires_on_a_real_batch():
