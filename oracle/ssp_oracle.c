@@ -154,15 +154,22 @@ static double window_fit(int n, const double *x, const double *v, const double *
 {
     int lo = window_lo(n, ibw, periodic, j);
     int hi = lo + 2 * ibw;
-    double sw = 0.0, swx = 0.0, swv = 0.0;
+    /* The mean abscissa is taken about the window's first abscissa x0, so a
+     * window of equal abscissae has xm = x0 and a spread of exactly 0, as
+     * the definition gives.  (sum(w x) / sum(w) over equal x can round off
+     * the common value; the spread is then rounding noise, which the slope
+     * test would take for a real spread where vsmlsq is 0.) */
+    double x0;
+    slot_point(n, lo, x, &x0);
+    double sw = 0.0, swd = 0.0, swv = 0.0;
     for (int e = lo; e <= hi; e++) {
         double xe;
         int p = slot_point(n, e, x, &xe);
         sw += w[p];
-        swx += w[p] * xe;
+        swd += w[p] * (xe - x0);
         swv += w[p] * v[p];
     }
-    double xm = swx / sw, vm = swv / sw;
+    double xm = x0 + swd / sw, vm = swv / sw;
     double sxx = 0.0, sxv = 0.0;
     for (int e = lo; e <= hi; e++) {
         double xe;

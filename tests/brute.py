@@ -33,9 +33,11 @@ def window(n: int, ibw: int, periodic: bool, j: int, x: np.ndarray):
 
 def wls_line(xs, vs, ws, x0, vsmlsq=0.0):
     """Weighted least-squares line through (xs, vs) evaluated at x0; a plain
-    weighted mean when the weighted spread of xs does not exceed vsmlsq."""
+    weighted mean when the weighted spread of xs does not exceed vsmlsq.  The
+    spread of equal abscissae is 0 exactly (a computed mean of equal values
+    may round off them and leave a spread of rounding noise)."""
     xm = np.sum(ws * xs) / np.sum(ws)
-    sxx = np.sum(ws * (xs - xm) ** 2)
+    sxx = 0.0 if np.all(xs == xs[0]) else np.sum(ws * (xs - xm) ** 2)
     if not sxx > vsmlsq:
         return np.sum(ws * vs) / np.sum(ws), False
     A = np.stack([np.ones_like(xs), xs], axis=1) * np.sqrt(ws)[:, None]

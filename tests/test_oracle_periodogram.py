@@ -53,6 +53,12 @@ def test_power_of_constant_signal_is_zero_and_chi0_zero_guard():
     y = np.full(20, 4.0)
     dy = np.full(20, 0.1)
     assert oracle.power_one(t, y, dy, 0.33, oracle.SS) == 0.0
+    # every power ties at 0: the best period is that of the first frequency
+    # (the first index of the largest power)
+    freq = np.array([0.33, 0.5, 0.71])
+    for variant in (oracle.SS, oracle.SP, oracle.SPG):
+        pw, best = oracle.periodogram(t, y, dy, [20], freq, variant)
+        assert np.all(pw == 0.0) and best[0] == 1.0 / 0.33
 
 
 def _best_ok(best, P, tol=0.01):
@@ -115,6 +121,34 @@ def test_periodogram_row_equals_single_power():
             t, y, dy = c.obj(o)
             for q in (0, 17, 49):
                 assert p[o, q] == oracle.power_one(t, y, dy, c.freq[q], variant)
+
+
+def test_best_period_of_every_object_is_its_own():
+    # each object's best period is 1 / (the first frequency of its own
+    # largest power); objects with different periods pick different ones
+    g = np.random.default_rng(8)
+    objs = []
+    for period in (0.7, 2.3, 5.1):
+        t = np.sort(g.uniform(0, 60, 80))
+        objs.append((t, np.sin(2 * np.pi * t / period) + g.normal(0, 0.1, 80), np.full(80, 0.1)))
+    freq = synth.uniform_grid(0.1, 2.0, 400)
+    cat = synth.concat([synth.single_object(*o, freq) for o in objs])
+    for variant in (oracle.SS, oracle.SP):
+        p, best = oracle.periodogram(cat.t, cat.y, cat.dy, cat.n_per_object, freq, variant)
+        expect = 1.0 / freq[np.argmax(p, axis=1)]
+        np.testing.assert_array_equal(best, expect)
+        assert np.unique(np.round(best, 1)).size == 3
+        np.testing.assert_allclose(best, [0.7, 2.3, 5.1], rtol=0.02)
+
+
+def test_one_frequency_and_the_smallest_object():
+    # a grid of one frequency, and an object of 4 points (the least the
+    # method reads: Listing 1 takes x[3(n/4) - 1])
+    t, y, dy = np.array([0.0, 0.31, 1.7, 2.2]), np.array([1.0, 2.0, 0.5, 1.5]), np.full(4, 0.1)
+    for variant in (oracle.SS, oracle.SP, oracle.SPG):
+        p, best = oracle.periodogram(t, y, dy, [4], [0.37], variant)
+        assert p.shape == (1, 1) and best[0] == 1.0 / 0.37
+        assert p[0, 0] == oracle.power_one(t, y, dy, 0.37, variant)
 
 
 def test_rejects_short_objects():

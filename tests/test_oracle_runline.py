@@ -22,6 +22,8 @@ def _data(n, seed, distinct=True):
 @pytest.mark.parametrize("n,span,expect", [
     (100, 0.05, 3), (100, 0.2, 10), (100, 0.5, 25), (3000, 0.05, 75), (3000, 0.2, 300),
     (3000, 0.5, 750), (10, 0.05, 2), (4, 0.5, 1), (5, 0.05, 2), (30, 0.05, 2), (41, 0.2, 4),
+    # fixed spans above 0.5 reach the cap: 2h + 1 <= n
+    (7, 1.0, 3), (21, 1.0, 10), (8, 1.0, 3), (9, 0.9, 4),
 ])
 def test_half_width_table(n, span, expect):
     # floor(0.5*span*n + 0.5), at least 2, at most (n-1)/2
@@ -110,6 +112,42 @@ def test_tie_average_equals_weighted_mean_of_fits():
     np.testing.assert_allclose(smo, ref, rtol=1e-12, atol=1e-12)
     run = np.flatnonzero(x == 0.25)
     assert run.size >= 3 and np.ptp(smo[run]) == 0.0
+
+
+@pytest.mark.parametrize("iper", [1, 2])
+def test_window_of_equal_abscissae_has_no_slope(iper):
+    # Seven of ten abscissae equal and vsmlsq = 0 (the middle half of the
+    # points tie, so Listing 1's scale is 0).  A window holding only the
+    # tied points has spread 0, which is not above vsmlsq: its line is the
+    # weighted mean, and the cross-validated residual is the distance to the
+    # weighted mean of the window's other points, with no leverage-1
+    # fallback (the residuals are per point, before tie averaging).  Centres 3, 4 and 5 have such windows at half width 2.
+    x = np.r_[0.05, np.full(7, 0.3), 0.6, 0.7]   # scale = x[5] - x[1] = 0
+    g = np.random.default_rng(31)
+    v = g.normal(0, 1, 10)
+    w = g.uniform(0.5, 2, 10)
+    assert oracle.vsmlsq(x) == 0.0
+    _, cv = oracle.runline(x, v, w, 0.05, iper, 0.0)
+    for j in (3, 4, 5):
+        win = np.arange(j - 2, j + 3)
+        assert np.all(x[win] == 0.3)
+        others = win[win != j]
+        loo = np.sum(w[others] * v[others]) / np.sum(w[others])
+        np.testing.assert_allclose(cv[j], abs(v[j] - loo), rtol=1e-12)
+
+
+@pytest.mark.parametrize("run", [2, 3])
+def test_tie_average_of_a_run_at_the_end(run):
+    # a run of equal abscissae that ends at the last point is averaged too
+    g = np.random.default_rng(4 + run)
+    x = np.sort(np.concatenate([g.uniform(0, 0.8, 9), np.full(run, 0.9)]))
+    v = g.normal(0, 1, x.size)
+    w = g.uniform(0.5, 2, x.size)
+    smo = oracle.tie_average(x, w, v)
+    np.testing.assert_allclose(smo, brute.tie_avg(x, w, v), rtol=1e-14, atol=1e-15)
+    tail = smo[-run:]
+    assert np.ptp(tail) == 0.0
+    np.testing.assert_allclose(tail[0], np.sum(w[-run:] * v[-run:]) / np.sum(w[-run:]), rtol=1e-14)
 
 
 def test_cv_fallback_for_exact_leverage_one_at_a_clamped_end():

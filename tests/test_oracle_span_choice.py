@@ -33,6 +33,7 @@ def test_half_widths_of_the_cases():
     assert [oracle.half_width(100, s) for s in (0.05, 0.2, 0.5)] == [3, 10, 25]
     assert [oracle.half_width(110, s) for s in (0.05, 0.2, 0.5)] == [3, 11, 28]
     assert [oracle.half_width(96, s) for s in (0.05, 0.2, 0.5)] == [2, 10, 24]
+    assert [oracle.half_width(28, s) for s in (0.05, 0.2, 0.5)] == [2, 3, 7]
 
 
 @pytest.mark.parametrize("alpha", [0.0, 9.0])
@@ -131,7 +132,8 @@ def test_sp_reading_on_the_same_cases():
     np.testing.assert_allclose(got, sgn / 57.0, rtol=0, atol=1e-15)
 
 
-@pytest.mark.parametrize("n,span,fit", [(100, 1, 1.0 / 21.0), (110, 2, 1.0 / 57.0)])
+@pytest.mark.parametrize("n,span,fit", [(100, 1, 1.0 / 21.0), (110, 2, 1.0 / 57.0),
+                                        (28, 2, -1.0 / 15.0)])
 def test_spg_reading_on_alternating_sequences(n, span, fit):
     # The SPG reading (one span per frequency, least summed squared
     # generalized-validation residual, reading 15): on y = (-1)^j every point
@@ -139,6 +141,9 @@ def test_spg_reading_on_alternating_sequences(n, span, fit):
     # means fit_h = +-1/(2h+1) of the cases above: n = 100 gives 1.6, 20/19
     # and 52/49 (the midrange wins), n = 110 gives 1.6, 8/7 and 56/55 (the
     # woofer wins).  The smooth is that span's fit, (-1)^j / 21 or / 57.
+    # n = 28 (half widths 2, 3, 7) gives 4/3, 1.6 and 16/13: the woofer wins
+    # only through the denominator, since with m one larger in it (6 and 16)
+    # the tweeter's 1.2 would beat the woofer's 1.22.  Its fit is -(-1)^j / 15.
     x, w = _grid(n)
     sgn = (-1.0) ** np.arange(n)
     got, k = oracle.supsmu_spg(x, sgn, w, iper=2)

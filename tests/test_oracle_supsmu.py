@@ -68,6 +68,35 @@ def test_affine_equivariance(fn):
     np.testing.assert_allclose(f(x, 2.5 * y + 40.0, w), 2.5 * base + 40.0, rtol=1e-12, atol=1e-10)
 
 
+def test_one_distinct_abscissa_is_not_degenerate():
+    # Listing 1 falls back to the weighted mean only when every abscissa is
+    # equal (x[n-1] <= x[0]); with all but the last tied the smoother runs
+    x = np.r_[np.full(9, 0.3), 0.7]
+    g = np.random.default_rng(12)
+    y = g.normal(0, 1, 10)
+    w = g.uniform(0.5, 2, 10)
+    for iper in (1, 2):
+        got = oracle.supsmu(x, y, w, iper=iper)
+        np.testing.assert_allclose(got, brute.supsmu(x, y, w, iper=iper), rtol=1e-9, atol=1e-10)
+        assert np.ptp(got) > 1e-3
+        np.testing.assert_allclose(oracle.supsmu_sp(x, y, w, iper=iper),
+                                   brute.supsmu_sp(x, y, w, iper=iper), rtol=1e-10, atol=1e-11)
+
+
+@pytest.mark.parametrize("fn", ["supsmu", "supsmu_sp"])
+def test_periodic_mode_needs_abscissae_in_the_unit_interval(fn):
+    # Listing 1 keeps periodic windows (iper = 2) only for 0 <= x[0] and
+    # x[n-1] <= 1; outside, it smooths with clamped windows (jper = 1)
+    f, bf = getattr(oracle, fn), getattr(brute, fn)
+    x, y, w = _lc(17, 21)
+    for xs in (np.r_[x[:-1], 1.2], np.r_[-0.1, x[1:]]):
+        np.testing.assert_allclose(f(xs, y, w, iper=2), bf(xs, y, w, iper=1), rtol=1e-9, atol=1e-10)
+    xs = np.r_[x[:-1], 1.0]                       # the closed end stays periodic
+    periodic = bf(xs, y, w, iper=2)
+    np.testing.assert_allclose(f(xs, y, w, iper=2), periodic, rtol=1e-9, atol=1e-10)
+    assert np.max(np.abs(periodic - bf(xs, y, w, iper=1))) > 1e-3
+
+
 @pytest.mark.parametrize("fn", ["supsmu", "supsmu_sp"])
 def test_periodic_rotation_invariance(fn):
     # rotating the phase circle permutes the points but keeps every window's
