@@ -64,8 +64,9 @@ typedef enum {
  *                   relative; scaled down for larger n, off above 2,048
  *                   points).  Flags the frequency for the binary64 recompute.
  *   SSP_NEAR_SS_ABS the same margin's absolute part, in FP32 units of the
- *                   object's largest centred magnitude (default 16; off
- *                   above 2,048 points).
+ *                   object's largest centred magnitude (default 8, scaled
+ *                   down for larger n like the relative part; off above
+ *                   2,048 points).
  *   SSP_NEAR_SP     SP near-tie margin in FP32 units of the magnitude scale
  *                   (default 32).
  *   SSP_SENS_TAU    SP: power budget per point; a near-tie whose other choice
