@@ -38,7 +38,8 @@
  *
  * Parity status: supsmu_sp and supsmu_spg have no value printed in the paper
  * to pin them to; they are pinned only against brute force of their own
- * readings ("parity unpinned" against the paper).
+ * readings and closed-form cases of their span choice ("parity unpinned"
+ * against the paper).
  */
 #include <math.h>
 #include <pthread.h>
