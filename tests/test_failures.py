@@ -94,7 +94,7 @@ def test_server_injected_stall_times_out_then_serves(testing):
 
 
 def test_server_failed_upload_is_answered_and_never_batched(testing):
-    # With a one-second batching window, request B is admitted and waits for
+    # With a two-second batching window, request B is admitted and waits for
     # company; request A's upload then fails (injected) and C follows.  A is
     # answered with SSP_ERR_CUDA at once and sits in the ring between B and
     # C: the batches formed at the end of the window must leave it out.  B
@@ -104,9 +104,9 @@ def test_server_failed_upload_is_answered_and_never_batched(testing):
     cat = _cat()
     refs = [ssp.ssp_periodogram(*cat.obj(k), [cat.n_per_object[k]], cat.freq)[0][0]
             for k in range(3)]
-    with ssp.Server(cat.freq, max_wait_ms=1000.0) as srv:
+    with ssp.Server(cat.freq, max_wait_ms=2000.0) as srv:
         tb = srv.submit(*cat.obj(0))
-        time.sleep(0.2)                          # B admitted (uploaded), batch window open
+        time.sleep(0.5)                          # B admitted (uploaded), batch window open
         ssp.ssp_test_fault(ssp.SSP_FAULT_UPLOAD, 1)
         ta = srv.submit(*cat.obj(1))
         tc = srv.submit(*cat.obj(2))
