@@ -35,6 +35,18 @@ def test_fold_matches_binary64_phase(seed):
         assert big.sum() > 0
 
 
+def test_fold_at_extreme_magnitudes():
+    # products from just above 2^-11 to near the top of binary64: at and
+    # beyond 2^53 the rounded product is an integer and the phase is 0
+    g = np.random.default_rng(17)
+    tt = np.concatenate([[1e15, 3.3e15, 2.0 ** 52 + 1, 2.0 ** 53, 2.0 ** 53 + 2, 1e16, 1e20, 1e300],
+                         10.0 ** g.uniform(8, 300, 400)])
+    for f in (1e-3, 0.37, 1.0, 3.3, 1e3):
+        keep = np.isfinite(tt * f)
+        got = ssp.ssp_fold_fixed(tt[keep], f)
+        assert [int(v) for v in got] == list(_expected(tt[keep], f)), f
+
+
 def test_fold_rounding_halfway_cases():
     # products that sit exactly halfway between two binary64 values
     tt = np.array([1.0 + 2.0 ** -52, 3.0 + 2.0 ** -51, 2.0 ** 40 + 1.0])
