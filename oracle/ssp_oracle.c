@@ -39,7 +39,8 @@
  * Parity status: supsmu_sp and supsmu_spg have no value printed in the paper
  * to pin them to; they are pinned only against brute force of their own
  * readings and closed-form cases of their span choice ("parity unpinned"
- * against the paper).
+ * against the paper).  supsmu_sp is also held to the paper's claim that SP
+ * finds periods about as often as SS (Sec. 5.6), on synthetic objects.
  */
 #include <math.h>
 #include <pthread.h>
