@@ -93,6 +93,46 @@ def test_frequency_count_limit():
     assert rc == ssp.SSP_ERR_ARG and "NULL array" in ssp.ssp_last_error()
 
 
+def _status(params=None, n=8):
+    # the call's status: past the argument checks a call reaches CUDA, which
+    # fails without a GPU (SSP_ERR_CUDA) and runs with one (SSP_OK)
+    t, y, dy = np.arange(float(n)), np.ones(n), np.ones(n)
+    try:
+        ssp.ssp_periodogram(t, y, dy, [n], [0.3, 0.4], params=params)
+        return ssp.SSP_OK
+    except ssp.SSPError as e:
+        return e.status
+
+
+@pytest.mark.parametrize("field,ok,bad", [
+    ("alpha", [0.0, 10.0], [-1e-9, 10.000001]),
+    ("hbm_fraction", [1.0, 1e-6], [0.0, 1.0000001]),
+    ("span", [0.0, 1.0], [-1e-12, 1.0000001]),
+    ("spans", [(0.05, 0.2, 1.0), (1e-6, 0.2, 0.5)],
+     [(0.0, 0.2, 0.5), (0.2, 0.2, 0.5), (0.05, 0.5, 0.5), (0.05, 0.2, 1.0000001)]),
+])
+def test_parameter_limits(field, ok, bad):
+    # each documented range: its ends accepted, just beyond them refused
+    for values, accepted in ((ok, True), (bad, False)):
+        for v in values:
+            p = ssp.ssp_default_params()
+            if field == "spans":
+                for i in range(3):
+                    p.spans[i] = v[i]
+            else:
+                setattr(p, field, v)
+            status = _status(params=p)
+            assert (status != ssp.SSP_ERR_ARG) == accepted, (field, v, status)
+
+
+def test_object_size_limits():
+    # 4 <= n <= 65,535 points per object
+    assert _status(n=3) == ssp.SSP_ERR_ARG
+    assert _status(n=4) != ssp.SSP_ERR_ARG
+    assert _status(n=65535) != ssp.SSP_ERR_ARG
+    assert _status(n=65536) == ssp.SSP_ERR_ARG
+
+
 @pytest.mark.parametrize("field,value", [("periodic", 2), ("periodic", -1), ("span", -0.1),
                                          ("span", 1.5), ("span", float("nan"))])
 def test_mode_fields_checked(field, value):
@@ -121,6 +161,15 @@ def test_server_rejects_bad_grid_and_params_before_cuda():
     assert ssp.ssp_status_string(ssp.SSP_ERR_BUSY) == "too many requests in flight"
     assert ssp.ssp_status_string(ssp.SSP_PENDING) == "pending"
     assert ctypes.sizeof(ssp.ssp_server_config) == 48
+    # at most 16 batch slots: 17 is refused before any device work, 16 passes
+    # the checks (and then needs a device)
+    with pytest.raises(ssp.SSPError) as ei:
+        ssp.Server([0.3, 0.4], slots=17)
+    assert ei.value.status == ssp.SSP_ERR_ARG
+    try:
+        ssp.Server([0.3, 0.4], slots=16).close()
+    except ssp.SSPError as e:
+        assert e.status != ssp.SSP_ERR_ARG
     # calls on a NULL handle are argument errors, not crashes
     t = ctypes.c_int64()
     assert ssp.lib().ssp_server_next(None, 0, ctypes.byref(t)) == ssp.SSP_ERR_ARG
@@ -151,6 +200,27 @@ def test_search_refine_rejects_bad_arguments_before_cuda():
         with pytest.raises(ssp.SSPError) as ei:
             ssp.ssp_search_refine(**args)
         assert ei.value.status == ssp.SSP_ERR_ARG
+
+
+def test_search_refine_limits():
+    # n_peaks in 1..64, n_peaks * n_fine <= 2^22, at least 2 coarse
+    # frequencies: the ends accepted, just beyond them refused
+    t, y, dy = np.arange(8.0), np.ones(8), np.ones(8)
+    base = dict(t=t, y=y, dy=dy, n_per_object=[8], coarse_grid=[0.3, 0.4])
+
+    def status(**kw):
+        args = dict(base)
+        args.update(kw)
+        try:
+            ssp.ssp_search_refine(**args)
+            return ssp.SSP_OK
+        except ssp.SSPError as e:
+            return e.status
+
+    for kw in (dict(n_peaks=1, n_fine=1), dict(n_peaks=64, n_fine=1), dict(n_peaks=64, n_fine=1 << 16)):
+        assert status(**kw) != ssp.SSP_ERR_ARG, kw
+    for kw in (dict(n_peaks=64, n_fine=(1 << 16) + 1), dict(coarse_grid=[0.3], n_peaks=1, n_fine=1)):
+        assert status(**kw) == ssp.SSP_ERR_ARG, kw
 
 
 def test_fault_injection_is_off_unless_testing(monkeypatch):
