@@ -177,6 +177,30 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _expect(a, name, f64, count, out=False):
+    """Checks an array the library will read or write before the call: element
+    type (float64, or float32 for FP32C powers), exactly `count` elements, a
+    contiguous layout and, for outputs in host memory, writeable.  A buffer of
+    the wrong type or size would otherwise be read or written past its end.
+    Raw device addresses (ints) are taken as given."""
+    if isinstance(a, int):
+        return
+    if hasattr(a, "data_ptr"):
+        import torch
+        want = torch.float64 if f64 else torch.float32
+        ok = a.dtype == want and a.numel() == count and a.is_contiguous()
+        got = f"{a.dtype}, {a.numel()} elements"
+    else:
+        want = np.float64 if f64 else np.float32
+        ok = (isinstance(a, np.ndarray) and a.dtype == want and a.size == count
+              and a.flags.c_contiguous and (a.flags.writeable or not out))
+        got = f"{getattr(a, 'dtype', type(a).__name__)}, {getattr(a, 'size', '?')} elements"
+    if not ok:
+        kind = "float64" if f64 else "float32"
+        raise ValueError(f"{name} must be a contiguous{' writeable' if out else ''} {kind} array "
+                         f"of {count} elements (got {got})")
+
+
 def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data)
 
@@ -197,6 +221,11 @@ def ssp_periodogram(t, y, dy, n_per_object, freq_grid, variant="ss", precision="
         out_power = np.empty((n_obj, n_freq), dtype=dt)
     if out_best_period is None:
         out_best_period = np.empty(n_obj, dtype=np.float64)
+    n_pts = int(npo.sum())
+    for a, name in ((t_, "t"), (y_, "y"), (dy_, "dy")):
+        _expect(a, name, True, n_pts)
+    _expect(out_power, "out_power", p.precision == SSP_FP64, n_obj * n_freq, out=True)
+    _expect(out_best_period, "out_best_period", True, n_obj, out=True)
     rc = lib().ssp_periodogram(_host_ptr(t_), _host_ptr(y_), _host_ptr(dy_), _ptr(npo), n_obj,
                                _host_ptr(fq), n_freq, VARIANTS[variant], ctypes.byref(p),
                                _host_ptr(out_power), _host_ptr(out_best_period))
@@ -213,13 +242,14 @@ def ssp_periodogram_device(t, y, dy, n_per_object, freq_grid, out_power, out_bes
     raw cudaStream_t address; default: torch's current stream)."""
     p = params if params is not None else ssp_default_params(precision, alpha, spans)
     npo = np.ascontiguousarray(n_per_object, dtype=np.int64)
+    n_freq = int(freq_grid.numel()) if hasattr(freq_grid, "numel") else None
+    if n_freq is None:
+        raise ValueError("freq_grid must be a tensor (its length is needed)")
+    _expect_device(p, npo, n_freq, t, y, dy, freq_grid, out_power, out_best_period)
     if stream is None:
         import torch
         stream = torch.cuda.current_stream()
     s = stream if isinstance(stream, int) else stream.cuda_stream
-    n_freq = int(freq_grid.numel()) if hasattr(freq_grid, "numel") else None
-    if n_freq is None:
-        raise ValueError("freq_grid must be a tensor (its length is needed)")
     rc = lib().ssp_periodogram_device(_dev_ptr(t), _dev_ptr(y), _dev_ptr(dy), _ptr(npo),
                                       int(npo.size), _dev_ptr(freq_grid), n_freq,
                                       VARIANTS[variant], ctypes.byref(p), _dev_ptr(out_power),
@@ -235,6 +265,10 @@ def ssp_periodogram_device_noalloc(t, y, dy, n_per_object, freq_grid, out_power,
     the library's fixed device array (see include/ssp.h for its limits)."""
     p = params if params is not None else ssp_default_params(precision, alpha, spans)
     npo = np.ascontiguousarray(n_per_object, dtype=np.int64)
+    if not hasattr(freq_grid, "numel"):
+        raise ValueError("freq_grid must be a tensor (its length is needed)")
+    _expect_device(p, npo, int(freq_grid.numel()), t, y, dy, freq_grid, out_power,
+                   out_best_period)
     if stream is None:
         import torch
         stream = torch.cuda.current_stream()
@@ -304,6 +338,8 @@ class Plan:
     def ssp_plan_execute(self, t, y, dy, freq_grid, out_power, out_best_period, stream=None):
         """Device arrays (torch CUDA tensors or raw addresses); enqueued on
         `stream` (default: torch's current stream)."""
+        _expect_device(self._p, self._npo, self.n_freq, t, y, dy, freq_grid, out_power,
+                       out_best_period)
         if stream is None:
             import torch
             stream = torch.cuda.current_stream()
@@ -433,6 +469,16 @@ def _host_ptr(a):
     if hasattr(a, "data_ptr"):
         return ctypes.c_void_p(a.data_ptr())
     return _ptr(a)
+
+
+def _expect_device(p, npo, n_freq, t, y, dy, freq_grid, out_power, out_best_period):
+    # element types and counts of a device call's arrays (see _expect)
+    n_pts, n_obj = int(npo.sum()), int(npo.size)
+    for a, name in ((t, "t"), (y, "y"), (dy, "dy")):
+        _expect(a, name, True, n_pts)
+    _expect(freq_grid, "freq_grid", True, n_freq)
+    _expect(out_power, "out_power", p.precision == SSP_FP64, n_obj * n_freq, out=True)
+    _expect(out_best_period, "out_best_period", True, n_obj, out=True)
 
 
 def _dev_ptr(a):

@@ -144,6 +144,52 @@ def test_mode_fields_checked(field, value):
     assert ei.value.status == ssp.SSP_ERR_ARG
 
 
+def test_binding_checks_buffers_before_the_call():
+    # a buffer of the wrong element type, size or layout would be read or
+    # written past its end: the binding refuses it before calling the library
+    t, y, dy = np.arange(8.0), np.ones(8), np.ones(8)
+    ok = dict(t=t, y=y, dy=dy, n_per_object=[8], freq_grid=[0.3, 0.4])
+    bad_outputs = [
+        dict(out_power=np.empty((1, 2), dtype=np.float64)),        # FP32C writes float32
+        dict(out_power=np.empty((1, 3), dtype=np.float32)),        # wrong size
+        dict(out_power=np.empty((1, 4), dtype=np.float32)[:, ::2]),  # not contiguous
+        dict(out_best_period=np.empty(2)),
+        dict(t=np.arange(7.0), y=np.ones(7), dy=np.ones(7)),       # fewer points than n_per_object
+    ]
+    ro = np.empty((1, 2), dtype=np.float32)
+    ro.flags.writeable = False
+    bad_outputs.append(dict(out_power=ro))
+    for kw in bad_outputs:
+        args = dict(ok)
+        args.update(kw)
+        with pytest.raises(ValueError):
+            ssp.ssp_periodogram(**args)
+    # FP64 writes float64
+    with pytest.raises(ValueError):
+        ssp.ssp_periodogram(**ok, precision="fp64", out_power=np.empty((1, 2), dtype=np.float32))
+
+
+def test_binding_checks_device_buffers_before_the_call():
+    torch = pytest.importorskip("torch")
+    t = torch.arange(8.0, dtype=torch.float64)
+    fq = torch.tensor([0.3, 0.4], dtype=torch.float64)
+    pw, bp = torch.empty((1, 2), dtype=torch.float32), torch.empty(1, dtype=torch.float64)
+    cases = [
+        dict(t=t.float()),                              # float32 times
+        dict(t=t[:7]),                                  # too few points
+        dict(freq_grid=fq.float()),
+        dict(out_power=torch.empty((1, 2), dtype=torch.float64)),
+        dict(out_best_period=torch.empty(2, dtype=torch.float64)),
+    ]
+    for kw in cases:
+        args = dict(t=t, y=t, dy=t, n_per_object=[8], freq_grid=fq, out_power=pw,
+                    out_best_period=bp)
+        args.update(kw)
+        for fn in (ssp.ssp_periodogram_device, ssp.ssp_periodogram_device_noalloc):
+            with pytest.raises(ValueError, match="must be a contiguous"):
+                fn(**args)
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(ssp, "SO", str(tmp_path / "nope.so"))
     monkeypatch.setattr(ssp, "_lib", None)
