@@ -288,6 +288,8 @@ def ssp_autotune(t, y, dy, n_per_object, freq_grid, variant="ss", precision="fp3
     p = params if params is not None else ssp_default_params(precision, alpha, spans)
     t_, y_, dy_, fq = _f64(t), _f64(y), _f64(dy), _f64(freq_grid)
     npo = np.ascontiguousarray(n_per_object, dtype=np.int64)
+    for a, name in ((t_, "t"), (y_, "y"), (dy_, "dy")):
+        _expect(a, name, True, int(npo.sum()))
     out = np.zeros(5, dtype=np.int32)
     _check(lib().ssp_autotune(_ptr(t_), _ptr(y_), _ptr(dy_), _ptr(npo), int(npo.size), _ptr(fq),
                               int(fq.size), VARIANTS[variant], ctypes.byref(p), float(budget_ptf),
@@ -313,6 +315,8 @@ def ssp_search_refine(t, y, dy, n_per_object, coarse_grid, coarse_variant="sp",
                                                              periodic=periodic)
     t_, y_, dy_, cg = _f64(t), _f64(y), _f64(dy), _f64(coarse_grid)
     npo = np.ascontiguousarray(n_per_object, dtype=np.int64)
+    for a, name in ((t_, "t"), (y_, "y"), (dy_, "dy")):
+        _expect(a, name, True, int(npo.sum()))
     bp, bw = np.empty(npo.size), np.empty(npo.size)
     _check(lib().ssp_search_refine(_ptr(t_), _ptr(y_), _ptr(dy_), _ptr(npo), int(npo.size),
                                    _ptr(cg), int(cg.size), VARIANTS[coarse_variant],

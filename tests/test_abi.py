@@ -167,6 +167,11 @@ def test_binding_checks_buffers_before_the_call():
     # FP64 writes float64
     with pytest.raises(ValueError):
         ssp.ssp_periodogram(**ok, precision="fp64", out_power=np.empty((1, 2), dtype=np.float32))
+    # the other host entry points: points to match n_per_object
+    with pytest.raises(ValueError):
+        ssp.ssp_autotune(np.arange(7.0), np.ones(7), np.ones(7), [8], [0.3, 0.4])
+    with pytest.raises(ValueError):
+        ssp.ssp_search_refine(np.arange(7.0), np.ones(7), np.ones(7), [8], [0.3, 0.4])
 
 
 def test_binding_checks_device_buffers_before_the_call():
