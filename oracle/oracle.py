@@ -188,6 +188,8 @@ def power_one(t, y, dy, f, variant=SS, alpha=9.0, spans=None, iper=2, span=0.0):
     """Power at one frequency.  iper 2 = periodic windows, 1 = clamped;
     span > 0 = Listing 1's fixed-span smooth (either variant)."""
     t, y, dy = _f64(t), _f64(y), _f64(dy)
+    if not (t.size == y.size == dy.size):
+        raise ValueError("t, y and dy must have the same length")
     sp = _spans(spans)
     return lib().ssp_oracle_power_one(t.size, _p(t), _p(y), _p(dy), float(f), int(variant),
                                       float(alpha), _p(sp), int(iper), float(span))
@@ -198,6 +200,8 @@ def periodogram(t, y, dy, n_per_object, freq, variant=SS, alpha=9.0, spans=None,
     """Whole periodogram: returns (power[n_objects, n_freq], best_period[n_objects])."""
     t, y, dy, freq = _f64(t), _f64(y), _f64(dy), _f64(freq)
     npo = np.ascontiguousarray(n_per_object, dtype=np.int64)
+    if not (t.size == y.size == dy.size == int(npo.sum())):
+        raise ValueError("t, y and dy must hold sum(n_per_object) points each")
     nobj, nf = npo.size, freq.size
     power = np.empty((nobj, nf))
     best = np.empty(nobj)
@@ -232,6 +236,8 @@ def search_refine(t, y, dy, n_per_object, coarse, coarse_variant=SP, fine_varian
     """(best_period[n_objects], best_power[n_objects]) of search-and-refine."""
     t, y, dy, coarse = _f64(t), _f64(y), _f64(dy), _f64(coarse)
     npo = np.ascontiguousarray(n_per_object, dtype=np.int64)
+    if not (t.size == y.size == dy.size == int(npo.sum())):
+        raise ValueError("t, y and dy must hold sum(n_per_object) points each")
     bp, bw = np.empty(npo.size), np.empty(npo.size)
     if n_threads is None:
         n_threads = os.cpu_count() or 1
