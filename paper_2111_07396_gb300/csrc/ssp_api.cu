@@ -475,6 +475,14 @@ bool prof_begin(int phase, cudaStream_t s, Mark &m)
     return true;
 }
 
+// a launch failed after prof_begin: its two events are never recorded
+void prof_drop(bool on, Mark &m)
+{
+    if (!on) return;
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+}
+
 void prof_end(bool on, Mark &m, cudaStream_t s)
 {
     if (!on) return;
@@ -671,7 +679,10 @@ cudaError_t enqueue_pipeline(const Plan &plan, const Workspace &w, const double 
     pa.bad = w.bad;
     Mark mk;
     bool on = prof && prof_begin(SSP_PHASE_PREP, s, mk);
-    if ((e = prep_launch(prec, pa, (int)n_obj, s))) return e;
+    if ((e = prep_launch(prec, pa, (int)n_obj, s))) {
+        prof_drop(on, mk);
+        return e;
+    }
     if (hook) hook->launched(LK_PREP, &pa);
     prof_end(on, mk, s);
     size_t item_base = 0, slab_cur = 0, smo_cur = 0, redo_cur = 0;
@@ -725,8 +736,10 @@ cudaError_t enqueue_pipeline(const Plan &plan, const Workspace &w, const double 
         const int ph = variant == SSP_SS ? SSP_PHASE_PGRAM_SS : SSP_PHASE_PGRAM_SP;
         on = prof && prof_begin(ph, s, mk);
         if ((e = pgram_launch(prec, kv, b.main.gmem, b.main.lng, per, b.shared, b.main.grid, b.G,
-                              b.main.smem, ga, s)))
+                              b.main.smem, ga, s))) {
+            prof_drop(on, mk);
             return e;
+        }
         if (hook) hook->launched(LK_PGRAM, &ga);
         prof_end(on, mk, s);
         if (plan.redo && !b.main.redo_inline) {
@@ -743,8 +756,10 @@ cudaError_t enqueue_pipeline(const Plan &plan, const Workspace &w, const double 
             slab_cur += b.redo.gmem ? b.redo.slab_bytes * (size_t)b.redo.grid : 0;
             on = prof && prof_begin(SSP_PHASE_REDO, s, mk);
             if ((e = pgram_launch(kPrecRedo, kv, b.redo.gmem, b.redo.lng, per, b.shared, b.redo.grid,
-                                  b.G_redo, b.redo.smem, ga, s)))
+                                  b.G_redo, b.redo.smem, ga, s))) {
+                prof_drop(on, mk);
                 return e;
+            }
             if (hook) hook->launched(LK_PGRAM, &ga);
             prof_end(on, mk, s);
         }
@@ -759,7 +774,10 @@ cudaError_t enqueue_pipeline(const Plan &plan, const Workspace &w, const double 
     aa.best_period = out_best;
     aa.best_power = out_best_power;
     on = prof && prof_begin(SSP_PHASE_ARGMAX, s, mk);
-    if ((e = argmax_launch(prec, aa, (int)n_obj, s))) return e;
+    if ((e = argmax_launch(prec, aa, (int)n_obj, s))) {
+        prof_drop(on, mk);
+        return e;
+    }
     if (hook) hook->launched(LK_ARGMAX, &aa);
     prof_end(on, mk, s);
     return cudaSuccess;
