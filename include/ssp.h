@@ -180,7 +180,7 @@ int ssp_fold_fixed(const double *tt, int64_t n, double f, uint64_t *out);
  * frame must fit shared memory (about 2,500 points per object); larger
  * requests return SSP_ERR_UNSUPPORTED with the reason in ssp_last_error().
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress).
  * All calls share the one array and the library clears what must start at
  * zero on every call, so calls whose work overlaps on the GPU (different
  * streams, or several host threads) race with each other and must be
