@@ -305,9 +305,10 @@ int ssp_server_poll(ssp_server *s, int64_t ticket, int wait_ms, void *out_power,
 int ssp_server_destroy(ssp_server *s);
 
 /*
- * Autotuning of the launch plan.  Objects are planned in five length ranges
- * (n <= 384, <= 768, <= 1536, <= 2048, larger); each range runs one launch
- * whose threads per CTA follow a fixed rule by default.  ssp_autotune times
+ * Autotuning of the launch plan (the paper has no counterpart).  Objects
+ * are planned in five length ranges (n <= 384, <= 768, <= 1536, <= 2048,
+ * larger); each range runs one launch whose threads per CTA follow a fixed
+ * rule by default.  ssp_autotune times
  * the rule's choice, half of it and double it (within 32..512, at least two
  * centres per thread) for every range that the given objects (host arrays,
  * as ssp_periodogram) occupy.  The timing runs the full device pipeline on
@@ -373,12 +374,14 @@ int ssp_search_refine(const double *t, const double *y, const double *dy,
 enum { SSP_FAULT_ALLOC = 1, SSP_FAULT_STALL = 2, SSP_FAULT_UPLOAD = 3 };
 int ssp_test_fault(int kind, int count);
 
-/* Static text for a status code. */
+/* Static text for a status code (library plumbing; no counterpart in the
+ * paper).  Never NULL; the text is static. */
 const char *ssp_status_string(int status);
-/* Detail of the last error returned on the calling thread ("" if none). */
+/* Detail of the last error returned on the calling thread ("" if none).  The
+ * text belongs to the library and stays valid until the thread's next call. */
 const char *ssp_last_error(void);
 
-/* Library version string, "ssp <major>.<minor> sm_103a". */
+/* Library version string, "ssp <major>.<minor> sm_103a" (static text). */
 const char *ssp_version(void);
 
 /*
